@@ -1,0 +1,80 @@
+/* Plain FP64 CPU oracle of the coupled finite-difference / lattice-Boltzmann scheme
+ * for catalytic flow (Kulyk, Berger, Smith, Harting, arXiv:1804.07588).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is the slow, obviously-correct reference that the
+ * CUDA solver is checked against. Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load it. It shares no source, header, table or helper
+ * with the CUDA solver library.
+ *
+ * Scope: D2Q9 lattice (the paper's lattice, Sec. 2, Eq. cx).
+ */
+#ifndef FDLBM_ORACLE_H
+#define FDLBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_MAX_NS 8
+#define ORA_MAX_NR 4
+
+/* Problem description, every array host-owned and copied at ora_create. */
+typedef struct {
+  int nx, ny;                      /* D2Q9 lattice size */
+  const unsigned char* mask;       /* nx*ny, x fastest: 0 gas, 1 inert solid, 2 catalytic */
+  int face_bc[4];                  /* x-, x+, y-, y+: 0 periodic 1 inlet 2 outlet 3 closed 4 fixed-T */
+  int ns;                          /* species count */
+  double M_gmol[ORA_MAX_NS];       /* molar masses (scaled by the lightest inside) */
+  double tau1[ORA_MAX_NS], tau2[ORA_MAX_NS];
+  double X_init[ORA_MAX_NS], X_inlet[ORA_MAX_NS];
+  double Pr; int energy_correction;
+  double T0_K, T_init_K, T_inlet_K, T_solid_init_K, T_outer_K;
+  double u_inlet; int inlet_profile;          /* 0 plug, 1 parabolic */
+  double alpha_s, rhocp_s, kappa_f; int coupling; /* 0 conservative, 1 paper law */
+  int nr;
+  int nu[ORA_MAX_NR][ORA_MAX_NS];
+  double k0[ORA_MAX_NR], Ea_Jmol[ORA_MAX_NR], Keq[ORA_MAX_NR], dH_Jmol[ORA_MAX_NR];
+  int rate_form[ORA_MAX_NR];                  /* 0 concentration bilinear, 1 mole-fraction reversible */
+  double rho_w_tol; int rho_w_maxit;
+  const double* init_X;   /* optional [ns][n] mole fractions */
+  const double* init_u;   /* optional [2][n] */
+  const double* init_T;   /* optional [n] gas temperature, K */
+  const double* init_Ts;  /* optional [n] solid temperature, K */
+  const double* init_C;   /* optional [n] molar concentration (lattice, default 1) */
+} ora_problem;
+
+typedef struct ora_state ora_state;
+
+/* Ledger layout returned by ora_balance (all lattice energy units). */
+enum {
+  ORA_B_STEPS = 0, ORA_B_E_GAS, ORA_B_E_GAS0, ORA_B_H_SOLID, ORA_B_H_SOLID0,
+  ORA_B_Q_RXN, ORA_B_Q_WALL, ORA_B_Q_COUPLE, ORA_B_Q_FIXEDT, ORA_B_RESIDUAL, ORA_B_SOLID_RESIDUAL,
+  ORA_B_EPS_PAPER, ORA_B_NOCONV, ORA_B_MASS /* then mass[ns], mass0[ns], moles[ns], moles0[ns] */
+};
+
+ora_state* ora_create(const ora_problem* p, char* err, int errlen);
+void ora_destroy(ora_state* s);
+int ora_step(ora_state* s, int nsteps);
+int ora_nfields(const ora_state* s);                 /* 2*ns + 4 */
+void ora_moments(const ora_state* s, double* out);   /* [field][n]: rho_j, X_j, ux, uy, T_K, Ts_K */
+void ora_populations(const ora_state* s, double* out); /* [ns][9][n] stored post-collision / wall-emitted */
+void ora_balance(const ora_state* s, double* out);
+double ora_residual(ora_state* s, int K);
+void ora_counts(const ora_state* s, long* out);      /* class counts [5] + stencil counts [6] */
+void ora_classes(const ora_state* s, int* out);      /* per-node class */
+
+/* Point functions exposed so that the test-suite can pin them individually. */
+void ora_units(double T0_K, double M0_gmol, double dx_m, double* out3);
+void ora_equilibrium(double rho, double ux, double uy, double M, double T, double* f9);
+double ora_interp(int code, double c, double s3, double s2, double s1, double s0, double sp);
+void ora_psi(double c, double* psix9, double* psiy9);
+void ora_phi(double c, double* phi9);
+double ora_uc(int ns, const double* rho, const double* Jx, const double* tau2, double ux);
+void ora_collide(int ns, const double* M, const double* tau1, const double* tau2,
+                 const double* g /* [ns][9] pulled */, const double* divq /* [ns] */,
+                 double* gout /* [ns][9] */, double* mom /* rho_j[ns], ux, uy, T, Tg */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

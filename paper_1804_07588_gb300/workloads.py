@@ -1,0 +1,260 @@
+"""Seeded synthetic workloads for the coupled FD-LBM solver.
+
+This module only *describes* problems: geometry masks, species and kinetics tables,
+solid properties and (optionally) random initial macroscopic fields. It holds none of
+the scheme's arithmetic -- no equilibria, no unit conversion, no streaming -- so that
+the CUDA library and the FP64 CPU oracle can both be fed from it while sharing no
+numerical code.
+
+A problem is a plain ``dict`` (see :func:`channel`, :func:`porous_disks`,
+:func:`periodic_box`) with these keys:
+
+``dim, nx, ny, nz, lattice``   lattice shape; ``lattice`` is 9 (D2Q9) or 19 (D3Q19)
+``mask``                       uint8 array, flat, x fastest: 0 gas, 1 inert solid,
+                               2 catalytic solid
+``face_bc``                    six ints for faces x-, x+, y-, y+, z-, z+:
+                               0 periodic, 1 inlet, 2 outlet, 3 closed, 4 fixed-T
+``species``                    list of dicts ``name, M_gmol, tau1, tau2, X_init, X_inlet``
+``Pr, energy_correction``      Prandtl number of the correction term and its switch
+``T0_K, T_init_K, T_inlet_K, T_solid_init_K, T_outer_K``  temperatures in kelvin
+``u_inlet, inlet_profile``     inlet velocity (lattice units); 0 plug, 1 parabolic
+``alpha_s, rhocp_s, kappa_f``  solid diffusivity and volumetric heat capacity, gas
+                               conductivity for the paper's wall-temperature coupling
+``coupling``                   0 conservative (default), 1 the paper's wall-temperature law
+``reactions``                  list of dicts ``nu, k0, Ea_Jmol, Keq, dH_Jmol, rate_form``
+``rho_w_tol, rho_w_maxit``     wall-density iteration tolerance and cap
+``init``                       ``None`` or dict of float64 arrays ``X [ns, n]``,
+                               ``u [dim, n]``, ``T_K [n]``, ``Ts_K [n]``, ``C [n]``
+                               (molar concentration, lattice units, default 1)
+
+The workloads follow the paper's test set-ups and the configurations the benchmark is
+quoted on: a catalytic channel between FD-solid walls (water-gas shift at the walls,
+Sec. 5 and Sec. 6 of the paper), a 2D porous bed of catalytic disks, and small periodic
+boxes used for conservation checks.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Faces and mask codes (mirrored by the C header and the oracle header).
+PERIODIC, INLET, OUTLET, CLOSED, FIXED_T = 0, 1, 2, 3, 4
+GAS, INERT, CATALYTIC = 0, 1, 2
+PLUG, PARABOLIC = 0, 1
+CONSERVATIVE, PAPER = 0, 1
+RATE_CONC_BILINEAR, RATE_XFRAC_REVERSIBLE = 0, 1
+
+# Molar masses (g/mol) built from standard atomic weights so that the water-gas
+# shift CO + H2O -> CO2 + H2 balances mass to rounding.
+_A = {"C": 12.011, "O": 15.999, "H": 1.008, "N": 14.007}
+MOLAR_MASS = {
+    "CO": _A["C"] + _A["O"],
+    "H2O": 2 * _A["H"] + _A["O"],
+    "CO2": _A["C"] + 2 * _A["O"],
+    "H2": 2 * _A["H"],
+    "N2": 2 * _A["N"],
+}
+SPECIES_ORDER = ("CO", "H2O", "CO2", "H2", "N2")
+
+# Relaxation times (lattice units) in the 0.6-1.0 range of the benchmark
+# configurations; tau1 (viscous/thermal) and tau2 (diffusive) differ so that both
+# relaxation stages of the two-step collision are exercised.
+TAU1 = {"CO": 0.8, "H2O": 0.7, "CO2": 1.0, "H2": 0.6, "N2": 0.9}
+TAU2 = {"CO": 0.7, "H2O": 0.9, "CO2": 0.65, "H2": 1.0, "N2": 0.75}
+
+# Inlet composition CO/H2O/CO2/H2/N2 = 0.1/0.1/0/0/0.8 with the product species held
+# at a 1e-6 trace (the paper's own inlet keeps 1e-6 of the products, Sec. 6) and the
+# balance taken from N2.
+X_INLET = {"CO": 0.1, "H2O": 0.1, "CO2": 1e-6, "H2": 1e-6, "N2": 0.8 - 2e-6}
+
+# Solid: diffusivity 0.03 in lattice units (the paper's showcase value). The volumetric
+# heat capacity 20.6 makes the solid conductivity alpha_s * rhocp_s ten times the gas
+# conductivity 0.0618 of the inlet mixture (nu / Pr times the 2D molar heat capacity
+# C (D + 2) / 2 at C = 1, T = 1/3, Pr = 0.7); 0.0618 is also the gas conductivity used
+# by the paper's wall-temperature law.
+ALPHA_S = 0.03
+RHOCP_S = 20.6
+KAPPA_F = 0.0618
+
+
+def wgs_reaction(k0: float = 167.0, Ea_Jmol: float = 50e3, Keq: float = 10.0,
+                 dH_Jmol: float = -41e3, rate_form: int = RATE_XFRAC_REVERSIBLE,
+                 order=SPECIES_ORDER) -> dict:
+    """Water-gas shift CO + H2O -> CO2 + H2 on the catalytic walls.
+
+    ``k0`` is in lattice moles per wall node per step at unit mole fractions; 167
+    gives k(500 K) ~ 1e-3 with Ea = 50 kJ/mol.
+    """
+    stoich = {"CO": -1, "H2O": -1, "CO2": 1, "H2": 1, "N2": 0}
+    return {"nu": [stoich.get(s, 0) for s in order], "k0": k0, "Ea_Jmol": Ea_Jmol,
+            "Keq": Keq, "dH_Jmol": dH_Jmol, "rate_form": rate_form}
+
+
+def species_table(order=SPECIES_ORDER, X_init=None, X_inlet=None, tau1=None, tau2=None):
+    X_init = X_init or X_INLET
+    X_inlet = X_inlet or X_INLET
+    tau1 = tau1 or TAU1
+    tau2 = tau2 or TAU2
+    return [{"name": s, "M_gmol": MOLAR_MASS[s], "tau1": tau1[s], "tau2": tau2[s],
+             "X_init": X_init[s], "X_inlet": X_inlet[s]} for s in order]
+
+
+def _base(dim, nx, ny, nz, mask, face_bc, **kw) -> dict:
+    p = {
+        "dim": dim, "nx": nx, "ny": ny, "nz": nz, "lattice": 9 if dim == 2 else 19,
+        "mask": np.ascontiguousarray(mask.reshape(-1), dtype=np.uint8),
+        "face_bc": list(face_bc) + [PERIODIC] * (6 - len(face_bc)),
+        "species": species_table(),
+        "Pr": 0.7, "energy_correction": 1,
+        "T0_K": 500.0, "T_init_K": 500.0, "T_inlet_K": 500.0,
+        "T_solid_init_K": 500.0, "T_outer_K": 500.0,
+        "u_inlet": 0.0, "inlet_profile": PLUG,
+        "alpha_s": ALPHA_S, "rhocp_s": RHOCP_S, "kappa_f": KAPPA_F,
+        "coupling": CONSERVATIVE,
+        "reactions": [wgs_reaction()],
+        "rho_w_tol": 1e-8, "rho_w_maxit": 50,
+        "init": None,
+    }
+    p.update(kw)
+    return p
+
+
+def channel(nx: int = 128, n_gas: int = 32, wall: int = 8, u_inlet: float = 0.02,
+            profile: int = PARABOLIC, **kw) -> dict:
+    """Catalytic channel: ``n_gas`` gas rows between two ``wall``-thick FD-solid walls.
+
+    Inlet on x-, outlet on x+, outer solid faces held at ``T_outer_K``. With the
+    defaults this is the 128x32 channel with 8-node walls (128 x 48 lattice).
+    """
+    ny = n_gas + 2 * wall
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[:wall, :] = CATALYTIC
+    mask[wall + n_gas:, :] = CATALYTIC
+    return _base(2, nx, ny, 1, mask, [INLET, OUTLET, FIXED_T, FIXED_T],
+                 u_inlet=u_inlet, inlet_profile=profile, **kw)
+
+
+def disk_mask(nx: int, ny: int, porosity: float, rmin: float, rmax: float, seed: int,
+              free_cols: int = 17, gap: float = 2.0, max_tries: int = 2_000_000):
+    """Seeded random sequential addition of non-overlapping disks, periodic in y.
+
+    Disk radii are uniform in [rmin, rmax]; centres keep ``gap`` lattice units of
+    clearance between disk surfaces and stay ``free_cols`` columns away from the inlet
+    and outlet. Disks are added until the digitised solid fraction of the whole
+    lattice reaches ``1 - porosity``. Returns (mask, list of (cx, cy, r)).
+    """
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((ny, nx), bool)
+    target = (1.0 - porosity) * nx * ny
+    n_solid = 0
+    disks = []
+    cx_arr = np.zeros(0)
+    cy_arr = np.zeros(0)
+    r_arr = np.zeros(0)
+    tries = 0
+    while n_solid < target:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("disk packing did not reach the target porosity")
+        r = rng.uniform(rmin, rmax)
+        lo = free_cols + r + 1
+        hi = nx - 1 - free_cols - r - 1
+        cx = rng.uniform(lo, hi)
+        cy = rng.uniform(0, ny)
+        if len(disks):
+            dy = np.abs(cy_arr - cy)
+            dy = np.minimum(dy, ny - dy)
+            d = np.hypot(cx_arr - cx, dy)
+            if np.any(d < r_arr + r + gap):
+                continue
+        disks.append((cx, cy, r))
+        cx_arr = np.append(cx_arr, cx)
+        cy_arr = np.append(cy_arr, cy)
+        r_arr = np.append(r_arr, r)
+        xs = np.arange(int(math.floor(cx - r)), int(math.ceil(cx + r)) + 1)
+        ys = np.arange(int(math.floor(cy - r)), int(math.ceil(cy + r)) + 1)
+        dy = ys[:, None] - cy
+        inside = (xs[None, :] - cx) ** 2 + dy ** 2 <= r * r
+        yw = np.broadcast_to((ys % ny)[:, None], inside.shape)[inside]
+        xw = np.broadcast_to(xs[None, :], inside.shape)[inside]
+        n_solid += int((~solid[yw, xw]).sum())
+        solid[yw, xw] = True
+    mask = np.where(solid, CATALYTIC, GAS).astype(np.uint8)
+    return mask, disks
+
+
+def porous_disks(nx: int = 1024, ny: int = 512, porosity: float = 0.6, rmin: float = 6.0,
+                 rmax: float = 12.0, seed: int = 1000, u_inlet: float = 0.01, **kw) -> dict:
+    """2D porous bed of catalytic FD-solid disks, inlet x-, outlet x+, periodic in y.
+
+    Defaults: the 1024x512 bed with radii U[6, 12], porosity 0.6 and plug inlet 0.01.
+    """
+    mask, _ = disk_mask(nx, ny, porosity, rmin, rmax, seed)
+    return _base(2, nx, ny, 1, mask, [INLET, OUTLET, PERIODIC, PERIODIC],
+                 u_inlet=u_inlet, inlet_profile=PLUG, **kw)
+
+
+def periodic_box(nx: int = 16, ny: int = 12, solid_rows: int = 0, solid_cols: int = 0,
+                 **kw) -> dict:
+    """Fully periodic box. ``solid_rows`` > 0 puts a catalytic solid slab of that many
+    rows at the bottom; ``solid_cols`` > 0 a slab of that many columns on the left (the
+    quasi-1D 200 x 3 solid/gas enthalpy test of the paper, Sec. 5, is
+    ``periodic_box(200, 3, solid_cols=100)``)."""
+    mask = np.zeros((ny, nx), np.uint8)
+    if solid_rows:
+        mask[:solid_rows, :] = CATALYTIC
+    if solid_cols:
+        mask[:, :solid_cols] = CATALYTIC
+    return _base(2, nx, ny, 1, mask, [PERIODIC] * 4, **kw)
+
+
+def smooth_noise(shape, rng, modes: int = 4) -> np.ndarray:
+    """Sum of a few random low-order Fourier modes, scaled to max |value| = 1."""
+    ny, nx = shape
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    out = np.zeros(shape)
+    for _ in range(modes):
+        kx = rng.integers(0, 4)
+        ky = rng.integers(0, 4)
+        ph = rng.uniform(0, 2 * np.pi)
+        out += rng.normal() * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny) + ph)
+    m = np.abs(out).max()
+    return out / m if m > 0 else out
+
+
+def random_fields(p: dict, seed: int, dX: float = 0.2, du: float = 0.01,
+                  dT_K: float = 5.0, dTs_K: float = 5.0) -> dict:
+    """Seeded smooth random initial fields around the problem's initial state.
+
+    Mole fractions are scaled by (1 + dX * noise) and renormalised, velocities are
+    +-``du``, gas and solid temperatures deviate by up to ``dT_K`` / ``dTs_K``.
+    """
+    if p["dim"] != 2:
+        raise NotImplementedError("random_fields: 2D only")
+    rng = np.random.default_rng(seed)
+    ny, nx = p["ny"], p["nx"]
+    ns = len(p["species"])
+    X0 = np.array([s["X_init"] for s in p["species"]])
+    X = np.empty((ns, ny, nx))
+    for j in range(ns):
+        X[j] = X0[j] * (1.0 + dX * smooth_noise((ny, nx), rng))
+    X /= X.sum(axis=0, keepdims=True)
+    u = np.stack([du * smooth_noise((ny, nx), rng), du * smooth_noise((ny, nx), rng)])
+    T = p["T_init_K"] + dT_K * smooth_noise((ny, nx), rng)
+    Ts = p["T_solid_init_K"] + dTs_K * smooth_noise((ny, nx), rng)
+    n = nx * ny
+    return {"X": X.reshape(ns, n).copy(), "u": u.reshape(2, n).copy(),
+            "T_K": T.reshape(n).copy(), "Ts_K": Ts.reshape(n).copy()}
+
+
+def config0(**kw) -> dict:
+    """2D D2Q9 catalytic channel: 128x32 gas nodes between two 8-node FD-solid walls,
+    parabolic inlet peak 0.02, T_in = walls = 500 K (run length 2000 steps)."""
+    return channel(**kw)
+
+
+def config1(**kw) -> dict:
+    """2D D2Q9 porous bed 1024x512, catalytic disks r ~ U[6, 12], porosity 0.6, seed
+    1000, plug inlet 0.01 (run length 20000 steps)."""
+    return porous_disks(**kw)
