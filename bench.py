@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled FD-LBM solver on the 2D porous catalytic bed
+(D2Q9, 1024 x 512 nodes, catalytic FD-solid disks r ~ U[6, 12], porosity 0.6, five
+species CO/H2O/CO2/H2/N2 with water-gas shift on the disk surfaces, FP32 storage).
+
+A step is one time step of the whole scheme: the wall + solid kernel and the fused gas
+kernel. Timing: W untimed warm-up steps, then K timed steps, each preceded by an L2
+flush (a 256 MB write, untimed) and bracketed by CUDA events on the solver's stream.
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle instead
+on a bounded crop of the same bed.
+
+Multi-GPU (torchrun, N > 1): the problem does not need more than one GPU; every rank
+runs an independent replica of the bed and the line reports the aggregate throughput
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "species-MLUPS & % HBM roofline; time-to-steady (res 1e-6) warm vs cold"
+UNIT = "species-MLUPS"
+BYTES_PER_SPECIES_NODE = 72  # D2Q9 FP32: read 9 + write 9 populations
+WORKLOAD = "porous-bed-d2q9-1024x512-5species-fp32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fdlbm", choices=["fdlbm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fdlbm_kernels.cu", "fdlbm_internal.h"):
+        with open(os.path.join(ROOT, "paper_1804_07588_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per gas-kernel launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "gas_kernel_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def crop_problem(n_target: int):
+    """A bounded sample of the benchmark bed: the top-left crop of the same seeded disk
+    packing with the last two columns opened for the outlet."""
+    import numpy as np
+
+    from paper_1804_07588_gb300 import workloads as W
+    full = W.config1()
+    side = max(32, int(math.sqrt(n_target)) // 8 * 8)
+    w, h = min(side, 1024), min(side, 512)
+    mask = full["mask"].reshape(512, 1024)[:h, :w].copy()
+    mask[:, w - 2:] = W.GAS
+    p = W._base(2, w, h, 1, mask, [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC],
+                u_inlet=full["u_inlet"], inlet_profile=W.PLUG)
+    return p, f"top-left {w}x{h} crop of the 1024x512 bed (same disk packing), outlet opened"
+
+
+def oracle_throughput(seconds: float = 10.0, n_target: int = 16384, max_steps=None):
+    import oracle
+    p, desc = crop_problem(n_target)
+    o = oracle.Oracle(p)
+    n_gas = o.counts()["gas"]
+    ns = len(p["species"])
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if max_steps is not None and steps >= max_steps:
+            break
+        if max_steps is None and el >= seconds and steps >= 3:
+            break
+    el = time.perf_counter() - t0
+    return ns * n_gas * steps / el / 1e6, f"{desc}, {steps} steps, {n_gas} gas nodes", el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    # each step a bounded sample: the crop is sized so that W + K oracle steps take about
+    # a minute or two on one host core.
+    total = max(args.steps + args.warmup, 1)
+    n_target = int(max(1024, min(65536, 40e6 / total)))
+    import oracle
+    p, desc = crop_problem(n_target)
+    o = oracle.Oracle(p)
+    n_gas = o.counts()["gas"]
+    ns = len(p["species"])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = ns * n_gas * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / max(args.steps, 1) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc, "oracle": "plain FP64 C, one host core"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_fdlbm(args, rank, world, local_rank):
+    import torch
+
+    from paper_1804_07588_gb300 import fdlbm, workloads
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
+    dev = local_rank
+    torch.cuda.set_device(dev)
+    p = workloads.config1()
+    s = fdlbm.Solver(p, device=dev)
+    info = s.info()
+    ns = info["ns"]
+    n_gas = info["n_gas"]
+    stream = s.stream
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=f"cuda:{dev}")  # 256 MB > L2
+    s.step(args.warmup)
+    s.sync()
+    s.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[k].record(stream)
+        s.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    ms_solid, ms_gas, timed = s.kernel_times()
+    s.profile(False)
+    s.sync()
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = ns * n_gas * args.steps * world
+    value = units / (total_ms * 1e-3) / 1e6
+    gas_ms = ms_gas / max(timed, 1)
+    alg_bytes = BYTES_PER_SPECIES_NODE * ns * n_gas
+    achieved = alg_bytes / (gas_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        s2 = fdlbm.Solver(p, device=dev)
+        s2.step(args.steps)
+        m = s2.moments_host()
+        s2.sync()
+        el = time.perf_counter() - t0
+        n = p["nx"] * p["ny"]
+        h2d = 4 * n + 4 * (info["n_wall"] + info["n_solid"]) + 8 * (ns + 5) * n + 8 * (p["ny"] + ns + 1) + n
+        d2h = m.nbytes
+        e2e = {"value": ns * n_gas * args.steps / el / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "what": "whole job through the C ABI: fdlbm_create from host arrays (geometry, "
+                       "initial fields), K steps, moment fields read back to host"}
+        s2.close()
+        del np
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, desc, el = oracle_throughput(seconds=10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(el, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": p["nx"], "ny": p["ny"], "porosity": 0.6,
+                       "species": ns, "gas_nodes": n_gas, "wall_nodes": info["n_wall"],
+                       "solid_nodes": info["n_solid"], "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "roofline": {"bound": "hbm", "kernel": "gas_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(),
+                         "peak_kind": peak_kind + " copy bandwidth",
+                         "alg_bytes_per_launch": alg_bytes, "gas_ms_per_launch": gas_ms,
+                         "solid_ms_per_launch": ms_solid / max(timed, 1)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_fdlbm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/* fdlbm.h — C ABI of the GB300 (sm_103a) solver for the coupled finite-difference /
+ * lattice-Boltzmann scheme for catalytic flow of Kulyk, Berger, Smith and Harting,
+ * "Catalytic flow with a coupled Finite Difference - Lattice Boltzmann scheme"
+ * (arXiv:1804.07588).
+ *
+ * One time step of the solver is the paper's scheme on a D2Q9 lattice:
+ *   - the multicomponent thermal LBM gas (Sec. 2-4): one population set per species,
+ *     off-lattice quadratic interpolation while streaming heavy species (Sec. 4.2),
+ *     two-step quasi-equilibrium collision of the transformed populations g with the
+ *     diffusion-velocity and energy correction terms (Eq. final_kinetic_equation);
+ *   - reactive diffusive-wall boundary conditions on gas-solid interface nodes with the
+ *     iterated wall density (Sec. 4.3, Eq. BC_gji);
+ *   - the explicit FD heat equation in the solid coupled through the interface nodes,
+ *     which also receive the reaction heat (Sec. 5, Eqs. heat_equation_fd,
+ *     wall_temperature).
+ *
+ * Conventions (every call):
+ *   - Every function returns an fdlbm_status; nothing throws across the ABI.
+ *   - Host pointers passed to fdlbm_create / fdlbm_set_fields are read during the call
+ *     only (the library copies what it needs); the caller keeps ownership.
+ *   - Output buffers are caller-owned. Device output pointers must be device memory of
+ *     the handle's device; transfers and kernels run on the handle's stream.
+ *   - Device memory is taken from the caller's allocator (fdlbm_options.alloc) or
+ *     cudaMalloc and released by fdlbm_destroy.
+ *   - Lattice nodes are indexed n = x + nx * y (x fastest); field arrays are
+ *     [field][n] in that order.
+ *   - Error messages of the last failing call on this thread: fdlbm_last_error().
+ */
+#ifndef FDLBM_H
+#define FDLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDLBM_MAX_SPECIES 6
+#define FDLBM_MAX_REACTIONS 4
+
+typedef struct fdlbm_handle fdlbm_handle; /* opaque, library-owned */
+
+typedef enum {
+  FDLBM_OK = 0,
+  FDLBM_EINVAL = -1,    /* bad argument or unsupported combination */
+  FDLBM_EGEOM = -2,     /* geometry rejected (gas touching a closed face, bad outlet) */
+  FDLBM_ECUDA = -3,     /* CUDA runtime error */
+  FDLBM_EUNSTABLE = -4, /* the gas kernel saw a non-finite or non-positive density/temperature */
+  FDLBM_ENOCONV = -5,   /* reserved: wall-density iteration cap reached (counted, see balance) */
+  FDLBM_ETIMEOUT = -6,  /* reserved for bounded device waits */
+  FDLBM_ENOMEM = -7     /* device allocation failed */
+} fdlbm_status;
+
+enum { FDLBM_D2Q9 = 9 };
+/* Face boundary kinds for faces x-, x+, y-, y+ (indices 0..3). Periodic faces come in
+ * pairs; inlet only on x-, outlet only on x+. */
+enum { FDLBM_FACE_PERIODIC = 0, FDLBM_FACE_INLET = 1, FDLBM_FACE_OUTLET = 2,
+       FDLBM_FACE_CLOSED = 3, FDLBM_FACE_FIXED_T = 4 };
+/* Geometry mask values. */
+enum { FDLBM_MASK_GAS = 0, FDLBM_MASK_INERT = 1, FDLBM_MASK_CATALYTIC = 2 };
+enum { FDLBM_PROFILE_PLUG = 0, FDLBM_PROFILE_PARABOLIC = 1 };
+/* Interface coupling: CONSERVATIVE gives the solid exactly the energy its diffusive
+ * wall took from the gas; PAPER is the wall-temperature law of Eq. wall_temperature. */
+enum { FDLBM_COUPLING_CONSERVATIVE = 0, FDLBM_COUPLING_PAPER = 1 };
+/* Surface rate laws: k C_a C_b of Eq. showcase_Sj, or the reversible mole-fraction
+ * law k (prod x_reactants - prod x_products / Keq). */
+enum { FDLBM_RATE_CONC_BILINEAR = 0, FDLBM_RATE_XFRAC_REVERSIBLE = 1 };
+enum { FDLBM_STORAGE_FP32 = 0 };
+
+/* Lattice and geometry (Sec. 4.3: walls sit on the solid nodes next to the gas). */
+typedef struct {
+  int nx, ny;              /* lattice size, each >= 4 */
+  int lattice;             /* FDLBM_D2Q9 */
+  const uint8_t* mask;     /* host, nx*ny, FDLBM_MASK_* */
+  int face_bc[4];          /* FDLBM_FACE_* for x-, x+, y-, y+ */
+} fdlbm_geometry;
+
+/* One gas species (Sec. 2; relaxation times in lattice units). */
+typedef struct {
+  double M_gmol;           /* molar mass; the lightest species streams on-lattice */
+  double tau1, tau2;       /* relaxation times of Eq. bare_kinetic_eq, > 0 */
+  double X_init, X_inlet;  /* default initial and inlet mole fractions */
+} fdlbm_species;
+
+/* Transport, thermal and solid parameters. Temperatures in kelvin; the lattice
+ * temperature is T / (3 T0) (Sec. 4.1). */
+typedef struct {
+  double Pr;               /* Prandtl number of the energy correction (Eq. q_Pr) */
+  int energy_correction;   /* 1: apply the energy correction Phi, 0: none */
+  double T0_K, T_init_K, T_inlet_K, T_solid_init_K, T_outer_K;
+  double u_inlet;          /* inlet velocity (peak for the parabolic profile), lattice */
+  int inlet_profile;       /* FDLBM_PROFILE_* */
+  double alpha_s;          /* solid thermal diffusivity, lattice (Eq. heat_equation_fd) */
+  double rhocp_s;          /* solid volumetric heat capacity, lattice energy / lattice T */
+  double kappa_f;          /* gas conductivity used by FDLBM_COUPLING_PAPER */
+  int coupling;            /* FDLBM_COUPLING_* */
+} fdlbm_transport;
+
+/* Surface reactions on catalytic wall nodes (Sec. 4.3 and Sec. 6). */
+typedef struct {
+  int n_react;
+  int nu[FDLBM_MAX_REACTIONS][FDLBM_MAX_SPECIES]; /* stoichiometry, <0 reactants */
+  double k0[FDLBM_MAX_REACTIONS];      /* lattice moles per wall node per step */
+  double Ea_Jmol[FDLBM_MAX_REACTIONS];
+  double Keq[FDLBM_MAX_REACTIONS];
+  double dH_Jmol[FDLBM_MAX_REACTIONS]; /* reaction enthalpy, < 0 exothermic */
+  int rate_form[FDLBM_MAX_REACTIONS];  /* FDLBM_RATE_* */
+  double rho_w_tol;                    /* wall-density iteration tolerance (1e-8) */
+  int rho_w_maxit;                     /* iteration cap */
+} fdlbm_kinetics;
+
+/* Optional initial fields (host, may be NULL individually): mole fractions [ns][n],
+ * velocity [2][n] (lattice), gas and solid temperatures [n] (K), molar concentration
+ * [n] (lattice, default 1). */
+typedef struct {
+  const double* X;
+  const double* u;
+  const double* T_K;
+  const double* Ts_K;
+  const double* C;
+} fdlbm_fields;
+
+/* Device memory and stream. alloc/free may be NULL (cudaMalloc / cudaFree). stream is a
+ * cudaStream_t (NULL: the legacy default stream). */
+typedef struct {
+  int storage;             /* FDLBM_STORAGE_FP32 */
+  int device;              /* CUDA device ordinal */
+  void* stream;
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* alloc_ctx;
+} fdlbm_options;
+
+/* Counts and derived constants of a handle. */
+typedef struct {
+  int64_t n_nodes, n_gas, n_inlet, n_outlet, n_wall, n_solid;
+  int64_t stencil_counts[6]; /* gas + wall pull directions by stencil: none, central,
+                                forward, backward, linear-s0, linear-s2 */
+  int ns;
+  double T_ref_lat;          /* lattice reference temperature T_inlet / (3 T0) */
+  int64_t steps;
+  size_t device_bytes;       /* device memory held by the handle */
+} fdlbm_info_t;
+
+/* FP64 ledger (Sec. 5, enthalpy conservation; lattice energy units, energy of the gas
+ * = internal + kinetic from the f-moments plus the populations emitted by walls and not
+ * yet streamed into the gas). */
+typedef struct {
+  int64_t steps;
+  double E_gas, E_gas0, H_solid, H_solid0;
+  double Q_reaction;       /* cumulative reaction heat released into wall nodes */
+  double Q_wall;           /* cumulative energy the diffusive walls put into the gas */
+  double Q_couple;         /* cumulative energy the solid received from the gas coupling */
+  double Q_fixedT;         /* cumulative heat into the solid through fixed-T faces */
+  double residual;         /* dE_gas + dH_solid - Q_reaction - Q_fixedT */
+  double solid_residual;   /* dH_solid - (Q_reaction + Q_couple + Q_fixedT) */
+  double eps_paper;        /* Eq. error_coupling with the gas-phase change of the first
+                              reactant of reaction 0 */
+  double noconv;           /* wall-density iterations that hit the cap */
+  double mass[FDLBM_MAX_SPECIES], mass0[FDLBM_MAX_SPECIES];
+  double moles[FDLBM_MAX_SPECIES], moles0[FDLBM_MAX_SPECIES];
+} fdlbm_balance;
+
+/* Build a solver: validate, convert units, classify nodes (gas / inlet / outlet /
+ * interface wall / solid), precompute the streaming stencil of every pull, allocate
+ * device state and initialise g* = f^eq(initial fields), wall emissions and T_s.
+ * init and opts may be NULL. On success *out owns device memory until fdlbm_destroy.
+ * Errors: EINVAL (parameters), EGEOM (geometry), ENOMEM, ECUDA. */
+fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* species, int n_species,
+                          const fdlbm_transport* tr, const fdlbm_kinetics* kin,
+                          const fdlbm_fields* init, const fdlbm_options* opts, fdlbm_handle** out);
+
+/* Enqueue n >= 0 time steps on the handle's stream (asynchronous). Each step is the
+ * wall + solid kernel (Sec. 4.3, Sec. 5) followed by the fused gas kernel (Sec. 4). */
+fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n);
+
+/* Wait for the handle's stream and report sticky device errors (EUNSTABLE). */
+fdlbm_status fdlbm_sync(fdlbm_handle* h);
+
+/* Moment fields at the current time into dst, [2 ns + 4][n] float32: rho_j, X_j, ux, uy,
+ * T (K) on gas nodes, T_s (K) on solid nodes, 0 elsewhere. dst_on_device selects a
+ * device or host destination; a host copy is synchronous. */
+fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device);
+
+/* Stored populations g* (post-collision on gas, inlet and outlet nodes, emissions on
+ * wall nodes), [ns][9][n] float32 (absolute values, not deviations). */
+fdlbm_status fdlbm_populations(fdlbm_handle* h, float* dst, int dst_on_device);
+
+/* FP64 ledger (synchronous). */
+fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out);
+
+/* Steady-state residual since the previous call (first call: +inf), K = steps since
+ * then; synchronous. */
+fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out);
+
+/* Re-initialise the gas (and solid) state from fields (warm start); NULL members keep
+ * the defaults of fdlbm_create. The ledger is reset. */
+fdlbm_status fdlbm_set_fields(fdlbm_handle* h, const fdlbm_fields* f);
+
+fdlbm_status fdlbm_info(const fdlbm_handle* h, fdlbm_info_t* out);
+
+/* Kernel timing for benchmarks. With enable != 0, fdlbm_step records CUDA events on the
+ * handle's stream around the solid kernel and the gas kernel of each step (at most
+ * 65536 steps are kept). fdlbm_kernel_times waits for the stream, writes the summed
+ * milliseconds {solid, gas} and the number of timed steps, and clears the record. */
+fdlbm_status fdlbm_profile(fdlbm_handle* h, int enable);
+fdlbm_status fdlbm_kernel_times(fdlbm_handle* h, double* ms_out2, int64_t* steps_out);
+
+void fdlbm_destroy(fdlbm_handle* h);
+
+/* Message of the last failing call on this thread (library-owned, never NULL). */
+const char* fdlbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,741 @@
+// Host side of the solver library: the C ABI of include/fdlbm.h.
+//
+// fdlbm_create validates the problem, converts units (Sec. 4.1: lattice temperature
+// T / (3 T0), molar masses relative to the lightest species, c_j = 1/sqrt(M_j)),
+// classifies nodes, precomputes the streaming stencil of every pull (Sec. 4.2 and the
+// near-wall readings), builds the solid-node list (interface wall nodes first) and
+// initialises the device state. Kernels live in fdlbm_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "fdlbm_internal.h"
+
+using namespace fdlbm;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+fdlbm_status fail(fdlbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+constexpr double R_GAS = 8.314462618;
+constexpr int HEX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int HEY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct fdlbm_handle {
+  DevParams P{};
+  DevState S{};
+  int cur = 0;                // buffer holding g*(t)
+  int64_t steps = 0;
+  int64_t steps_at_residual = 0;
+  bool have_snap = false;
+  bool mom_fresh = true;      // S.mom holds the moments of the current time
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, size_t, void*) = nullptr;
+  void* uctx = nullptr;
+  std::vector<Alloc> allocs;
+  size_t bytes = 0;
+  float* out_buf = nullptr;   // staging for host copies of outputs
+  // host-side description kept for re-initialisation and outputs
+  int nx = 0, ny = 0, ns = 0;
+  std::vector<uint32_t> code;
+  std::vector<double> X_init, X_inlet, inlet_u;
+  double T0 = 0, T_init_lat = 0, T_inlet_lat = 0, Ts_init_lat = 0;
+  double heat0 = 0;           // -dH / (3 R T0) of reaction 0
+  int eps_species = -1, eps_nu = 0;
+  double E0 = 0, H0 = 0, mass0[MAX_NS] = {}, moles0[MAX_NS] = {};
+  int64_t counts[5] = {};
+  int64_t stencil_counts[6] = {};
+  // optional kernel timing: three events per step (before solid, between, after gas)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+fdlbm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FDLBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                           \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+fdlbm_status dalloc(fdlbm_handle* h, size_t bytes, void** out) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->ualloc) {
+    p = h->ualloc(bytes, h->uctx);
+    if (!p) return fail(FDLBM_ENOMEM, "caller allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(FDLBM_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back({p, bytes});
+  h->bytes += bytes;
+  *out = p;
+  return FDLBM_OK;
+}
+
+void release(fdlbm_handle* h) {
+  for (auto& a : h->allocs) {
+    if (h->ufree) h->ufree(a.p, a.bytes, h->uctx);
+    else cudaFree(a.p);
+  }
+  h->allocs.clear();
+}
+
+// --- geometry -----------------------------------------------------------------------
+
+struct Geo {
+  int nx, ny;
+  bool px, py;
+  std::vector<uint32_t> cls;
+  int at(int x, int y) const {
+    if (x < 0 || x >= nx) {
+      if (!px) return -1;
+      x = ((x % nx) + nx) % nx;
+    }
+    if (y < 0 || y >= ny) {
+      if (!py) return -1;
+      y = ((y % ny) + ny) % ny;
+    }
+    return x + nx * y;
+  }
+  uint32_t cls_at(int x, int y) const {
+    int k = at(x, y);
+    return k < 0 ? uint32_t(OUTSIDE) : cls[k];
+  }
+  // Node (x, y) holds a population moving along i: gas, inlet and outlet nodes emit all
+  // directions, an interface wall node only towards a gas neighbour.
+  bool emits(int x, int y, int i) const {
+    uint32_t c = cls_at(x, y);
+    if (c == GAS || c == INLET || c == OUTLET) return true;
+    return c == WALL && cls_at(x + HEX[i], y + HEY[i]) == GAS;
+  }
+  uint32_t stencil(int x, int y, int i) const {
+    const int ex = HEX[i], ey = HEY[i];
+    const bool up2 = emits(x - 2 * ex, y - 2 * ey, i);
+    const bool self = emits(x, y, i);
+    const bool down = emits(x + ex, y + ey, i);
+    const bool up3 = emits(x - 3 * ex, y - 3 * ey, i);
+    if (up2 && self) return ST_CENTRAL;
+    if (self && down) return ST_FORWARD;
+    if (up2 && up3) return ST_BACKWARD;
+    if (self) return ST_LIN_S0;
+    if (up2) return ST_LIN_S2;
+    return ST_NONE;
+  }
+};
+
+fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f);
+
+}  // namespace
+
+extern "C" {
+
+const char* fdlbm_last_error(void) { return g_err.c_str(); }
+
+fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* species, int n_species,
+                          const fdlbm_transport* tr, const fdlbm_kinetics* kin, const fdlbm_fields* init,
+                          const fdlbm_options* opts, fdlbm_handle** out) {
+  if (!out) return fail(FDLBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!geom || !species || !tr || !kin || !geom->mask)
+    return fail(FDLBM_EINVAL, "geometry, species, transport, kinetics and mask are required");
+  if (geom->lattice != FDLBM_D2Q9) return fail(FDLBM_EINVAL, "only the D2Q9 lattice is supported");
+  if (geom->nx < 4 || geom->ny < 4) return fail(FDLBM_EINVAL, "lattice must be at least 4x4 (got %dx%d)", geom->nx, geom->ny);
+  if ((long long)geom->nx * geom->ny > (1LL << 30)) return fail(FDLBM_EINVAL, "lattice too large");
+  if (n_species < 1 || n_species > MAX_NS) return fail(FDLBM_EINVAL, "n_species must be 1..%d", MAX_NS);
+  if (kin->n_react < 0 || kin->n_react > MAX_NR) return fail(FDLBM_EINVAL, "n_react must be 0..%d", MAX_NR);
+  const int* fb = geom->face_bc;
+  for (int f = 0; f < 4; ++f)
+    if (fb[f] < 0 || fb[f] > 4) return fail(FDLBM_EINVAL, "face_bc[%d] invalid", f);
+  if ((fb[0] == FDLBM_FACE_PERIODIC) != (fb[1] == FDLBM_FACE_PERIODIC) ||
+      (fb[2] == FDLBM_FACE_PERIODIC) != (fb[3] == FDLBM_FACE_PERIODIC))
+    return fail(FDLBM_EINVAL, "periodic faces must come in pairs");
+  if (fb[1] == FDLBM_FACE_INLET || fb[0] == FDLBM_FACE_OUTLET || fb[2] == FDLBM_FACE_INLET ||
+      fb[3] == FDLBM_FACE_INLET || fb[2] == FDLBM_FACE_OUTLET || fb[3] == FDLBM_FACE_OUTLET)
+    return fail(FDLBM_EINVAL, "inlet only on x-, outlet only on x+");
+  if (!(tr->T0_K > 0) || !(tr->T_inlet_K > 0) || !(tr->T_init_K > 0) || !(tr->T_solid_init_K > 0))
+    return fail(FDLBM_EINVAL, "temperatures must be positive");
+  if (!(tr->Pr > 0)) return fail(FDLBM_EINVAL, "Pr must be positive");
+  if (tr->alpha_s < 0 || tr->alpha_s > 0.25 || !(tr->rhocp_s > 0))
+    return fail(FDLBM_EINVAL, "alpha_s must be in [0, 1/4] (explicit FD stability in 2D) and rhocp_s > 0");
+  if (tr->coupling != FDLBM_COUPLING_CONSERVATIVE && tr->coupling != FDLBM_COUPLING_PAPER)
+    return fail(FDLBM_EINVAL, "unknown coupling");
+  if (kin->rho_w_maxit < 1 || !(kin->rho_w_tol > 0)) return fail(FDLBM_EINVAL, "rho_w_tol > 0 and rho_w_maxit >= 1 required");
+  const int storage = opts ? opts->storage : FDLBM_STORAGE_FP32;
+  if (storage != FDLBM_STORAGE_FP32) return fail(FDLBM_EINVAL, "unsupported storage %d", storage);
+
+  double Mmin = 1e300;
+  for (int j = 0; j < n_species; ++j) {
+    if (!(species[j].M_gmol > 0) || !(species[j].tau1 > 0) || !(species[j].tau2 > 0))
+      return fail(FDLBM_EINVAL, "species %d: M, tau1, tau2 must be positive", j);
+    Mmin = std::min(Mmin, species[j].M_gmol);
+  }
+  for (int r = 0; r < kin->n_react; ++r) {
+    if (kin->rate_form[r] != FDLBM_RATE_CONC_BILINEAR && kin->rate_form[r] != FDLBM_RATE_XFRAC_REVERSIBLE)
+      return fail(FDLBM_EINVAL, "reaction %d: unknown rate form", r);
+    if (kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE && !(kin->Keq[r] > 0))
+      return fail(FDLBM_EINVAL, "reaction %d: Keq must be positive", r);
+    for (int j = 0; j < n_species; ++j)
+      if (kin->nu[r][j] < -4 || kin->nu[r][j] > 4) return fail(FDLBM_EINVAL, "reaction %d: |nu| <= 4", r);
+  }
+
+  fdlbm_handle* h = new fdlbm_handle();
+  h->device = opts ? opts->device : 0;
+  DeviceGuard guard(h->device);
+  h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+  if (opts) {
+    h->ualloc = opts->alloc;
+    h->ufree = opts->free;
+    h->uctx = opts->alloc_ctx;
+  }
+  const int nx = geom->nx, ny = geom->ny, n = nx * ny, ns = n_species;
+  h->nx = nx;
+  h->ny = ny;
+  h->ns = ns;
+
+  // Node classes.
+  Geo G;
+  G.nx = nx;
+  G.ny = ny;
+  G.px = fb[0] == FDLBM_FACE_PERIODIC;
+  G.py = fb[2] == FDLBM_FACE_PERIODIC;
+  G.cls.assign(n, GAS);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int k = x + nx * y;
+      const uint8_t m = geom->mask[k];
+      if (m > 2) {
+        delete h;
+        return fail(FDLBM_EINVAL, "mask value %d at (%d,%d)", m, x, y);
+      }
+      if (m == FDLBM_MASK_GAS) {
+        if (x == 0 && fb[0] == FDLBM_FACE_INLET) G.cls[k] = INLET;
+        else if (x == nx - 1 && fb[1] == FDLBM_FACE_OUTLET) G.cls[k] = OUTLET;
+        else G.cls[k] = GAS;
+      } else {
+        G.cls[k] = SOLID;
+      }
+    }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int k = x + nx * y;
+      if (G.cls[k] != SOLID) continue;
+      for (int i = 1; i < Q; ++i)
+        if (G.cls_at(x + HEX[i], y + HEY[i]) == GAS) G.cls[k] = WALL;
+    }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int k = x + nx * y;
+      if (G.cls[k] == GAS) {
+        for (int i = 1; i < Q; ++i)
+          if (G.at(x + HEX[i], y + HEY[i]) < 0) {
+            delete h;
+            return fail(FDLBM_EGEOM, "gas node (%d,%d) touches a closed lattice face", x, y);
+          }
+      } else if (G.cls[k] == OUTLET && G.cls[k - 1] != GAS) {
+        delete h;
+        return fail(FDLBM_EGEOM, "outlet node (%d,%d) has no upstream gas node", x, y);
+      }
+    }
+  // Code words: class, catalytic bit, per-direction stencils (gas: every direction;
+  // wall: arrival directions, others marked NOT_ARRIVAL).
+  h->code.assign(n, 0);
+  std::vector<int32_t> walls, solids;
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      const int k = x + nx * y;
+      const uint32_t c = G.cls[k];
+      uint32_t w = c;
+      if (geom->mask[k] == FDLBM_MASK_CATALYTIC) w |= CATALYTIC_BIT;
+      if (c == GAS) {
+        for (int i = 1; i < Q; ++i) {
+          const uint32_t st = G.stencil(x, y, i);
+          w |= st << (STENCIL_SHIFT + 3 * (i - 1));
+          h->stencil_counts[st]++;
+        }
+      } else if (c == WALL) {
+        for (int i = 1; i < Q; ++i) {
+          uint32_t st = ST_NOT_ARRIVAL;
+          if (G.cls_at(x - HEX[i], y - HEY[i]) == GAS) {
+            st = G.stencil(x, y, i);
+            h->stencil_counts[st]++;
+          }
+          w |= st << (STENCIL_SHIFT + 3 * (i - 1));
+        }
+        walls.push_back(k);
+      } else if (c == SOLID) {
+        solids.push_back(k);
+      }
+      h->code[k] = w;
+      h->counts[c]++;
+    }
+  std::vector<int32_t> solid_list(walls);
+  solid_list.insert(solid_list.end(), solids.begin(), solids.end());
+
+  // Parameters (Sec. 4.1 units).
+  DevParams& P = h->P;
+  P.nx = nx;
+  P.ny = ny;
+  P.n = n;
+  P.plane = ((long long)n + 63) / 64 * 64;
+  P.ns = ns;
+  P.periodic_x = G.px;
+  P.periodic_y = G.py;
+  P.n_solid_list = (int)solid_list.size();
+  P.n_wall_list = (int)walls.size();
+  P.energy_correction = tr->energy_correction ? 1 : 0;
+  P.coupling = tr->coupling;
+  for (int f = 0; f < 4; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
+  h->T0 = tr->T0_K;
+  const double tl = 1.0 / (3.0 * tr->T0_K);
+  const double Tref = tr->T_inlet_K * tl;
+  h->T_inlet_lat = Tref;
+  h->T_init_lat = tr->T_init_K * tl;
+  h->Ts_init_lat = tr->T_solid_init_K * tl;
+  P.Tref = (float)Tref;
+  P.p_out = (float)Tref;  // C_in T_in with C_in = 1
+  P.u_inlet = (float)tr->u_inlet;
+  P.Tin_lat = (float)Tref;
+  h->X_init.resize(ns);
+  h->X_inlet.resize(ns);
+  for (int j = 0; j < ns; ++j) {
+    const double M = species[j].M_gmol / Mmin;
+    const double c = 1.0 / std::sqrt(M);
+    const double t1 = species[j].tau1, t2 = species[j].tau2;
+    P.M[j] = (float)M;
+    P.invM[j] = (float)(1.0 / M);
+    P.sqrtM[j] = (float)std::sqrt(M);
+    P.c[j] = (float)c;
+    P.c2[j] = (float)(1.0 / M);
+    P.a[j] = (float)(1.0 - c);
+    P.onlattice[j] = (M == 1.0);
+    P.rref[j] = (float)(species[j].X_inlet * M);
+    P.Xin[j] = (float)species[j].X_inlet;
+    P.omega[j] = (float)(2.0 / (1.0 + 2.0 * t1));
+    P.t1t2[j] = (float)(t1 / t2);
+    P.wt1[j] = (float)(2.0 * t1 / (1.0 + 2.0 * t1));
+    P.a2[j] = (float)(1.0 / (2.0 * t2));
+    P.inv1a2[j] = (float)(1.0 / (1.0 + 1.0 / (2.0 * t2)));
+    P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
+    P.invtau2[j] = (float)(1.0 / t2);
+    // Energy-correction flux K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T, c_pj = 2 / M_j (2D).
+    P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.0 / M) / tr->Pr - 1.0 / M) * t1) : 0.f;
+    h->X_init[j] = species[j].X_init;
+    h->X_inlet[j] = species[j].X_inlet;
+  }
+  for (int i = 0; i < Q; ++i) {
+    const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
+    const double wy = HEY[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
+    P.W0[i] = (float)(wx * wy);
+  }
+  P.alpha_s = (float)tr->alpha_s;
+  P.rhocp_s = (float)tr->rhocp_s;
+  P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
+  P.kappa_f = (float)tr->kappa_f;
+  P.dTout = (float)(tr->T_outer_K * tl - Tref);
+  P.nr = kin->n_react;
+  for (int r = 0; r < kin->n_react; ++r) {
+    for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
+    P.rate_form[r] = kin->rate_form[r];
+    P.k0[r] = (float)kin->k0[r];
+    P.EaR[r] = (float)(kin->Ea_Jmol[r] / R_GAS);
+    P.inv_Keq[r] = kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE ? (float)(1.0 / kin->Keq[r]) : 0.f;
+    P.heat[r] = (float)(-kin->dH_Jmol[r] / (3.0 * R_GAS * tr->T0_K));
+  }
+  P.T3T0 = (float)(3.0 * tr->T0_K);
+  P.rho_w_tol = (float)kin->rho_w_tol;
+  P.rho_w_maxit = kin->rho_w_maxit;
+  if (kin->n_react > 0) {
+    h->heat0 = -kin->dH_Jmol[0] / (3.0 * R_GAS * tr->T0_K);
+    for (int j = 0; j < ns && h->eps_species < 0; ++j)
+      if (kin->nu[0][j] < 0) {
+        h->eps_species = j;
+        h->eps_nu = kin->nu[0][j];
+      }
+  }
+  // Inlet velocity per row: plug, or a parabola vanishing on the bounding wall nodes of
+  // each contiguous inlet run.
+  h->inlet_u.assign(ny, 0.0);
+  for (int y = 0; y < ny; ++y) {
+    if (G.cls[0 + nx * y] != INLET) continue;
+    if (tr->inlet_profile == FDLBM_PROFILE_PLUG) {
+      h->inlet_u[y] = tr->u_inlet;
+      continue;
+    }
+    int y0 = y, y1 = y;
+    while (y0 - 1 >= 0 && G.cls[nx * (y0 - 1)] == INLET) --y0;
+    while (y1 + 1 < ny && G.cls[nx * (y1 + 1)] == INLET) ++y1;
+    const double H = double(y1 - y0 + 2), s = double(y - y0 + 1) / H;
+    h->inlet_u[y] = 4.0 * tr->u_inlet * s * (1.0 - s);
+  }
+
+  // Device state.
+  fdlbm_status st;
+  DevState& S = h->S;
+  const size_t pop_bytes = sizeof(float) * (size_t)ns * Q * (size_t)P.plane;
+  void* p;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(h, pop_bytes, &p)) != FDLBM_OK) { release(h); delete h; return st; }
+    S.h[b] = (float*)p;
+    if ((st = dalloc(h, sizeof(float) * n, &p)) != FDLBM_OK) { release(h); delete h; return st; }
+    S.Ts[b] = (float*)p;
+  }
+#define ALLOC(field, type, count)                                                    \
+  if ((st = dalloc(h, sizeof(type) * (size_t)(count), &p)) != FDLBM_OK) {             \
+    release(h);                                                                      \
+    delete h;                                                                        \
+    return st;                                                                       \
+  }                                                                                  \
+  field = (type*)p;
+  ALLOC(S.code, uint32_t, n);
+  ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
+  ALLOC(S.mom, float, (size_t)(ns + 3) * n);
+  ALLOC(S.Tgas, float, n);
+  ALLOC(S.snap, float, (size_t)(ns + 4) * n);
+  ALLOC(S.ledger, double, LG_COUNT);
+  ALLOC(S.flags, int, 4);
+  ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + 8);
+  ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
+#undef ALLOC
+  cudaError_t e = cudaMemcpyAsync(S.code, h->code.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !solid_list.empty())
+    e = cudaMemcpyAsync(S.solid_list, solid_list.data(), sizeof(int32_t) * solid_list.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    delete h;
+    return cuda_fail(e, "upload geometry");
+  }
+  if ((st = upload_and_init(h, init)) != FDLBM_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n) {
+  if (!h || n < 0) return fail(FDLBM_EINVAL, "bad handle or step count");
+  DeviceGuard guard(h->device);
+  for (int64_t k = 0; k < n; ++k) {
+    if (h->profiling && h->events_used + 3 <= h->events.size()) {
+      cudaEvent_t* ev = h->events.data() + h->events_used;
+      CK(cudaEventRecord(ev[0], h->stream), "event record");
+      CK(launch_solid(h->P, h->S, h->cur, h->stream), "solid launch");
+      CK(cudaEventRecord(ev[1], h->stream), "event record");
+      CK(launch_gas(h->P, h->S, h->cur, h->stream), "gas launch");
+      CK(cudaEventRecord(ev[2], h->stream), "event record");
+      h->events_used += 3;
+    } else {
+      CK(launch_step(h->P, h->S, h->cur, false, h->stream), "step launch");
+    }
+    h->cur ^= 1;
+  }
+  if (n > 0) h->mom_fresh = false;
+  h->steps += n;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_sync(fdlbm_handle* h) {
+  if (!h) return fail(FDLBM_EINVAL, "bad handle");
+  DeviceGuard guard(h->device);
+  int flags = 0;
+  CK(cudaMemcpyAsync(&flags, h->S.flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  if (flags) return fail(FDLBM_EUNSTABLE, "non-finite or non-positive density/temperature seen in the gas");
+  return FDLBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+fdlbm_status ensure_moments(fdlbm_handle* h) {
+  if (h->mom_fresh) return FDLBM_OK;
+  // The buffer read by the last step still holds its input: recompute that step's
+  // pre-collision moments (time t) from it.
+  CK(launch_step(h->P, h->S, h->cur ^ 1, true, h->stream), "moments launch");
+  h->mom_fresh = true;
+  return FDLBM_OK;
+}
+
+fdlbm_status read_totals(fdlbm_handle* h, double* tot) {
+  fdlbm_status st = ensure_moments(h);
+  if (st != FDLBM_OK) return st;
+  CK(launch_totals(h->P, h->S, h->cur, h->stream), "totals launch");
+  CK(cudaMemcpyAsync(tot, h->S.red, sizeof(double) * totals_count(h->ns), cudaMemcpyDeviceToHost, h->stream),
+     "read totals");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  return FDLBM_OK;
+}
+
+fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
+  const int n = h->nx * h->ny, ns = h->ns;
+  const double tl = 1.0 / (3.0 * h->T0);
+  std::vector<double> X((size_t)ns * n), u(2 * (size_t)n, 0.0), T(n), Ts(n), C(n, 1.0);
+  for (int j = 0; j < ns; ++j)
+    for (int k = 0; k < n; ++k) X[(size_t)j * n + k] = (f && f->X) ? f->X[(size_t)j * n + k] : h->X_init[j];
+  if (f && f->u) std::memcpy(u.data(), f->u, sizeof(double) * 2 * n);
+  for (int k = 0; k < n; ++k) {
+    T[k] = (f && f->T_K) ? f->T_K[k] * tl : h->T_init_lat;
+    Ts[k] = (f && f->Ts_K) ? f->Ts_K[k] * tl : h->Ts_init_lat;
+    if (f && f->C) C[k] = f->C[k];
+    if (!(T[k] > 0) || !(C[k] > 0)) return fail(FDLBM_EINVAL, "initial T and C must be positive (node %d)", k);
+  }
+  std::vector<double> inlet(h->inlet_u);
+  inlet.insert(inlet.end(), h->X_inlet.begin(), h->X_inlet.end());
+  inlet.push_back(h->T_inlet_lat);
+  // Temporary device copies of the FP64 fields.
+  const size_t total = X.size() + u.size() + T.size() + Ts.size() + C.size() + inlet.size();
+  double* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(double) * total), "init staging alloc");
+  size_t off = 0;
+  double* dX = d + off; off += X.size();
+  double* du = d + off; off += u.size();
+  double* dT = d + off; off += T.size();
+  double* dTs = d + off; off += Ts.size();
+  double* dC = d + off; off += C.size();
+  double* dIn = d + off;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](double* dst, const std::vector<double>& v) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  };
+  up(dX, X);
+  up(du, u);
+  up(dT, T);
+  up(dTs, Ts);
+  up(dC, C);
+  up(dIn, inlet);
+  if (e == cudaSuccess) e = launch_init(h->P, h->S, dX, du, dT, dTs, dC, dIn, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->S.ledger, 0, sizeof(double) * LG_COUNT, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->S.flags, 0, sizeof(int) * 4, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "initialise state");
+  h->cur = 0;
+  h->steps = 0;
+  h->steps_at_residual = 0;
+  h->have_snap = false;
+  h->mom_fresh = true;
+  std::vector<double> tot(totals_count(ns));
+  fdlbm_status st = read_totals(h, tot.data());
+  if (st != FDLBM_OK) return st;
+  h->E0 = tot[0];
+  h->H0 = tot[1];
+  for (int j = 0; j < ns; ++j) {
+    h->mass0[j] = tot[2 + j];
+    h->moles0[j] = tot[2 + ns + j];
+  }
+  return FDLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fdlbm_status fdlbm_set_fields(fdlbm_handle* h, const fdlbm_fields* f) {
+  if (!h) return fail(FDLBM_EINVAL, "bad handle");
+  DeviceGuard guard(h->device);
+  return upload_and_init(h, f);
+}
+
+fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device) {
+  if (!h || !dst) return fail(FDLBM_EINVAL, "bad handle or destination");
+  DeviceGuard guard(h->device);
+  fdlbm_status st = ensure_moments(h);
+  if (st != FDLBM_OK) return st;
+  const size_t count = (size_t)(2 * h->ns + 4) * h->nx * h->ny;
+  if (dst_on_device) {
+    CK(launch_moments_out(h->P, h->S, h->cur, dst, h->stream), "moments output");
+    return FDLBM_OK;
+  }
+  CK(launch_moments_out(h->P, h->S, h->cur, h->out_buf, h->stream), "moments output");
+  CK(cudaMemcpyAsync(dst, h->out_buf, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream), "copy moments");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_populations(fdlbm_handle* h, float* dst, int dst_on_device) {
+  if (!h || !dst) return fail(FDLBM_EINVAL, "bad handle or destination");
+  DeviceGuard guard(h->device);
+  const size_t count = (size_t)h->ns * Q * h->nx * h->ny;
+  if (dst_on_device) {
+    CK(launch_populations_out(h->P, h->S, h->cur, dst, h->stream), "populations output");
+    return FDLBM_OK;
+  }
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(float) * count), "staging alloc");
+  cudaError_t e = launch_populations_out(h->P, h->S, h->cur, tmp, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "populations output");
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out) {
+  if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
+  DeviceGuard guard(h->device);
+  const int ns = h->ns;
+  std::vector<double> tot(totals_count(ns));
+  fdlbm_status st = read_totals(h, tot.data());
+  if (st != FDLBM_OK) return st;
+  double lg[LG_COUNT];
+  CK(cudaMemcpy(lg, h->S.ledger, sizeof(lg), cudaMemcpyDeviceToHost), "read ledger");
+  std::memset(out, 0, sizeof(*out));
+  out->steps = h->steps;
+  out->E_gas = tot[0];
+  out->E_gas0 = h->E0;
+  out->H_solid = tot[1];
+  out->H_solid0 = h->H0;
+  out->Q_reaction = lg[LG_QRXN];
+  out->Q_wall = lg[LG_QWALL];
+  out->Q_couple = lg[LG_QCOUPLE];
+  out->Q_fixedT = lg[LG_QFIXEDT];
+  out->noconv = lg[LG_NOCONV];
+  out->residual = (tot[0] - h->E0) + (tot[1] - h->H0) - lg[LG_QRXN] - lg[LG_QFIXEDT];
+  out->solid_residual = (tot[1] - h->H0) - (lg[LG_QRXN] + lg[LG_QCOUPLE] + lg[LG_QFIXEDT]);
+  for (int j = 0; j < ns; ++j) {
+    out->mass[j] = tot[2 + j];
+    out->mass0[j] = h->mass0[j];
+    out->moles[j] = tot[2 + ns + j];
+    out->moles0[j] = h->moles0[j];
+  }
+  out->eps_paper = 0.0;
+  if (h->eps_species >= 0) {
+    const int jr = h->eps_species;
+    const double Qco = h->heat0 * (tot[2 + ns + jr] - h->moles0[jr]) / h->eps_nu;
+    if (Qco != 0.0) out->eps_paper = ((tot[0] - h->E0) + (tot[1] - h->H0) - Qco) / Qco;
+  }
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out) {
+  if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
+  DeviceGuard guard(h->device);
+  fdlbm_status st = ensure_moments(h);
+  if (st != FDLBM_OK) return st;
+  const int ns = h->ns, nf = ns + 4;
+  CK(launch_residual(h->P, h->S, h->cur, h->stream), "residual launch");
+  std::vector<double> sums(residual_count(ns));
+  CK(cudaMemcpyAsync(sums.data(), h->S.red + totals_count(ns), sizeof(double) * sums.size(),
+                     cudaMemcpyDeviceToHost, h->stream),
+     "read residual");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  double r = std::numeric_limits<double>::infinity();
+  if (h->have_snap) {
+    const double K = double(std::max<int64_t>(h->steps - h->steps_at_residual, 1));
+    r = 0.0;
+    for (int f = 0; f < nf; ++f) {
+      const double dn = std::sqrt(sums[2 * f]), fn = std::sqrt(sums[2 * f + 1]);
+      r = std::max(r, dn / (K * std::max(fn, 1e-30)));
+    }
+  }
+  h->have_snap = true;
+  h->steps_at_residual = h->steps;
+  *out = r;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_info(const fdlbm_handle* h, fdlbm_info_t* out) {
+  if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
+  std::memset(out, 0, sizeof(*out));
+  out->n_nodes = (int64_t)h->nx * h->ny;
+  out->n_gas = h->counts[GAS];
+  out->n_inlet = h->counts[INLET];
+  out->n_outlet = h->counts[OUTLET];
+  out->n_wall = h->counts[WALL];
+  out->n_solid = h->counts[SOLID];
+  for (int c = 0; c < 6; ++c) out->stencil_counts[c] = h->stencil_counts[c];
+  out->ns = h->ns;
+  out->T_ref_lat = h->T_inlet_lat;
+  out->steps = h->steps;
+  out->device_bytes = h->bytes;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_profile(fdlbm_handle* h, int enable) {
+  if (!h) return fail(FDLBM_EINVAL, "bad handle");
+  DeviceGuard guard(h->device);
+  if (enable && h->events.empty()) {
+    h->events.resize(3 * 65536);
+    for (auto& e : h->events) CK(cudaEventCreate(&e), "event create");
+  }
+  h->profiling = enable != 0;
+  h->events_used = 0;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_kernel_times(fdlbm_handle* h, double* ms_out2, int64_t* steps_out) {
+  if (!h || !ms_out2) return fail(FDLBM_EINVAL, "bad handle or output");
+  DeviceGuard guard(h->device);
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  double solid = 0.0, gas = 0.0;
+  for (size_t k = 0; k + 3 <= h->events_used; k += 3) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, h->events[k], h->events[k + 1]), "event time");
+    CK(cudaEventElapsedTime(&b, h->events[k + 1], h->events[k + 2]), "event time");
+    solid += a;
+    gas += b;
+  }
+  ms_out2[0] = solid;
+  ms_out2[1] = gas;
+  if (steps_out) *steps_out = (int64_t)(h->events_used / 3);
+  h->events_used = 0;
+  return FDLBM_OK;
+}
+
+void fdlbm_destroy(fdlbm_handle* h) {
+  if (!h) return;
+  {
+    DeviceGuard guard(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto& e : h->events) cudaEventDestroy(e);
+    release(h);
+  }
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations shared by the host side (fdlbm_api.cu) and the kernels
+// (fdlbm_kernels.cu) of the solver library. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fdlbm.h"
+
+namespace fdlbm {
+
+constexpr int Q = 9;
+constexpr int MAX_NS = FDLBM_MAX_SPECIES;
+constexpr int MAX_NR = FDLBM_MAX_REACTIONS;
+
+// Node classes (bits 0..2 of the node code word).
+enum NodeClass : uint32_t { GAS = 0, INLET = 1, OUTLET = 2, WALL = 3, SOLID = 4, OUTSIDE = 7 };
+// Streaming stencils, 3 bits per direction i = 1..8 at bit 4 + 3 (i - 1).
+enum Stencil : uint32_t { ST_NONE = 0, ST_CENTRAL = 1, ST_FORWARD = 2, ST_BACKWARD = 3,
+                          ST_LIN_S0 = 4, ST_LIN_S2 = 5, ST_NOT_ARRIVAL = 7 };
+constexpr uint32_t CATALYTIC_BIT = 1u << 3;
+constexpr int STENCIL_SHIFT = 4;
+
+__host__ __device__ inline uint32_t node_class(uint32_t code) { return code & 7u; }
+__host__ __device__ inline uint32_t stencil_of(uint32_t code, int i) {
+  return (code >> (STENCIL_SHIFT + 3 * (i - 1))) & 7u;
+}
+
+// Scalars every kernel needs, passed by value (kernel parameter space).
+struct DevParams {
+  int nx, ny, n;        // lattice, node count
+  long long plane;      // elements between population planes (j, i)
+  int ns;
+  int periodic_x, periodic_y;
+  int n_solid_list, n_wall_list;  // solid list: wall nodes first
+  int energy_correction, coupling;
+  int fixedT_face[4];   // x-, x+, y-, y+
+  // species
+  float M[MAX_NS], invM[MAX_NS], sqrtM[MAX_NS], c[MAX_NS], c2[MAX_NS];
+  float a[MAX_NS];      // 1 - c_j
+  int onlattice[MAX_NS];
+  float rref[MAX_NS];   // reference density X_inlet,j M_j of the stored deviations
+  float omega[MAX_NS], t1t2[MAX_NS], wt1[MAX_NS], a2[MAX_NS], inv1a2[MAX_NS];
+  float uc_w[MAX_NS], invtau2[MAX_NS];
+  float kcoef[MAX_NS];  // energy-correction flux coefficient K_j / (C_j T)
+  float W0[Q];          // rest-equilibrium weights at T_ref
+  float Tref, p_out;    // lattice reference temperature, outlet pressure
+  float u_inlet;
+  // solid and coupling
+  float alpha_s, rhocp_s, inv_rhocp_s, kappa_f, dTout;
+  // reactions
+  int nr;
+  int nu[MAX_NR][MAX_NS];
+  int rate_form[MAX_NR];
+  float k0[MAX_NR], EaR[MAX_NR], inv_Keq[MAX_NR], heat[MAX_NR];  // heat = -dH / (3 R T0)
+  float T3T0;           // kelvin per lattice temperature unit
+  float rho_w_tol;
+  int rho_w_maxit;
+  // steady-state residual references
+  float Xin[MAX_NS];
+  float Tin_lat;
+};
+
+// Device state of one handle.
+struct DevState {
+  float* h[2];          // populations (deviations from rref W0), [ns][Q][plane]
+  float* Ts[2];         // solid temperature deviation from Tref, [n]
+  uint32_t* code;       // node code words, [n]
+  int32_t* solid_list;  // wall nodes first, then interior solid nodes
+  float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
+  float* Tgas;          // gas temperature of the current time (lattice), [n]
+  float* snap;          // residual snapshot [(ns + 4)][n]
+  double* ledger;       // device accumulators, see LEDGER_*
+  int* flags;           // sticky error flags
+  double* red;          // reduction scratch (doubles)
+};
+
+enum Ledger { LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV, LG_COUNT };
+
+// Launchers (fdlbm_kernels.cu).
+// Initial state from device FP64 fields: X [ns][n], u [2][n], T_lat [n], Ts_lat [n], C [n];
+// inlet holds the ny inlet velocities, then the ns inlet mole fractions, then the inlet
+// lattice temperature.
+cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, const double* u,
+                        const double* T_lat, const double* Ts_lat, const double* C,
+                        const double* inlet, cudaStream_t st);
+// One time step reading buffer src and writing 1 - src; with moments_only the gas kernel
+// recomputes the pre-collision moments of the step that read src into S.mom instead.
+cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only,
+                        cudaStream_t st);
+// The two kernels of a step, separately (for per-kernel timing).
+cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st);
+cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st);
+cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst,
+                               cudaStream_t st);
+cudaError_t launch_populations_out(const DevParams& P, const DevState& S, int cur, float* dst,
+                                   cudaStream_t st);
+cudaError_t launch_totals(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
+cudaError_t launch_residual(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
+
+// Number of doubles written by launch_totals into S.red: E_gas, H_solid, mass[ns], moles[ns].
+inline int totals_count(int ns) { return 2 + 2 * ns; }
+// Number of doubles written by launch_residual into S.red (after the totals):
+// per field: ||F - snap||^2 and ||F - ref||^2 for fields ux, uy, X_j, T, Ts.
+inline int residual_count(int ns) { return 2 * (ns + 4); }
+
+}  // namespace fdlbm

@@ -1,0 +1,300 @@
+"""Python binding of the C-ABI solver library ``libfdlbm.so`` (include/fdlbm.h).
+
+Argument marshalling only: every step of the scheme runs in the library's CUDA kernels.
+PyTorch provides the device memory (its caching allocator is handed to the library as
+the allocation callback) and the stream. There is no CPU fallback: constructing a
+:class:`Solver` without a CUDA device, or without the built library, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_NS = 6
+MAX_NR = 4
+Q = 9
+STATUS = {0: "FDLBM_OK", -1: "FDLBM_EINVAL", -2: "FDLBM_EGEOM", -3: "FDLBM_ECUDA",
+          -4: "FDLBM_EUNSTABLE", -5: "FDLBM_ENOCONV", -6: "FDLBM_ETIMEOUT", -7: "FDLBM_ENOMEM"}
+
+
+class FdlbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Geometry(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lattice", C.c_int),
+                ("mask", C.POINTER(C.c_uint8)), ("face_bc", C.c_int * 4)]
+
+
+class Species(C.Structure):
+    _fields_ = [("M_gmol", C.c_double), ("tau1", C.c_double), ("tau2", C.c_double),
+                ("X_init", C.c_double), ("X_inlet", C.c_double)]
+
+
+class Transport(C.Structure):
+    _fields_ = [("Pr", C.c_double), ("energy_correction", C.c_int),
+                ("T0_K", C.c_double), ("T_init_K", C.c_double), ("T_inlet_K", C.c_double),
+                ("T_solid_init_K", C.c_double), ("T_outer_K", C.c_double),
+                ("u_inlet", C.c_double), ("inlet_profile", C.c_int),
+                ("alpha_s", C.c_double), ("rhocp_s", C.c_double), ("kappa_f", C.c_double),
+                ("coupling", C.c_int)]
+
+
+class Kinetics(C.Structure):
+    _fields_ = [("n_react", C.c_int), ("nu", (C.c_int * MAX_NS) * MAX_NR),
+                ("k0", C.c_double * MAX_NR), ("Ea_Jmol", C.c_double * MAX_NR),
+                ("Keq", C.c_double * MAX_NR), ("dH_Jmol", C.c_double * MAX_NR),
+                ("rate_form", C.c_int * MAX_NR), ("rho_w_tol", C.c_double),
+                ("rho_w_maxit", C.c_int)]
+
+
+class Fields(C.Structure):
+    _fields_ = [("X", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)),
+                ("T_K", C.POINTER(C.c_double)), ("Ts_K", C.POINTER(C.c_double)),
+                ("C", C.POINTER(C.c_double))]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("storage", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_gas", C.c_int64), ("n_inlet", C.c_int64),
+                ("n_outlet", C.c_int64), ("n_wall", C.c_int64), ("n_solid", C.c_int64),
+                ("stencil_counts", C.c_int64 * 6), ("ns", C.c_int), ("T_ref_lat", C.c_double),
+                ("steps", C.c_int64), ("device_bytes", C.c_size_t)]
+
+
+class Balance(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("E_gas", C.c_double), ("E_gas0", C.c_double),
+                ("H_solid", C.c_double), ("H_solid0", C.c_double), ("Q_reaction", C.c_double),
+                ("Q_wall", C.c_double), ("Q_couple", C.c_double), ("Q_fixedT", C.c_double),
+                ("residual", C.c_double), ("solid_residual", C.c_double),
+                ("eps_paper", C.c_double), ("noconv", C.c_double),
+                ("mass", C.c_double * MAX_NS), ("mass0", C.c_double * MAX_NS),
+                ("moles", C.c_double * MAX_NS), ("moles0", C.c_double * MAX_NS)]
+
+
+_lib = None
+EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_populations",
+           "fdlbm_enthalpy_balance", "fdlbm_residual", "fdlbm_set_fields", "fdlbm_info",
+           "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_destroy", "fdlbm_last_error")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfdlbm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"solver library not built: {path}")
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.fdlbm_create.argtypes = [P(Geometry), P(Species), C.c_int, P(Transport), P(Kinetics),
+                               P(Fields), P(Options), P(C.c_void_p)]
+    L.fdlbm_step.argtypes = [C.c_void_p, C.c_int64]
+    L.fdlbm_sync.argtypes = [C.c_void_p]
+    L.fdlbm_moments.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.fdlbm_populations.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.fdlbm_enthalpy_balance.argtypes = [C.c_void_p, P(Balance)]
+    L.fdlbm_residual.argtypes = [C.c_void_p, P(C.c_double)]
+    L.fdlbm_set_fields.argtypes = [C.c_void_p, P(Fields)]
+    L.fdlbm_info.argtypes = [C.c_void_p, P(Info)]
+    L.fdlbm_profile.argtypes = [C.c_void_p, C.c_int]
+    L.fdlbm_kernel_times.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int64)]
+    L.fdlbm_destroy.argtypes = [C.c_void_p]
+    L.fdlbm_destroy.restype = None
+    L.fdlbm_last_error.restype = C.c_char_p
+    for name in EXPORTS[:-2]:
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise FdlbmError(status, load().fdlbm_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fields(init, keep):
+    f = Fields()
+    if not init:
+        return f
+    for key, name in (("X", "X"), ("u", "u"), ("T_K", "T_K"), ("Ts_K", "Ts_K"), ("C", "C")):
+        if init.get(key) is not None:
+            a = np.ascontiguousarray(init[key], dtype=np.float64)
+            keep.append(a)
+            setattr(f, name, _dptr(a))
+    return f
+
+
+class Solver:
+    """One coupled FD-LBM problem on one GPU, built from a problem dict (see
+    ``paper_1804_07588_gb300.workloads``)."""
+
+    def __init__(self, p: dict, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
+        if p["dim"] != 2 or p["lattice"] != 9:
+            raise FdlbmError(-1, "only D2Q9 problems are supported")
+        L = load()
+        self._torch = torch
+        self.device = device
+        torch.cuda.set_device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        keep = []
+        g = Geometry()
+        g.nx, g.ny, g.lattice = p["nx"], p["ny"], 9
+        mask = np.ascontiguousarray(p["mask"], dtype=np.uint8)
+        keep.append(mask)
+        g.mask = mask.ctypes.data_as(C.POINTER(C.c_uint8))
+        for f in range(4):
+            g.face_bc[f] = p["face_bc"][f]
+        sp = p["species"]
+        ns = len(sp)
+        spec = (Species * ns)()
+        for j, d in enumerate(sp):
+            spec[j] = Species(d["M_gmol"], d["tau1"], d["tau2"], d["X_init"], d["X_inlet"])
+        tr = Transport(p["Pr"], int(p["energy_correction"]), p["T0_K"], p["T_init_K"],
+                       p["T_inlet_K"], p["T_solid_init_K"], p["T_outer_K"], p["u_inlet"],
+                       int(p["inlet_profile"]), p["alpha_s"], p["rhocp_s"], p["kappa_f"],
+                       int(p["coupling"]))
+        kin = Kinetics()
+        kin.n_react = len(p["reactions"])
+        for r, d in enumerate(p["reactions"]):
+            for j, v in enumerate(d["nu"]):
+                kin.nu[r][j] = int(v)
+            kin.k0[r], kin.Ea_Jmol[r], kin.Keq[r], kin.dH_Jmol[r] = (
+                d["k0"], d["Ea_Jmol"], d["Keq"], d["dH_Jmol"])
+            kin.rate_form[r] = int(d["rate_form"])
+        kin.rho_w_tol = p["rho_w_tol"]
+        kin.rho_w_maxit = int(p["rho_w_maxit"])
+        fields = _fields(p.get("init"), keep)
+
+        # torch's caching allocator on the solver's stream
+        self._blocks = {}
+
+        def _alloc(nbytes, ctx):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device, self.stream)
+            except Exception:
+                return None
+            self._blocks[ptr] = nbytes
+            return ptr
+
+        def _free(ptr, nbytes, ctx):
+            if ptr in self._blocks:
+                del self._blocks[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        opts = Options(0, device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb, self._free_cb, None)
+        h = C.c_void_p()
+        _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
+                              C.byref(opts), C.byref(h)))
+        self._h = h
+        self.ns = ns
+        self.nx, self.ny = p["nx"], p["ny"]
+        self.n = self.nx * self.ny
+
+    # -- life cycle ---------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().fdlbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls ----------------------------------------------------------------------
+    def step(self, n: int = 1):
+        _check(load().fdlbm_step(self._h, int(n)))
+
+    def sync(self):
+        _check(load().fdlbm_sync(self._h))
+
+    def moments(self, out=None):
+        """[2 ns + 4, n] float32: rho_j, X_j, ux, uy, T (K), T_s (K). Returns a CUDA tensor
+        (``out`` may be a preallocated CUDA tensor or a numpy float32 array)."""
+        torch = self._torch
+        nf = 2 * self.ns + 4
+        if out is None:
+            out = torch.empty((nf, self.n), dtype=torch.float32, device=f"cuda:{self.device}")
+        if isinstance(out, np.ndarray):
+            assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == nf * self.n
+            _check(load().fdlbm_moments(self._h, out.ctypes.data_as(C.c_void_p), 0))
+            return out
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == nf * self.n
+        _check(load().fdlbm_moments(self._h, C.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def moments_host(self) -> np.ndarray:
+        out = np.empty((2 * self.ns + 4, self.n), np.float32)
+        return self.moments(out)
+
+    def populations(self) -> np.ndarray:
+        out = np.empty((self.ns, Q, self.n), np.float32)
+        _check(load().fdlbm_populations(self._h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def balance(self) -> dict:
+        b = Balance()
+        _check(load().fdlbm_enthalpy_balance(self._h, C.byref(b)))
+        ns = self.ns
+        d = {k: getattr(b, k) for k, _ in Balance._fields_ if k not in ("mass", "mass0", "moles", "moles0")}
+        for k in ("mass", "mass0", "moles", "moles0"):
+            d[k] = np.array(list(getattr(b, k))[:ns])
+        return d
+
+    def residual(self) -> float:
+        r = C.c_double()
+        _check(load().fdlbm_residual(self._h, C.byref(r)))
+        return r.value
+
+    def set_fields(self, init: dict):
+        keep = []
+        f = _fields(init, keep)
+        _check(load().fdlbm_set_fields(self._h, C.byref(f)))
+
+    def profile(self, enable: bool = True):
+        _check(load().fdlbm_profile(self._h, int(bool(enable))))
+
+    def kernel_times(self):
+        """(ms solid kernel, ms gas kernel, timed steps) summed since profile()."""
+        ms = (C.c_double * 2)()
+        n = C.c_int64()
+        _check(load().fdlbm_kernel_times(self._h, ms, C.byref(n)))
+        return ms[0], ms[1], n.value
+
+    def info(self) -> dict:
+        i = Info()
+        _check(load().fdlbm_info(self._h, C.byref(i)))
+        d = {k: getattr(i, k) for k, _ in Info._fields_}
+        d["stencil_counts"] = list(i.stencil_counts)
+        return d

@@ -1,0 +1,162 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the FP64 oracle on the same
+seeded inputs, field by field, at sizes that span several 32x8 tiles with ragged tails,
+plus the full-size porous bed of the benchmark for a few steps.
+
+Tolerance: 1e-5 of max |field| on every moment field (field-normalised relative error),
+the bar the FP32 path is held to after 1000 steps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_07588_gb300 import workloads as W
+from parity import TOL, assert_parity, field_errors, run_both
+
+pytestmark = pytest.mark.gpu
+
+
+def _fdlbm():
+    from paper_1804_07588_gb300 import fdlbm
+    return fdlbm
+
+
+def test_initial_moments_match():
+    p = W.periodic_box(40, 28, solid_rows=5)
+    p["init"] = W.random_fields(p, seed=21)
+    s, o = run_both(p, 0)
+    assert_parity(s, o, tol=1e-6, what="t=0")
+
+
+def test_populations_one_step_periodic_ragged():
+    """One step on a 40x28 periodic box (one full and one ragged tile in x, a ragged tile
+    in y): every stored population matches."""
+    p = W.periodic_box(40, 28, reactions=[])
+    p["init"] = W.random_fields(p, seed=22)
+    s, o = run_both(p, 1)
+    g_gpu = s.populations().astype(np.float64)
+    g_ora = o.populations()
+    gas = o.classes() == 0
+    err = np.abs(g_gpu[:, :, gas] - g_ora[:, :, gas]).max() / np.abs(g_ora[:, :, gas]).max()
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("pr,ec", [(0.7, 1), (1.0, 0)])
+def test_parity_periodic_random(pr, ec):
+    p = W.periodic_box(40, 28, reactions=[], Pr=pr, energy_correction=ec)
+    p["init"] = W.random_fields(p, seed=23)
+    s, o = run_both(p, 100)
+    assert_parity(s, o, what="periodic")
+
+
+def test_parity_closed_box_reactive():
+    p = W.periodic_box(70, 20, solid_rows=5)
+    p["init"] = W.random_fields(p, seed=24)
+    s, o = run_both(p, 200)
+    assert_parity(s, o, what="reactive box")
+
+
+@pytest.mark.parametrize("coupling", [W.CONSERVATIVE, W.PAPER])
+def test_parity_channel_short(coupling):
+    p = W.channel(nx=72, n_gas=20, wall=4, coupling=coupling)
+    s, o = run_both(p, 150)
+    assert_parity(s, o, what=f"channel coupling={coupling}")
+
+
+def test_parity_channel_conc_bilinear():
+    p = W.channel(nx=48, n_gas=12, wall=3, reactions=[W.wgs_reaction(k0=50.0, rate_form=W.RATE_CONC_BILINEAR)])
+    s, o = run_both(p, 120)
+    assert_parity(s, o, what="bilinear")
+
+
+def test_parity_porous_small():
+    """Digitised disks (concave staircase corners, one-node fallbacks), periodic in y,
+    inlet and outlet, from random fields."""
+    p = W.porous_disks(nx=100, ny=60, porosity=0.65, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01)
+    p["init"] = W.random_fields(p, seed=25, du=0.005)
+    s, o = run_both(p, 200)
+    info = s.info()
+    assert info["stencil_counts"][4] + info["stencil_counts"][5] + info["stencil_counts"][0] > 0
+    assert_parity(s, o, what="porous")
+
+
+def test_parity_config0_1000_steps():
+    """The catalytic channel (128x32 gas between 8-node FD walls) after 1000 steps:
+    every moment field within 1e-5 of the FP64 oracle."""
+    p = W.config0()
+    s, o = run_both(p, 1000, chunks=4)
+    errs = assert_parity(s, o, what="config0 1000 steps")
+    print("config0 errors", errs)
+
+
+def test_parity_config1_full_size_few_steps():
+    """The full 1024x512 porous bed, in the launch configuration the benchmark times,
+    from random fields: 4 steps, every node of every field."""
+    p = W.config1()
+    p["init"] = W.random_fields(p, seed=26, du=0.005)
+    s, o = run_both(p, 4)
+    assert_parity(s, o, what="config1 full size")
+
+
+def test_ledger_matches_oracle():
+    p = W.periodic_box(60, 20, solid_rows=6)
+    p["init"] = W.random_fields(p, seed=27)
+    s, o = run_both(p, 300)
+    bg, bo = s.balance(), o.balance()
+    for k in ("E_gas", "H_solid", "E_gas0", "H_solid0"):
+        assert abs(bg[k] - bo[k]) <= 1e-6 * abs(bo[k]), (k, bg[k], bo[k])
+    for k in ("Q_reaction", "Q_wall", "Q_couple"):
+        assert abs(bg[k] - bo[k]) <= 1e-4 * max(abs(bo[k]), 1e-12), (k, bg[k], bo[k])
+    np.testing.assert_allclose(bg["mass"], bo["mass"], rtol=1e-6)
+    np.testing.assert_allclose(bg["moles"], bo["moles"], rtol=1e-6)
+    assert abs(bg["solid_residual"]) < 1e-6 * bo["H_solid0"]
+
+
+def test_residual_matches_oracle():
+    p = W.channel(nx=64, n_gas=16, wall=4)
+    from paper_1804_07588_gb300 import fdlbm
+    s = fdlbm.Solver(p)
+    o = oracle.Oracle(p)
+    assert s.residual() == float("inf") and o.residual(0) == float("inf")
+    s.step(50)
+    o.step(50)
+    rg, ro = s.residual(), o.residual(50)
+    assert abs(rg - ro) <= 1e-3 * ro, (rg, ro)
+
+
+def test_set_fields_restarts():
+    p = W.periodic_box(36, 20, solid_rows=4)
+    init = W.random_fields(p, seed=28)
+    from paper_1804_07588_gb300 import fdlbm
+    s = fdlbm.Solver(p)
+    s.step(10)
+    s.set_fields(init)
+    p2 = dict(p)
+    p2["init"] = init
+    o = oracle.Oracle(p2)
+    s.step(30)
+    o.step(30)
+    assert_parity(s, o, what="after set_fields")
+
+
+def test_single_species_and_no_solid():
+    p = W.periodic_box(33, 17, reactions=[])
+    p["species"] = p["species"][:1]
+    p["species"][0]["X_init"] = p["species"][0]["X_inlet"] = 1.0
+    n = 33 * 17
+    p["init"] = {"u": np.vstack([0.01 * np.sin(np.arange(n) / 7.0), np.zeros(n)]),
+                 "T_K": 500 + 3 * np.cos(np.arange(n) / 5.0)}
+    s, o = run_both(p, 60)
+    assert_parity(s, o, what="1 species")
+
+
+def test_unstable_state_is_reported_not_faulted():
+    """A state far outside the equilibrium's validity blows up to NaN; the kernel's
+    sticky flag turns that into FDLBM_EUNSTABLE on the host (no device trap)."""
+    fdlbm = _fdlbm()
+    p = W.periodic_box(32, 16, reactions=[])
+    n = 32 * 16
+    p["init"] = {"u": np.vstack([np.full(n, 0.6), np.zeros(n)])}
+    s = fdlbm.Solver(p)
+    s.step(200)
+    with pytest.raises(fdlbm.FdlbmError) as ei:
+        s.sync()
+    assert ei.value.status == -4
