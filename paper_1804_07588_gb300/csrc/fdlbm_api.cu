@@ -317,7 +317,26 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.nx = nx;
   P.ny = ny;
   P.n = n;
-  P.plane = ((long long)n + 63) / 64 * 64;
+  P.xoff = XOFF;
+  P.yoff = YOFF;
+  P.pitch = (nx + XOFF + 2 * GHOST + 31) / 32 * 32;
+  P.plane = ((long long)P.pitch * (ny + 2 * YOFF) + 63) / 64 * 64;
+  // Code words on the padded lattice: ghost cells within GHOST of a periodic face carry
+  // the wrapped node's word, everything else outside the lattice is OUTSIDE.
+  std::vector<uint32_t> pcode((size_t)P.plane, uint32_t(OUTSIDE));
+  for (int py = 0; py < ny + 2 * YOFF; ++py)
+    for (int px = 0; px < P.pitch; ++px) {
+      int x = px - XOFF, y = py - YOFF;
+      if (x < 0 || x >= nx) {
+        if (!G.px || x < -GHOST || x >= nx + GHOST) continue;
+        x = x < 0 ? x + nx : x - nx;
+      }
+      if (y < 0 || y >= ny) {
+        if (!G.py || y < -GHOST || y >= ny + GHOST) continue;
+        y = y < 0 ? y + ny : y - ny;
+      }
+      pcode[(size_t)px + (size_t)py * P.pitch] = h->code[x + nx * y];
+    }
   P.ns = ns;
   P.periodic_x = G.px;
   P.periodic_y = G.py;
@@ -347,7 +366,17 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     P.sqrtM[j] = (float)std::sqrt(M);
     P.c[j] = (float)c;
     P.c2[j] = (float)(1.0 / M);
-    P.a[j] = (float)(1.0 - c);
+    const double a = 1.0 - c, aa = a * a;
+    P.a[j] = (float)a;
+    P.wc2[j] = (float)(0.5 * (aa - a));
+    P.wc1[j] = (float)(1.0 - aa);
+    P.wc0[j] = (float)(0.5 * (aa + a));
+    P.wf1[j] = (float)(1.0 - 1.5 * a + 0.5 * aa);
+    P.wf0[j] = (float)(2.0 * a - aa);
+    P.wfp[j] = (float)(0.5 * (aa - a));
+    P.wb1[j] = (float)(1.0 + 1.5 * a + 0.5 * aa);
+    P.wb2[j] = (float)(-2.0 * a - aa);
+    P.wb3[j] = (float)(0.5 * (a + aa));
     P.onlattice[j] = (M == 1.0);
     P.rref[j] = (float)(species[j].X_inlet * M);
     P.Xin[j] = (float)species[j].X_inlet;
@@ -427,7 +456,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     return st;                                                                       \
   }                                                                                  \
   field = (type*)p;
-  ALLOC(S.code, uint32_t, n);
+  ALLOC(S.code, uint32_t, P.plane);
   ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
   ALLOC(S.mom, float, (size_t)(ns + 3) * n);
   ALLOC(S.Tgas, float, n);
@@ -437,7 +466,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + 8);
   ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
 #undef ALLOC
-  cudaError_t e = cudaMemcpyAsync(S.code, h->code.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e = cudaMemcpyAsync(S.code, pcode.data(), sizeof(uint32_t) * pcode.size(), cudaMemcpyHostToDevice,
+                                  h->stream);
   if (e == cudaSuccess && !solid_list.empty())
     e = cudaMemcpyAsync(S.solid_list, solid_list.data(), sizeof(int32_t) * solid_list.size(),
                         cudaMemcpyHostToDevice, h->stream);

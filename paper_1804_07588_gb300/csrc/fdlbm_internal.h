@@ -10,6 +10,11 @@
 namespace fdlbm {
 
 constexpr int Q = 9;
+// Ghost layers around the lattice on the padded population/code arrays: the deepest
+// pull reaches 3 nodes upstream of a cell one node outside the tile's lattice range.
+constexpr int GHOST = 4;
+constexpr int XOFF = 8;  // padded column of x = 0 (keeps rows 32-byte aligned)
+constexpr int YOFF = GHOST;
 constexpr int MAX_NS = FDLBM_MAX_SPECIES;
 constexpr int MAX_NR = FDLBM_MAX_REACTIONS;
 
@@ -29,7 +34,8 @@ __host__ __device__ inline uint32_t stencil_of(uint32_t code, int i) {
 // Scalars every kernel needs, passed by value (kernel parameter space).
 struct DevParams {
   int nx, ny, n;        // lattice, node count
-  long long plane;      // elements between population planes (j, i)
+  int pitch, xoff, yoff;  // padded lattice: node (x, y) at (x + xoff) + (y + yoff) * pitch
+  long long plane;      // elements of one padded plane (>= pitch * (ny + 2 yoff))
   int ns;
   int periodic_x, periodic_y;
   int n_solid_list, n_wall_list;  // solid list: wall nodes first
@@ -38,6 +44,10 @@ struct DevParams {
   // species
   float M[MAX_NS], invM[MAX_NS], sqrtM[MAX_NS], c[MAX_NS], c2[MAX_NS];
   float a[MAX_NS];      // 1 - c_j
+  // interpolation weights (Sec. 4.2) of s2, s1, s0 (central), s1, s0, s+ (forward),
+  // s1, s2, s3 (backward)
+  float wc2[MAX_NS], wc1[MAX_NS], wc0[MAX_NS], wf1[MAX_NS], wf0[MAX_NS], wfp[MAX_NS];
+  float wb1[MAX_NS], wb2[MAX_NS], wb3[MAX_NS];
   int onlattice[MAX_NS];
   float rref[MAX_NS];   // reference density X_inlet,j M_j of the stored deviations
   float omega[MAX_NS], t1t2[MAX_NS], wt1[MAX_NS], a2[MAX_NS], inv1a2[MAX_NS];
@@ -63,9 +73,9 @@ struct DevParams {
 
 // Device state of one handle.
 struct DevState {
-  float* h[2];          // populations (deviations from rref W0), [ns][Q][plane]
+  float* h[2];          // populations (deviations from rref W0), [ns][Q][plane] padded
   float* Ts[2];         // solid temperature deviation from Tref, [n]
-  uint32_t* code;       // node code words, [n]
+  uint32_t* code;       // node code words on the padded lattice, [plane]
   int32_t* solid_list;  // wall nodes first, then interior solid nodes
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
   float* Tgas;          // gas temperature of the current time (lattice), [n]

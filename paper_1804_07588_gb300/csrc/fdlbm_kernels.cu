@@ -1,19 +1,22 @@
 // CUDA kernels of the coupled FD-LBM solver (sm_103a).
 //
-// Storage: populations are FP32 deviations h = g - rref_j W0_i from the rest equilibrium
+// Storage. Populations are FP32 deviations h = g - rref_j W0_i from the rest equilibrium
 // of the inlet state (rref_j = X_inlet,j M_j, W0 = f^eq(1, 0, T_ref)); the solid
-// temperature is stored as T_s - T_ref. Every moment and equilibrium is evaluated in
-// that deviation form, so FP32 keeps the precision the FP64 reference needs.
+// temperature is stored as T_s - T_ref. Every moment and equilibrium is evaluated in that
+// deviation form, so FP32 keeps the precision the FP64 reference needs. Population planes
+// [species][direction] live on a padded lattice with GHOST = 4 ghost layers around the
+// nodes: a node within GHOST of a periodic face also writes its populations into the
+// ghost copy on the other side, so every pull is a plain linear offset.
 //
-// Per time step (all kernels read time level t only):
+// Per time step (both kernels read time level t only):
 //   solid_kernel: interface (wall) nodes stream in the populations arriving from the gas,
-//     iterate the wall density with the surface reaction (Sec. 4.3, Eq. BC_gji), emit
-//     the unknown populations and apply the FD heat step with the interface coupling and
-//     the reaction heat (Sec. 5); interior solid nodes apply the FD step only.
-//   gas_kernel: fused pull streaming with the off-lattice interpolation (Sec. 4.2),
-//     moments (Eq. moments_of_g), energy-correction divergence on a shared-memory tile
-//     with a recomputed one-node halo, two-step collision (Eq. final_kinetic_equation),
-//     outlet equilibrium.
+//     iterate the wall density with the surface reaction (Sec. 4.3, Eq. BC_gji), emit the
+//     unknown populations and apply the FD heat step with the interface coupling and the
+//     reaction heat (Sec. 5); interior solid nodes apply the FD step only.
+//   gas_kernel: fused pull streaming with the off-lattice interpolation (Sec. 4.2) into
+//     shared memory, moments (Eq. moments_of_g), divergence of the energy-correction flux
+//     on the 32x8 tile with a recomputed one-node halo, two-step collision (Eq.
+//     final_kinetic_equation), outlet equilibrium.
 #include <cfloat>
 #include <cmath>
 
@@ -25,6 +28,9 @@ namespace {
 
 constexpr int TX = 32;
 constexpr int TY = 8;
+constexpr int NT = TX * TY;
+constexpr int CW = TX + 2;                    // tile width with halo
+constexpr int NCELL = (TX + 2) * (TY + 2);
 constexpr int HALO_N = 2 * (TX + 2) + 2 * TY;
 
 __host__ __device__ constexpr int EX(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
@@ -34,7 +40,11 @@ __host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : (i <= 4 ? ((i
 __host__ __device__ constexpr float PSX(int i) { return i == 1 ? 4.f : i == 3 ? -4.f : (i == 5 || i == 8) ? -1.f : (i == 6 || i == 7) ? 1.f : 0.f; }
 __host__ __device__ constexpr float PSY(int i) { return i == 2 ? 4.f : i == 4 ? -4.f : (i == 5 || i == 6) ? -1.f : (i == 7 || i == 8) ? 1.f : 0.f; }
 
-// Linear index of (x, y), wrapped on periodic axes; -1 off the lattice.
+__device__ __forceinline__ int pad_index(const DevParams& P, int x, int y) {
+  return (x + P.xoff) + (y + P.yoff) * P.pitch;
+}
+
+// Compact index of (x, y) wrapped on periodic axes; -1 off the lattice.
 __device__ __forceinline__ int lat_index(const DevParams& P, int x, int y) {
   if (x < 0) { if (!P.periodic_x) return -1; x += P.nx; }
   else if (x >= P.nx) { if (!P.periodic_x) return -1; x -= P.nx; }
@@ -43,173 +53,136 @@ __device__ __forceinline__ int lat_index(const DevParams& P, int x, int y) {
   return x + P.nx * y;
 }
 
-// Tile cells resolve only positions at most one node off the lattice (a single wrap on
-// periodic axes); farther cells of a ragged tile are never read and stay empty.
-__device__ __forceinline__ int cell_index(const DevParams& P, int x, int y) {
-  if (x < -1 || x > P.nx || y < -1 || y > P.ny) return -1;
-  return lat_index(P, x, y);
+// Padded-lattice offsets of the ghost copies a node at (x, y) must also write: along x
+// and y (0 when none) on periodic axes within GHOST of a face.
+struct Ghost { int dx, dy; };
+__device__ __forceinline__ Ghost ghost_of(const DevParams& P, int x, int y) {
+  Ghost g{0, 0};
+  if (P.periodic_x) g.dx = x < GHOST ? P.nx : (x >= P.nx - GHOST ? -P.nx : 0);
+  if (P.periodic_y) g.dy = y < GHOST ? P.ny * P.pitch : (y >= P.ny - GHOST ? -P.ny * P.pitch : 0);
+  return g;
+}
+__device__ __forceinline__ void store_with_ghosts(float* p, int k, const Ghost& g, float v) {
+  p[k] = v;
+  if (g.dx) p[k + g.dx] = v;
+  if (g.dy) {
+    p[k + g.dy] = v;
+    if (g.dx) p[k + g.dx + g.dy] = v;
+  }
 }
 
-// Interpolation weights of the stencils (Eqs. interpol_bulk, interpol_away,
-// interpol_towards expanded into weights of the streamed off-lattice values).
-struct Weights { float c2, c1, c0, f1, f0, fp, b1, b2, b3, a; };
-__device__ __forceinline__ Weights weights_of(float a) {
-  Weights w;
-  float aa = a * a;
-  w.c2 = 0.5f * (aa - a); w.c1 = 1.f - aa; w.c0 = 0.5f * (aa + a);
-  w.f1 = 1.f - 1.5f * a + 0.5f * aa; w.f0 = 2.f * a - aa; w.fp = 0.5f * (aa - a);
-  w.b1 = 1.f + 1.5f * a + 0.5f * aa; w.b2 = -2.f * a - aa; w.b3 = 0.5f * (a + aa);
-  w.a = a;
-  return w;
-}
-
-// Pull one non-rest population of species j into target (x, y) along direction i.
-template <int I>
-__device__ __forceinline__ float pull_dir(const DevParams& P, const float* __restrict__ pl, int x, int y,
-                                          int n, uint32_t st, bool onlat, const Weights& w) {
-  constexpr int ex = EX(I), ey = EY(I);
-  float s1 = __ldg(pl + lat_index(P, x - ex, y - ey));
-  if (onlat) return s1;
+// Pull one non-rest population into the node at padded index k along direction i, with
+// off = e_i on the padded lattice (Eqs. interpol_bulk, interpol_away, interpol_towards
+// expanded into weights of the streamed off-lattice values).
+__device__ __forceinline__ float pull_one(const DevParams& P, const float* __restrict__ pl, int k, int off,
+                                          uint32_t st, int j) {
+  const float s1 = __ldg(pl + k - off);
+  if (P.onlattice[j]) return s1;
   switch (st) {
-    case ST_CENTRAL: {
-      float s2 = __ldg(pl + lat_index(P, x - 2 * ex, y - 2 * ey));
-      float s0 = __ldg(pl + n);
-      return fmaf(w.c2, s2, fmaf(w.c1, s1, w.c0 * s0));
-    }
-    case ST_FORWARD: {
-      float s0 = __ldg(pl + n);
-      float sp = __ldg(pl + lat_index(P, x + ex, y + ey));
-      return fmaf(w.f1, s1, fmaf(w.f0, s0, w.fp * sp));
-    }
-    case ST_BACKWARD: {
-      float s2 = __ldg(pl + lat_index(P, x - 2 * ex, y - 2 * ey));
-      float s3 = __ldg(pl + lat_index(P, x - 3 * ex, y - 3 * ey));
-      return fmaf(w.b1, s1, fmaf(w.b2, s2, w.b3 * s3));
-    }
-    case ST_LIN_S0: {
-      float s0 = __ldg(pl + n);
-      return fmaf(w.a, s0 - s1, s1);
-    }
-    case ST_LIN_S2: {
-      float s2 = __ldg(pl + lat_index(P, x - 2 * ex, y - 2 * ey));
-      return fmaf(w.a, s1 - s2, s1);
-    }
+    case ST_CENTRAL:
+      return fmaf(P.wc2[j], __ldg(pl + k - 2 * off), fmaf(P.wc1[j], s1, P.wc0[j] * __ldg(pl + k)));
+    case ST_FORWARD:
+      return fmaf(P.wf1[j], s1, fmaf(P.wf0[j], __ldg(pl + k), P.wfp[j] * __ldg(pl + k + off)));
+    case ST_BACKWARD:
+      return fmaf(P.wb1[j], s1, fmaf(P.wb2[j], __ldg(pl + k - 2 * off), P.wb3[j] * __ldg(pl + k - 3 * off)));
+    case ST_LIN_S0:
+      return fmaf(P.a[j], __ldg(pl + k) - s1, s1);
+    case ST_LIN_S2:
+      return fmaf(P.a[j], s1 - __ldg(pl + k - 2 * off), s1);
     default:
       return s1;
   }
 }
 
-template <int NS, int I>
-__device__ __forceinline__ void pull_species_dir(const DevParams& P, const float* __restrict__ src, int x,
-                                                 int y, int n, uint32_t cw, float (&hv)[NS][Q]) {
-  uint32_t st = stencil_of(cw, I);
+// Running species moments of pulled deviations.
+template <int NS>
+struct Acc {
+  float dr[NS], ax[NS], ay[NS], e[NS];
+};
+
+template <int NS, int I, bool STORE>
+__device__ __forceinline__ void pull_dir_all(const DevParams& P, const float* __restrict__ src, int k,
+                                             uint32_t cw, Acc<NS>& a, float* __restrict__ s_h, int tid,
+                                             const float (&ecoef)[3]) {
+  const int off = I == 0 ? 0 : EX(I) + EY(I) * P.pitch;
+  const uint32_t st = I == 0 ? 0u : stencil_of(cw, I);
+  constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     const float* pl = src + (long long)(j * Q + I) * P.plane;
-    Weights w = weights_of(P.a[j]);
-    hv[j][I] = pull_dir<I>(P, pl, x, y, n, st, P.onlattice[j] != 0, w);
+    const float v = I == 0 ? __ldg(pl + k) : pull_one(P, pl, k, off, st, j);
+    if (STORE) s_h[(j * Q + I) * NT + tid] = v;
+    a.dr[j] += v;
+    if (EX(I) > 0) a.ax[j] += v;
+    if (EX(I) < 0) a.ax[j] -= v;
+    if (EY(I) > 0) a.ay[j] += v;
+    if (EY(I) < 0) a.ay[j] -= v;
+    a.e[j] = fmaf(ecoef[e2], v, a.e[j]);
   }
 }
 
-// Stream every population of species 0..NS-1 into gas node (x, y) (index n).
-template <int NS>
-__device__ __forceinline__ void pull_node(const DevParams& P, const float* __restrict__ src, int x, int y,
-                                          int n, uint32_t cw, float (&hv)[NS][Q]) {
+// Stream all populations into the gas node at padded index k and accumulate moments;
+// with STORE the pulled values also go to shared memory.
+template <int NS, bool STORE>
+__device__ __forceinline__ void pull_node(const DevParams& P, const float* __restrict__ src, int k, uint32_t cw,
+                                          Acc<NS>& a, float* __restrict__ s_h, int tid) {
+  const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
 #pragma unroll
-  for (int j = 0; j < NS; ++j) hv[j][0] = __ldg(src + (long long)(j * Q) * P.plane + n);
-  pull_species_dir<NS, 1>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 2>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 3>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 4>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 5>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 6>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 7>(P, src, x, y, n, cw, hv);
-  pull_species_dir<NS, 8>(P, src, x, y, n, cw, hv);
+  for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
+  pull_dir_all<NS, 0, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 1, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 2, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 3, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 4, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 5, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 6, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 7, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
+  pull_dir_all<NS, 8, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
 }
 
-// Runtime-direction pull used on wall nodes (few, divergent anyway).
-__device__ float pull_rt(const DevParams& P, const float* __restrict__ src, int j, int i, int x, int y,
-                         int n, uint32_t st) {
-  const float* pl = src + (long long)(j * Q + i) * P.plane;
-  Weights w = weights_of(P.a[j]);
-  bool onlat = P.onlattice[j] != 0;
-  switch (i) {
-    case 1: return pull_dir<1>(P, pl, x, y, n, st, onlat, w);
-    case 2: return pull_dir<2>(P, pl, x, y, n, st, onlat, w);
-    case 3: return pull_dir<3>(P, pl, x, y, n, st, onlat, w);
-    case 4: return pull_dir<4>(P, pl, x, y, n, st, onlat, w);
-    case 5: return pull_dir<5>(P, pl, x, y, n, st, onlat, w);
-    case 6: return pull_dir<6>(P, pl, x, y, n, st, onlat, w);
-    case 7: return pull_dir<7>(P, pl, x, y, n, st, onlat, w);
-    default: return pull_dir<8>(P, pl, x, y, n, st, onlat, w);
-  }
-}
-
-// Moments of the pulled deviations: species densities, momenta and the g-temperature
-// deviation dTg = T_g - T_ref (Eq. moments_of_g, Eq. moments_of_f).
+// Mixture moments from the species accumulators (Eq. moments_of_g, Eq. moments_of_f):
+// densities, momenta, C and the g-temperature deviation dTg = T_g - T_ref.
 template <int NS>
 struct Mom {
-  float drho[NS], rho[NS], Jx[NS], Jy[NS];
+  float drho[NS], Jx[NS], Jy[NS];
   float r, jx, jy, C, dTg;
 };
 
 template <int NS>
-__device__ __forceinline__ void moments(const DevParams& P, const float (&hv)[NS][Q], Mom<NS>& m) {
-  m.r = 0.f; m.jx = 0.f; m.jy = 0.f; m.C = 0.f;
+__device__ __forceinline__ void finish_moments(const DevParams& P, const Acc<NS>& a, Mom<NS>& m) {
+  m.r = m.jx = m.jy = m.C = 0.f;
   float de = 0.f;
-  const float t2 = 2.f * P.Tref;
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    float dr = 0.f, ax = 0.f, ay = 0.f, e = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float v = hv[j][i];
-      dr += v;
-      if (EX(i) != 0) ax += EX(i) > 0 ? v : -v;
-      if (EY(i) != 0) ay += EY(i) > 0 ? v : -v;
-      e = fmaf(float(EX(i) * EX(i) + EY(i) * EY(i)) - t2, v, e);
-    }
-    m.drho[j] = dr;
-    m.rho[j] = P.rref[j] + dr;
-    m.Jx[j] = P.c[j] * ax;
-    m.Jy[j] = P.c[j] * ay;
-    m.r += m.rho[j];
+    m.drho[j] = a.dr[j];
+    const float rho = P.rref[j] + a.dr[j];
+    m.Jx[j] = P.c[j] * a.ax[j];
+    m.Jy[j] = P.c[j] * a.ay[j];
+    m.r += rho;
     m.jx += m.Jx[j];
     m.jy += m.Jy[j];
-    m.C = fmaf(m.rho[j], P.invM[j], m.C);
-    de = fmaf(P.c2[j], e, de);
+    m.C = fmaf(rho, P.invM[j], m.C);
+    de = fmaf(P.c2[j], a.e[j], de);
   }
   m.dTg = (de - (m.jx * m.jx + m.jy * m.jy) / m.r) / (2.f * m.C);
 }
 
-// One Cartesian factor of the product-form equilibrium (Eq. eq_state_pop, positive-sign
-// form) and its deviation from the rest factor at T_ref.
-__device__ __forceinline__ float wfac(int e, float sv, float Mv2, float T) {
-  return e == 0 ? 1.f - Mv2 - T : 0.5f * (float(e) * sv + Mv2 + T);
-}
-__device__ __forceinline__ float dwfac(int e, float sv, float Mv2, float dT) {
-  return e == 0 ? -(Mv2 + dT) : 0.5f * (float(e) * sv + Mv2 + dT);
-}
-__device__ __forceinline__ float w0fac(int e, float Tref) { return e == 0 ? 1.f - Tref : 0.5f * Tref; }
-
-// Deviation of rho W(e; u) from rref W0(e): (rho - rref) W + rref (dWx Wy + W0x dWy).
-struct EqFactors {
-  float wx[3], wy[3], dwx[3], dwy[3];  // index e + 1
+// One axis of the product-form equilibrium (Eq. eq_state_pop, positive-sign form) for
+// velocity component v: factors w(e) and their deviations dw(e) from the rest factors
+// at T_ref, index e + 1.
+struct Axis {
+  float w[3], dw[3];
 };
-__device__ __forceinline__ void eq_factors(float sqrtM, float M, float ux, float uy, float T, float dT,
-                                           EqFactors& f) {
-  float sx = sqrtM * ux, sy = sqrtM * uy, mx = M * ux * ux, my = M * uy * uy;
-#pragma unroll
-  for (int e = -1; e <= 1; ++e) {
-    f.wx[e + 1] = wfac(e, sx, mx, T);
-    f.wy[e + 1] = wfac(e, sy, my, T);
-    f.dwx[e + 1] = dwfac(e, sx, mx, dT);
-    f.dwy[e + 1] = dwfac(e, sy, my, dT);
-  }
-}
-__device__ __forceinline__ float eq_dev(const EqFactors& f, int i, float drho, float rref, float Tref) {
-  int a = EX(i) + 1, b = EY(i) + 1;
-  return drho * f.wx[a] * f.wy[b] + rref * (f.dwx[a] * f.wy[b] + w0fac(EX(i), Tref) * f.dwy[b]);
+__device__ __forceinline__ Axis axis_factors(float sqrtM, float M, float v, float T, float dT) {
+  const float s = sqrtM * v, m = M * v * v;
+  Axis a;
+  a.w[1] = 1.f - m - T;
+  a.w[2] = 0.5f * (m + T + s);
+  a.w[0] = 0.5f * (m + T - s);
+  a.dw[1] = -(m + dT);
+  a.dw[2] = 0.5f * (m + dT + s);
+  a.dw[0] = 0.5f * (m + dT - s);
+  return a;
 }
 
 template <int NS>
@@ -221,85 +194,90 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // Gas kernel
 // ---------------------------------------------------------------------------------------
 // MODE 0: full step (collide, write populations). MODE 1: moments only (no population
-// writes; writes mom[]).
+// writes; writes mom[] at compact indices).
 template <int NS, bool PHI, int MODE>
-__global__ void __launch_bounds__(TX * TY) gas_kernel(DevParams P, const float* __restrict__ src,
-                                                      float* __restrict__ dst,
-                                                      const uint32_t* __restrict__ code, float* __restrict__ mom,
-                                                      float* __restrict__ Tgas, int* __restrict__ flags) {
-  __shared__ float s_dT[TY + 2][TX + 2];
-  __shared__ float s_K[PHI ? NS : 1][TY + 2][TX + 2];
+__global__ void __launch_bounds__(NT, 3) gas_kernel(DevParams P, const float* __restrict__ src,
+                                                    float* __restrict__ dst, const uint32_t* __restrict__ code,
+                                                    float* __restrict__ mom, float* __restrict__ Tgas,
+                                                    int* __restrict__ flags) {
+  extern __shared__ float smem[];
+  float* s_h = smem;                                        // [NS * Q][NT] (MODE 0)
+  float* s_dT = smem + (MODE == 0 ? NS * Q * NT : 0);       // [NCELL]
+  float* s_K = s_dT + NCELL;                                // [NS][NCELL]
+  unsigned char* s_g = reinterpret_cast<unsigned char*>(s_K + NS * NCELL);  // [NCELL]
 
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool own = gx < P.nx && gy < P.ny;
-  // Interior cells beyond a ragged edge hold the wrapped node on periodic axes so that
-  // the owners' neighbour reads find it.
-  const int n = own ? gx + P.nx * gy : cell_index(P, gx, gy);
-  const uint32_t cw = n >= 0 ? __ldg(code + n) : uint32_t(OUTSIDE);
-  const bool gas = n >= 0 && node_class(cw) == GAS;
-  const int wx = n >= 0 ? n % P.nx : 0, wy = n >= 0 ? n / P.nx : 0;
+  // Cells one node past a ragged edge hold the ghost copy (periodic) or nothing.
+  const bool valid = gx <= P.nx && gy <= P.ny;
+  const int k = pad_index(P, gx, gy);
+  const uint32_t cw = valid ? __ldg(code + k) : uint32_t(OUTSIDE);
+  const bool gas = node_class(cw) == GAS;
 
-  float hv[NS][Q];
+  Acc<NS> acc;
   Mom<NS> m;
   if (gas) {
-    pull_node<NS>(P, src, wx, wy, n, cw, hv);
-    moments<NS>(P, hv, m);
+    pull_node<NS, MODE == 0>(P, src, k, cw, acc, s_h, tid);
+    finish_moments<NS>(P, acc, m);
   }
   if (PHI) {
-    s_dT[ty + 1][tx + 1] = gas ? m.dTg : 0.f;
+    const int c = (ty + 1) * CW + tx + 1;
+    s_dT[c] = gas ? m.dTg : 0.f;
+    s_g[c] = gas ? 1 : 0;
 #pragma unroll
     for (int j = 0; j < NS; ++j)
-      s_K[j][ty + 1][tx + 1] = gas ? P.kcoef[j] * (m.rho[j] * P.invM[j]) * (P.Tref + m.dTg) : 0.f;
-    const int t = ty * TX + tx;
-    if (t < HALO_N) {
+      s_K[j * NCELL + c] = gas ? P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg) : 0.f;
+    if (tid < HALO_N) {
       int hx, hy;
-      if (t < TX + 2) { hx = t - 1; hy = -1; }
-      else if (t < 2 * (TX + 2)) { hx = t - (TX + 2) - 1; hy = TY; }
-      else if (t < 2 * (TX + 2) + TY) { hx = -1; hy = t - 2 * (TX + 2); }
-      else { hx = TX; hy = t - 2 * (TX + 2) - TY; }
-      const int hn = cell_index(P, x0 + hx, y0 + hy);
-      const uint32_t hcw = hn >= 0 ? __ldg(code + hn) : uint32_t(OUTSIDE);
-      float hdT = 0.f, hK[NS];
-#pragma unroll
-      for (int j = 0; j < NS; ++j) hK[j] = 0.f;
-      if (hn >= 0 && node_class(hcw) == GAS) {
-        float hh[NS][Q];
+      if (tid < TX + 2) { hx = tid - 1; hy = -1; }
+      else if (tid < 2 * (TX + 2)) { hx = tid - (TX + 2) - 1; hy = TY; }
+      else if (tid < 2 * (TX + 2) + TY) { hx = -1; hy = tid - 2 * (TX + 2); }
+      else { hx = TX; hy = tid - 2 * (TX + 2) - TY; }
+      const int cx = x0 + hx, cy = y0 + hy;
+      const bool hvalid = cx >= -1 && cy >= -1 && cx <= P.nx && cy <= P.ny;
+      const int hk = pad_index(P, cx, cy);
+      const uint32_t hcw = hvalid ? __ldg(code + hk) : uint32_t(OUTSIDE);
+      const bool hgas = node_class(hcw) == GAS;
+      const int hc = (hy + 1) * CW + hx + 1;
+      float hdT = 0.f;
+      if (hgas) {
+        Acc<NS> ha;
         Mom<NS> hm;
-        pull_node<NS>(P, src, hn % P.nx, hn / P.nx, hn, hcw, hh);
-        moments<NS>(P, hh, hm);
+        pull_node<NS, false>(P, src, hk, hcw, ha, nullptr, 0);
+        finish_moments<NS>(P, ha, hm);
         hdT = hm.dTg;
 #pragma unroll
-        for (int j = 0; j < NS; ++j) hK[j] = P.kcoef[j] * (hm.rho[j] * P.invM[j]) * (P.Tref + hm.dTg);
-      }
-      s_dT[hy + 1][hx + 1] = hdT;
+        for (int j = 0; j < NS; ++j)
+          s_K[j * NCELL + hc] = P.kcoef[j] * ((P.rref[j] + hm.drho[j]) * P.invM[j]) * (P.Tref + hm.dTg);
+      } else {
 #pragma unroll
-      for (int j = 0; j < NS; ++j) s_K[j][hy + 1][hx + 1] = hK[j];
+        for (int j = 0; j < NS; ++j) s_K[j * NCELL + hc] = 0.f;
+      }
+      s_dT[hc] = hdT;
+      s_g[hc] = hgas ? 1 : 0;
     }
     __syncthreads();
   }
   if (!own || !gas) return;
 
-  // Divergence of the energy-correction flux K_j grad T on the 4 axis neighbours: faces
-  // to non-gas nodes carry no flux (their K is stored as 0 and their face is skipped).
+  // Divergence of the energy-correction flux K_j grad T (4 axis neighbours; faces to
+  // non-gas nodes carry no flux).
   float divq[NS];
   float sdq = 0.f;
 #pragma unroll
   for (int j = 0; j < NS; ++j) divq[j] = 0.f;
   if (PHI) {
-    const float Tc = s_dT[ty + 1][tx + 1];
+    const int c = (ty + 1) * CW + tx + 1;
+    const float Tc = s_dT[c];
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
-      const int ox = d == 0 ? 1 : d == 1 ? -1 : 0;
-      const int oy = d == 2 ? 1 : d == 3 ? -1 : 0;
-      const int nn = lat_index(P, gx + ox, gy + oy);
-      const bool ngas = nn >= 0 && node_class(__ldg(code + nn)) == GAS;
-      if (!ngas) continue;
-      const float Tn = s_dT[ty + 1 + oy][tx + 1 + ox];
+      const int cn = c + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? CW : -CW);
+      if (!s_g[cn]) continue;
+      const float dTn = s_dT[cn] - Tc;
 #pragma unroll
-      for (int j = 0; j < NS; ++j)
-        divq[j] += 0.5f * (s_K[j][ty + 1][tx + 1] + s_K[j][ty + 1 + oy][tx + 1 + ox]) * (Tn - Tc);
+      for (int j = 0; j < NS; ++j) divq[j] = fmaf(0.5f * (s_K[j * NCELL + c] + s_K[j * NCELL + cn]), dTn, divq[j]);
     }
 #pragma unroll
     for (int j = 0; j < NS; ++j) sdq += divq[j];
@@ -308,76 +286,105 @@ __global__ void __launch_bounds__(TX * TY) gas_kernel(DevParams P, const float* 
   const float ux = m.jx / m.r, uy = m.jy / m.r;
   const float dT = m.dTg + sdq / (4.f * m.C);
   const float T = P.Tref + dT;
-
-  if (MODE == 1 || Tgas != nullptr) {
-    if (MODE == 1) {
+  const int n = gx + P.nx * gy;
+  if (MODE == 1) {
 #pragma unroll
-      for (int j = 0; j < NS; ++j) mom[(long long)j * P.n + n] = m.rho[j];
-      mom[(long long)NS * P.n + n] = ux;
-      mom[(long long)(NS + 1) * P.n + n] = uy;
-      mom[(long long)(NS + 2) * P.n + n] = T;
-    }
-    if (Tgas != nullptr) Tgas[n] = T;
+    for (int j = 0; j < NS; ++j) mom[(long long)j * P.n + n] = P.rref[j] + m.drho[j];
+    mom[(long long)NS * P.n + n] = ux;
+    mom[(long long)(NS + 1) * P.n + n] = uy;
+    mom[(long long)(NS + 2) * P.n + n] = T;
+    return;
   }
-  if (MODE == 1) return;
+  if (Tgas != nullptr) Tgas[n] = T;
   flag_bad<NS>(flags, m, T);
 
   // Corrective diffusion velocity (reading R3: weights 1/(tau2 + 1/2)).
-  float nx_ = 0.f, ny_ = 0.f, den = 0.f;
+  float ncx = 0.f, ncy = 0.f, den = 0.f;
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    nx_ = fmaf(P.uc_w[j], m.Jx[j] - m.rho[j] * ux, nx_);
-    ny_ = fmaf(P.uc_w[j], m.Jy[j] - m.rho[j] * uy, ny_);
-    den = fmaf(P.uc_w[j], m.rho[j], den);
+    const float rho = P.rref[j] + m.drho[j];
+    ncx = fmaf(P.uc_w[j], m.Jx[j] - rho * ux, ncx);
+    ncy = fmaf(P.uc_w[j], m.Jy[j] - rho * uy, ncy);
+    den = fmaf(P.uc_w[j], rho, den);
   }
-  const float Ucx = nx_ / den, Ucy = ny_ / den;
+  const float Ucx = ncx / den, Ucy = ncy / den;
+  const Ghost gh = ghost_of(P, gx, gy);
 
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    // f-momentum of the species (Eq. moments_of_g, second line) and its velocity,
-    // limited for trace species (reading R15).
-    const float Jfx = (m.Jx[j] + P.a2[j] * m.rho[j] * (ux + Ucx)) * P.inv1a2[j];
-    const float Jfy = (m.Jy[j] + P.a2[j] * m.rho[j] * (uy + Ucy)) * P.inv1a2[j];
+    const float rho = P.rref[j] + m.drho[j];
+    // f-momentum of the species (Eq. moments_of_g) and its velocity, limited for trace
+    // species (reading R15).
+    const float Jfx = (m.Jx[j] + P.a2[j] * rho * (ux + Ucx)) * P.inv1a2[j];
+    const float Jfy = (m.Jy[j] + P.a2[j] * rho * (uy + Ucy)) * P.inv1a2[j];
     float ujx = ux, ujy = uy;
-    if (m.rho[j] != 0.f) {
+    if (rho != 0.f) {
       const float lim = sqrtf(fmaxf(1.f - T, 0.f) * P.invM[j]);
-      ujx = fminf(fmaxf(Jfx / m.rho[j], -lim), lim);
-      ujy = fminf(fmaxf(Jfy / m.rho[j], -lim), lim);
+      const float ir = 1.f / rho;
+      ujx = fminf(fmaxf(Jfx * ir, -lim), lim);
+      ujy = fminf(fmaxf(Jfy * ir, -lim), lim);
     }
-    EqFactors fe, fs;
-    eq_factors(P.sqrtM[j], P.M[j], ux, uy, T, dT, fe);
-    eq_factors(P.sqrtM[j], P.M[j], ujx, ujy, T, dT, fs);
-    const float om = P.omega[j], omt = P.omega[j] * P.t1t2[j], wt1 = P.wt1[j];
-    const float psi_s = m.rho[j] * P.invtau2[j] * 0.25f / P.c[j];
-    const float phi_s = P.M[j] * divq[j];
+    const float M = P.M[j], sM = P.sqrtM[j], dr = m.drho[j], rr = P.rref[j];
+    const Axis ex = axis_factors(sM, M, ux, T, dT), ey = axis_factors(sM, M, uy, T, dT);
+    const Axis sx = axis_factors(sM, M, ujx, T, dT), sy = axis_factors(sM, M, ujy, T, dT);
+    // f(a, b) = (drho wx(a) + rref dwx(a)) wy(b) + rref w0(a) dwy(b): the deviation of
+    // rho wx wy from rref w0x w0y.
+    float pe[3], ps[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      pe[e] = fmaf(dr, ex.w[e], rr * ex.dw[e]);
+      ps[e] = fmaf(dr, sx.w[e], rr * sx.dw[e]);
+    }
+    const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;  // rref w0(0), rref w0(+-1)
+    const float c1 = 1.f - P.omega[j];
+    const float cA = P.omega[j] * (1.f - P.t1t2[j]);
+    const float cB = P.omega[j] * P.t1t2[j];
+    // w1 tau1 Psi_i = PSX_i gfx + PSY_i gfy with psi = PSX / (4 c_j), 1 / c_j = sqrt(M_j)
+    const float gfs = P.wt1[j] * rho * P.invtau2[j] * 0.25f * P.sqrtM[j];
+    const float gfx = gfs * Ucx, gfy = gfs * Ucy;
+    // w1 tau1 Phi_i with phi = M_j {-1, 1/4 on the axis links, 0 on diagonals}
+    const float gphi = P.wt1[j] * M * divq[j];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const float feq = eq_dev(fe, i, m.drho[j], P.rref[j], P.Tref);
-      const float fst = eq_dev(fs, i, m.drho[j], P.rref[j], P.Tref);
-      float force = psi_s * (PSX(i) * Ucx + PSY(i) * Ucy);
-      if (i == 0) force -= phi_s;
-      else if (i <= 4) force += 0.25f * phi_s;
-      const float h = hv[j][i];
-      const float hn = h - om * (h - fst) - omt * (fst - feq) + wt1 * force;
-      dst[(long long)(j * Q + i) * P.plane + n] = hn;
+      const int a = EX(i) + 1, b = EY(i) + 1;
+      const float qa = EX(i) == 0 ? q0 : q1;
+      const float feq = fmaf(pe[a], ey.w[b], qa * ey.dw[b]);
+      const float fst = fmaf(ps[a], sy.w[b], qa * sy.dw[b]);
+      float force = PSX(i) * gfx + PSY(i) * gfy;
+      if (i == 0) force -= gphi;
+      else if (i <= 4) force += 0.25f * gphi;
+      const float h = s_h[(j * Q + i) * NT + tid];
+      // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi)
+      const float hn = fmaf(c1, h, fmaf(cA, fst, fmaf(cB, feq, force)));
+      store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, hn);
     }
   }
 
   // Outlet (reading R13): equilibrium at the outlet pressure with this node's
   // composition, velocity and temperature.
-  if (gx + 1 < P.nx && !P.periodic_x && node_class(__ldg(code + n + 1)) == OUTLET) {
+  if (gx + 1 == P.nx - 1 && node_class(__ldg(code + k + 1)) == OUTLET) {
     const float Cout = P.p_out / T;
+    const Ghost go = ghost_of(P, gx + 1, gy);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-      EqFactors fe;
-      eq_factors(P.sqrtM[j], P.M[j], ux, uy, T, dT, fe);
-      const float rj = m.rho[j] * P.invM[j] / m.C * Cout * P.M[j];
-      const float dr = rj - P.rref[j];
+      const float rj = (P.rref[j] + m.drho[j]) * P.invM[j] / m.C * Cout * P.M[j];
+      const float dr = rj - P.rref[j], rr = P.rref[j];
+      const Axis ex = axis_factors(P.sqrtM[j], P.M[j], ux, T, dT), ey = axis_factors(P.sqrtM[j], P.M[j], uy, T, dT);
+      const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
-        dst[(long long)(j * Q + i) * P.plane + n + 1] = eq_dev(fe, i, dr, P.rref[j], P.Tref);
+      for (int i = 0; i < Q; ++i) {
+        const int a = EX(i) + 1, b = EY(i) + 1;
+        const float pa = fmaf(dr, ex.w[a], rr * ex.dw[a]);
+        const float v = fmaf(pa, ey.w[b], (EX(i) == 0 ? q0 : q1) * ey.dw[b]);
+        store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k + 1, go, v);
+      }
     }
   }
+}
+
+template <int NS, int MODE>
+size_t gas_smem_bytes() {
+  return sizeof(float) * ((MODE == 0 ? NS * Q * NT : 0) + NCELL * (1 + NS)) + NCELL;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -387,29 +394,26 @@ __device__ __forceinline__ float wrest(int i, float T) {
   return (EX(i) == 0 ? 1.f - T : 0.5f * T) * (EY(i) == 0 ? 1.f - T : 0.5f * T);
 }
 
-__device__ void rates(const DevParams& P, const float* rw, float Tw, float* rate) {
-  float Cw[MAX_NS], Ct = 0.f;
-  for (int j = 0; j < P.ns; ++j) {
+template <int NS>
+__device__ void rates(const DevParams& P, const float (&rw)[NS], float Tw, float* rate) {
+  float Cw[NS], Ct = 0.f;
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
     Cw[j] = rw[j] * P.invM[j];
     Ct += Cw[j];
   }
   const float TK = P.T3T0 * Tw;
   for (int r = 0; r < P.nr; ++r) {
     const float k = P.k0[r] * expf(-P.EaR[r] / TK);
-    if (P.rate_form[r] == FDLBM_RATE_CONC_BILINEAR) {
-      float prod = 1.f;
-      for (int j = 0; j < P.ns; ++j)
-        for (int q = 0; q < -P.nu[r][j]; ++q) prod *= Cw[j];
-      rate[r] = k * prod;
-    } else {
-      float fwd = 1.f, bwd = 1.f;
-      for (int j = 0; j < P.ns; ++j) {
-        const float xj = Cw[j] / Ct;
-        for (int q = 0; q < -P.nu[r][j]; ++q) fwd *= xj;
-        for (int q = 0; q < P.nu[r][j]; ++q) bwd *= xj;
-      }
-      rate[r] = k * (fwd - bwd * P.inv_Keq[r]);
+    float fwd = 1.f, bwd = 1.f;
+    const bool conc = P.rate_form[r] == FDLBM_RATE_CONC_BILINEAR;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const float v = conc ? Cw[j] : Cw[j] / Ct;
+      for (int q = 0; q < -P.nu[r][j]; ++q) fwd *= v;
+      for (int q = 0; q < P.nu[r][j]; ++q) bwd *= v;
     }
+    rate[r] = conc ? k * fwd : k * (fwd - bwd * P.inv_Keq[r]);
   }
 }
 
@@ -427,6 +431,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 constexpr int SOLID_BLOCK = 128;
 
+template <int NS>
 __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const float* __restrict__ src,
                                                             float* __restrict__ dst,
                                                             const float* __restrict__ Ts_src,
@@ -439,9 +444,10 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double acc_q = 0.0, acc_w = 0.0, acc_c = 0.0, acc_f = 0.0, acc_nc = 0.0;
   if (t < P.n_solid_list) {
-    const int n = __ldg(list + t);
+    const int n = __ldg(list + t);  // compact index
     const int x = n % P.nx, y = n / P.nx;
-    const uint32_t cw = __ldg(code + n);
+    const int k = pad_index(P, x, y);
+    const uint32_t cw = __ldg(code + k);
     const float Tx = Ts_src[n];
     float lap = 0.f, gas_term = 0.f;
 #pragma unroll
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
         }
         continue;
       }
-      const uint32_t c = node_class(__ldg(code + nb));
+      const uint32_t c = node_class(__ldg(code + k + ox + oy * P.pitch));
       if (c == WALL || c == SOLID) lap += Ts_src[nb] - Tx;
       else if (c == GAS && Tgas != nullptr) gas_term += Tgas[nb] - (P.Tref + Tx);
     }
@@ -468,22 +474,32 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       // directions (towards its gas neighbours).
       uint32_t arr = 0;
       float B = 0.f;
+#pragma unroll
       for (int i = 1; i < Q; ++i)
         if (stencil_of(cw, i) != ST_NOT_ARRIVAL) arr |= 1u << i;
+#pragma unroll
       for (int i = 1; i < Q; ++i)
         if (arr & (1u << OPP(i))) B += wrest(i, Tw);
-      float A[MAX_NS], rw[MAX_NS], mj[MAX_NS];
+      float A[NS], rw[NS], mj[NS];
       float Earr = 0.f;
-      for (int j = 0; j < P.ns; ++j) {
-        float a = 0.f;
-        for (int i = 1; i < Q; ++i) {
-          if (!(arr & (1u << i))) continue;
-          const float v = pull_rt(P, src, j, i, x, y, n, stencil_of(cw, i)) + P.rref[j] * P.W0[i];
-          a += v;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) A[j] = 0.f;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!(arr & (1u << i))) continue;
+        const int off = EX(i) + EY(i) * P.pitch;
+        const uint32_t st = stencil_of(cw, i);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const float v = pull_one(P, src + (long long)(j * Q + i) * P.plane, k, off, st, j) + P.rref[j] * P.W0[i];
+          A[j] += v;
           Earr = fmaf(0.5f * P.c2[j] * float(EX(i) * EX(i) + EY(i) * EY(i)), v, Earr);
         }
-        A[j] = a;
-        rw[j] = a / B;
+      }
+      const float iB = 1.f / B;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        rw[j] = A[j] * iB;
         mj[j] = 0.f;
       }
       float rate[MAX_NR] = {0.f, 0.f, 0.f, 0.f};
@@ -491,12 +507,13 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       if (cat) {
         bool conv = false;
         for (int it = 0; it < P.rho_w_maxit; ++it) {
-          rates(P, rw, Tw, rate);
+          rates<NS>(P, rw, Tw, rate);
           float d = 0.f, rmax = 0.f;
-          for (int j = 0; j < P.ns; ++j) {
-            float m = 0.f;
-            for (int r = 0; r < P.nr; ++r) m += P.M[j] * float(P.nu[r][j]) * rate[r];
-            const float nw = (A[j] + m) / B;
+#pragma unroll
+          for (int j = 0; j < NS; ++j) {
+            float mm = 0.f;
+            for (int r = 0; r < P.nr; ++r) mm += P.M[j] * float(P.nu[r][j]) * rate[r];
+            const float nw = (A[j] + mm) * iB;
             d = fmaxf(d, fabsf(nw - rw[j]));
             rmax = fmaxf(rmax, fabsf(nw));
             rw[j] = nw;
@@ -504,20 +521,24 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
           if (d <= fmaxf(P.rho_w_tol, 4.f * FLT_EPSILON * rmax)) { conv = true; break; }
         }
         if (!conv) acc_nc += 1.0;
-        rates(P, rw, Tw, rate);
-        for (int j = 0; j < P.ns; ++j) {
-          float m = 0.f;
-          for (int r = 0; r < P.nr; ++r) m += P.M[j] * float(P.nu[r][j]) * rate[r];
-          mj[j] = m;
+        rates<NS>(P, rw, Tw, rate);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          float mm = 0.f;
+          for (int r = 0; r < P.nr; ++r) mm += P.M[j] * float(P.nu[r][j]) * rate[r];
+          mj[j] = mm;
         }
       }
+      const Ghost gh = ghost_of(P, x, y);
       float Eout = 0.f;
-      for (int j = 0; j < P.ns; ++j) {
-        const float scale = (A[j] + mj[j]) / B;
-        for (int i = 1; i < Q; ++i) {
-          if (!(arr & (1u << OPP(i)))) continue;
-          const float w = wrest(i, Tw) * scale;
-          dst[(long long)(j * Q + i) * P.plane + n] = w - P.rref[j] * P.W0[i];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        if (!(arr & (1u << OPP(i)))) continue;
+        const float wr = wrest(i, Tw);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          const float w = wr * (A[j] + mj[j]) * iB;
+          store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, w - P.rref[j] * P.W0[i]);
           Eout = fmaf(0.5f * P.c2[j] * float(EX(i) * EX(i) + EY(i) * EY(i)), w, Eout);
         }
       }
@@ -549,7 +570,8 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
 }
 
 // ---------------------------------------------------------------------------------------
-// Initialisation (FP64 arithmetic, then rounded)
+// Initialisation (FP64 arithmetic, then rounded), over every padded cell so that ghost
+// copies start consistent.
 // ---------------------------------------------------------------------------------------
 __device__ double wfac_d(int e, double v, double M, double T) {
   return e == 0 ? 1.0 - M * v * v - T : 0.5 * (double(e) * sqrt(M) * v + M * v * v + T);
@@ -562,10 +584,30 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
                             const double* __restrict__ Tl, const double* __restrict__ Tsl,
                             const double* __restrict__ Cn, const double* __restrict__ inlet_u,
                             const double* __restrict__ X_inlet, double Tref) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= P.n) return;
-  const int x = n % P.nx, y = n / P.nx;
-  const uint32_t c = node_class(code[n]);
+  const long long kk = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (kk >= P.plane) return;
+  const int k = int(kk);
+  for (int j = 0; j < P.ns; ++j)
+    for (int i = 0; i < Q; ++i) {
+      h0[(long long)(j * Q + i) * P.plane + k] = 0.f;
+      h1[(long long)(j * Q + i) * P.plane + k] = 0.f;
+    }
+  if (k >= P.pitch * (P.ny + 2 * P.yoff)) return;
+  const int px = k % P.pitch, py = k / P.pitch;
+  int x = px - P.xoff, y = py - P.yoff;
+  // Ghost cells within GHOST of a periodic face take the wrapped node's state.
+  if (x < 0 || x >= P.nx) {
+    if (!P.periodic_x || x < -GHOST || x >= P.nx + GHOST) return;
+    x = x < 0 ? x + P.nx : x - P.nx;
+  }
+  if (y < 0 || y >= P.ny) {
+    if (!P.periodic_y || y < -GHOST || y >= P.ny + GHOST) return;
+    y = y < 0 ? y + P.ny : y - P.ny;
+  }
+  const bool real = px - P.xoff == x && py - P.yoff == y;
+  const int n = x + P.nx * y;
+  const uint32_t cw = code[pad_index(P, x, y)];
+  const uint32_t c = node_class(cw);
   double Xn[MAX_NS];
   for (int j = 0; j < P.ns; ++j) Xn[j] = X[(long long)j * P.n + n];
   double ux = u[n], uy = u[P.n + n], T = Tl[n], C = Cn[n];
@@ -576,12 +618,6 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
     T = X_inlet[P.ns];
     C = 1.0;
   }
-  for (int j = 0; j < P.ns; ++j)
-    for (int i = 0; i < Q; ++i) {
-      h0[(long long)(j * Q + i) * P.plane + n] = 0.f;
-      h1[(long long)(j * Q + i) * P.plane + n] = 0.f;
-    }
-  Ts0[n] = Ts1[n] = 0.f;
   if (c == GAS || c == INLET || c == OUTLET) {
     for (int j = 0; j < P.ns; ++j) {
       const double M = P.M[j];
@@ -590,11 +626,11 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
         const double f = rho * wfac_d(EX(i), ux, M, T) * wfac_d(EY(i), uy, M, T);
         const double w0 = (EX(i) == 0 ? 1.0 - Tref : 0.5 * Tref) * (EY(i) == 0 ? 1.0 - Tref : 0.5 * Tref);
         const float v = float(f - double(P.rref[j]) * w0);
-        h0[(long long)(j * Q + i) * P.plane + n] = v;
-        h1[(long long)(j * Q + i) * P.plane + n] = v;
+        h0[(long long)(j * Q + i) * P.plane + k] = v;
+        h1[(long long)(j * Q + i) * P.plane + k] = v;
       }
     }
-    if (c == GAS) {
+    if (c == GAS && real) {
       for (int j = 0; j < P.ns; ++j) mom[(long long)j * P.n + n] = float(C * Xn[j] * P.M[j]);
       mom[(long long)P.ns * P.n + n] = float(ux);
       mom[(long long)(P.ns + 1) * P.n + n] = float(uy);
@@ -603,9 +639,8 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
     }
   } else if (c == WALL || c == SOLID) {
     const double Ts = Tsl[n];
-    Ts0[n] = Ts1[n] = float(Ts - Tref);
+    if (real) Ts0[n] = Ts1[n] = float(Ts - Tref);
     if (c == WALL) {
-      const uint32_t cw = code[n];
       for (int j = 0; j < P.ns; ++j) {
         const double rho = C * Xn[j] * P.M[j];
         for (int i = 1; i < Q; ++i) {
@@ -613,24 +648,28 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
           const double wr = (EX(i) == 0 ? 1.0 - Ts : 0.5 * Ts) * (EY(i) == 0 ? 1.0 - Ts : 0.5 * Ts);
           const double w0 = (EX(i) == 0 ? 1.0 - Tref : 0.5 * Tref) * (EY(i) == 0 ? 1.0 - Tref : 0.5 * Tref);
           const float v = float(rho * wr - double(P.rref[j]) * w0);
-          h0[(long long)(j * Q + i) * P.plane + n] = v;
-          h1[(long long)(j * Q + i) * P.plane + n] = v;
+          h0[(long long)(j * Q + i) * P.plane + k] = v;
+          h1[(long long)(j * Q + i) * P.plane + k] = v;
         }
       }
     }
   }
-  (void)x;
+}
+
+__global__ void zero_solid_ts(DevParams P, float* __restrict__ Ts0, float* __restrict__ Ts1) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < P.n) Ts0[n] = Ts1[n] = 0.f;
 }
 
 // ---------------------------------------------------------------------------------------
-// Outputs and reductions
+// Outputs and reductions (compact node indices)
 // ---------------------------------------------------------------------------------------
 __global__ void moments_out_kernel(DevParams P, const float* __restrict__ mom, const float* __restrict__ Ts,
                                    const uint32_t* __restrict__ code, float* __restrict__ dst) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P.n) return;
   const int ns = P.ns;
-  const uint32_t c = node_class(code[n]);
+  const uint32_t c = node_class(code[pad_index(P, n % P.nx, n / P.nx)]);
   const long long N = P.n;
   for (int f = 0; f < 2 * ns + 4; ++f) dst[f * N + n] = 0.f;
   if (c == GAS) {
@@ -649,13 +688,13 @@ __global__ void moments_out_kernel(DevParams P, const float* __restrict__ mom, c
 }
 
 __global__ void populations_out_kernel(DevParams P, const float* __restrict__ h, float* __restrict__ dst) {
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long total = (long long)P.ns * Q * P.n;
-  if (k >= total) return;
-  const int n = int(k % P.n);
-  const int ji = int(k / P.n);
+  if (q >= total) return;
+  const int n = int(q % P.n);
+  const int ji = int(q / P.n);
   const int j = ji / Q, i = ji % Q;
-  dst[k] = h[(long long)ji * P.plane + n] + P.rref[j] * P.W0[i];
+  dst[q] = h[(long long)ji * P.plane + pad_index(P, n % P.nx, n / P.nx)] + P.rref[j] * P.W0[i];
 }
 
 // Ledger totals: E_gas (f-moments + in-transit wall emissions), H_solid, mass_j, moles_j.
@@ -669,7 +708,8 @@ __global__ void totals_kernel(DevParams P, const float* __restrict__ mom, const 
   double E = 0.0, H = 0.0, mass[MAX_NS], moles[MAX_NS];
   for (int j = 0; j < ns; ++j) mass[j] = moles[j] = 0.0;
   if (n < P.n) {
-    const uint32_t cw = code[n];
+    const int k = pad_index(P, n % P.nx, n / P.nx);
+    const uint32_t cw = code[k];
     const uint32_t c = node_class(cw);
     if (c == GAS) {
       double C = 0.0, r = 0.0;
@@ -688,7 +728,7 @@ __global__ void totals_kernel(DevParams P, const float* __restrict__ mom, const 
         for (int i = 1; i < Q; ++i) {
           if (stencil_of(cw, OPP(i)) == ST_NOT_ARRIVAL) continue;
           for (int j = 0; j < ns; ++j) {
-            const double w = double(h[(long long)(j * Q + i) * P.plane + n]) + double(P.rref[j]) * double(P.W0[i]);
+            const double w = double(h[(long long)(j * Q + i) * P.plane + k]) + double(P.rref[j]) * double(P.W0[i]);
             mass[j] += w;
             moles[j] += w / double(P.M[j]);
             E += 0.5 * double(P.c2[j]) * double(EX(i) * EX(i) + EY(i) * EY(i)) * w;
@@ -720,11 +760,11 @@ __global__ void residual_kernel(DevParams P, const float* __restrict__ mom, cons
   const long long N = P.n;
   float cur[MAX_NS + 4];
   bool on_gas = false, on_solid = false;
+  for (int f = 0; f < nf; ++f) cur[f] = 0.f;
   if (n < P.n) {
-    const uint32_t c = node_class(code[n]);
+    const uint32_t c = node_class(code[pad_index(P, n % P.nx, n / P.nx)]);
     on_gas = c == GAS;
     on_solid = c == WALL || c == SOLID;
-    for (int f = 0; f < nf; ++f) cur[f] = 0.f;
     if (on_gas) {
       float C = 0.f;
       for (int j = 0; j < ns; ++j) C += mom[j * N + n] * P.invM[j];
@@ -753,34 +793,44 @@ __global__ void residual_kernel(DevParams P, const float* __restrict__ mom, cons
     for (int f = 0; f < nf; ++f) snap[f * N + n] = cur[f];
 }
 
+template <int NS>
 cudaError_t solid_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
   if (P.n_solid_list <= 0) return cudaSuccess;
   const int dstb = 1 - src;
   float* Tg = P.coupling == FDLBM_COUPLING_PAPER ? S.Tgas : nullptr;
   const int nb = (P.n_solid_list + SOLID_BLOCK - 1) / SOLID_BLOCK;
-  solid_kernel<<<nb, SOLID_BLOCK, 0, st>>>(P, S.h[src], S.h[dstb], S.Ts[src], S.Ts[dstb], S.code, S.solid_list,
-                                           Tg, S.ledger);
+  solid_kernel<NS><<<nb, SOLID_BLOCK, 0, st>>>(P, S.h[src], S.h[dstb], S.Ts[src], S.Ts[dstb], S.code,
+                                               S.solid_list, Tg, S.ledger);
+  return cudaGetLastError();
+}
+
+template <int NS, bool PHI, int MODE>
+cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+  const size_t smem = gas_smem_bytes<NS, MODE>();
+  // Opt in to the dynamic shared memory once per device and instantiation.
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    e = cudaFuncSetAttribute(gas_kernel<NS, PHI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  const int dstb = 1 - src;
+  dim3 block(TX, TY);
+  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas : nullptr;
+  gas_kernel<NS, PHI, MODE><<<grid, block, smem, st>>>(P, S.h[src], S.h[dstb], S.code, MODE == 1 ? S.mom : nullptr,
+                                                       Tg, S.flags);
   return cudaGetLastError();
 }
 
 template <int NS>
 cudaError_t gas_ns(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st) {
-  const int dstb = 1 - src;
-  dim3 block(TX, TY);
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  float* Tg = P.coupling == FDLBM_COUPLING_PAPER ? S.Tgas : nullptr;
-  if (moments_only) {
-    if (P.energy_correction)
-      gas_kernel<NS, true, 1><<<grid, block, 0, st>>>(P, S.h[src], S.h[dstb], S.code, S.mom, nullptr, S.flags);
-    else
-      gas_kernel<NS, false, 1><<<grid, block, 0, st>>>(P, S.h[src], S.h[dstb], S.code, S.mom, nullptr, S.flags);
-  } else {
-    if (P.energy_correction)
-      gas_kernel<NS, true, 0><<<grid, block, 0, st>>>(P, S.h[src], S.h[dstb], S.code, nullptr, Tg, S.flags);
-    else
-      gas_kernel<NS, false, 0><<<grid, block, 0, st>>>(P, S.h[src], S.h[dstb], S.code, nullptr, Tg, S.flags);
-  }
-  return cudaGetLastError();
+  if (moments_only)
+    return P.energy_correction ? gas_launch<NS, true, 1>(P, S, src, st) : gas_launch<NS, false, 1>(P, S, src, st);
+  return P.energy_correction ? gas_launch<NS, true, 0>(P, S, src, st) : gas_launch<NS, false, 0>(P, S, src, st);
 }
 
 cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st) {
@@ -795,27 +845,40 @@ cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, bool mo
   }
 }
 
+cudaError_t dispatch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+  switch (P.ns) {
+    case 1: return solid_ns<1>(P, S, src, st);
+    case 2: return solid_ns<2>(P, S, src, st);
+    case 3: return solid_ns<3>(P, S, src, st);
+    case 4: return solid_ns<4>(P, S, src, st);
+    case 5: return solid_ns<5>(P, S, src, st);
+    case 6: return solid_ns<6>(P, S, src, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, const double* u,
                         const double* T_lat, const double* Ts_lat, const double* C, const double* inlet,
                         cudaStream_t st) {
   const double* X_inlet = inlet + P.ny;
-  const int nb = (P.n + 255) / 256;
-  init_kernel<<<nb, 256, 0, st>>>(P, S.h[0], S.h[1], S.Ts[0], S.Ts[1], S.mom, S.Tgas, S.code, X, u, T_lat, Ts_lat,
-                                  C, inlet, X_inlet, double(P.Tref));
+  zero_solid_ts<<<(P.n + 255) / 256, 256, 0, st>>>(P, S.Ts[0], S.Ts[1]);
+  const long long nb = (P.plane + 255) / 256;
+  init_kernel<<<(unsigned)nb, 256, 0, st>>>(P, S.h[0], S.h[1], S.Ts[0], S.Ts[1], S.mom, S.Tgas, S.code, X, u, T_lat,
+                                            Ts_lat, C, inlet, X_inlet, double(P.Tref));
   return cudaGetLastError();
 }
 
 cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st) {
   if (moments_only) return dispatch_gas(P, S, src, true, st);
-  cudaError_t e = solid_ns(P, S, src, st);
+  cudaError_t e = dispatch_solid(P, S, src, st);
   if (e != cudaSuccess) return e;
   return dispatch_gas(P, S, src, false, st);
 }
 
 cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  return solid_ns(P, S, src, st);
+  return dispatch_solid(P, S, src, st);
 }
 
 cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st) {

@@ -70,7 +70,7 @@ def test_parity_channel_conc_bilinear():
 def test_parity_porous_small():
     """Digitised disks (concave staircase corners, one-node fallbacks), periodic in y,
     inlet and outlet, from random fields."""
-    p = W.porous_disks(nx=100, ny=60, porosity=0.65, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01)
+    p = W.porous_disks(nx=100, ny=60, porosity=0.75, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01)
     p["init"] = W.random_fields(p, seed=25, du=0.005)
     s, o = run_both(p, 200)
     info = s.info()
@@ -138,7 +138,7 @@ def test_set_fields_restarts():
 
 
 def test_single_species_and_no_solid():
-    p = W.periodic_box(33, 17, reactions=[])
+    p = W.periodic_box(33, 17, reactions=[], energy_correction=0)
     p["species"] = p["species"][:1]
     p["species"][0]["X_init"] = p["species"][0]["X_inlet"] = 1.0
     n = 33 * 17
