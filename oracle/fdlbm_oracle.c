@@ -20,8 +20,9 @@
  *      its conservative reading R12) and the reaction heat, plus the ledger fluxes;
  *   3. gas pass: every gas node pulls g*(t) (wall emissions w(t) included) with the
  *      off-lattice quadratic interpolation (Sec. 4.2), takes its moments (Eq.
- *      moments_of_g), the Prandtl correction divergence on its 4 axis neighbours and
- *      collides (Eq. final_kinetic_equation).
+ *      moments_of_g), the energy-correction divergence on its 4 axis neighbours (from
+ *      the moments of the previous time level) and collides (Eq.
+ *      final_kinetic_equation).
  */
 #include "fdlbm_oracle.h"
 
@@ -57,8 +58,10 @@ struct ora_state {
   double* ux;
   double* uy;
   double* T;                 /* mixture temperature T(f), lattice units */
-  double* Tg;                /* scratch: g-temperature */
-  double* Cj;                /* scratch [ns][n] concentrations */
+  double* Tg;                /* g-temperature of the current step */
+  double* Cj;                /* [ns][n] concentrations of the current step */
+  double* Tg_prev;           /* g-temperature of the previous time level (reading R8) */
+  double* Cj_prev;           /* [ns][n] concentrations of the previous time level */
   double* divq;              /* scratch [ns][n] */
   double* q;                 /* [n] reaction heat of the step at wall nodes */
   double* dE;                /* [n] energy the wall put into the gas this step */
@@ -455,6 +458,8 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
   s->T = (double*)xcalloc((size_t)n, sizeof(double));
   s->Tg = (double*)xcalloc((size_t)n, sizeof(double));
   s->Cj = (double*)xcalloc((size_t)ns * n, sizeof(double));
+  s->Tg_prev = (double*)xcalloc((size_t)n, sizeof(double));
+  s->Cj_prev = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->divq = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->q = (double*)xcalloc((size_t)n, sizeof(double));
   s->dE = (double*)xcalloc((size_t)n, sizeof(double));
@@ -531,7 +536,11 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
         }
         if (c == CL_GAS) {
           double Xc[ORA_MAX_NS];
-          for (int j = 0; j < ns; ++j) Xc[j] = Cn * X[j];
+          for (int j = 0; j < ns; ++j) {
+            Xc[j] = Cn * X[j];
+            s->Cj_prev[(size_t)j * n + k] = Cn * X[j];
+          }
+          s->Tg_prev[k] = T;
           fill_moments_from_fields(s, k, Xc, ux, uy, T);
         }
       } else {
@@ -568,6 +577,8 @@ void ora_destroy(ora_state* s) {
   free(s->T);
   free(s->Tg);
   free(s->Cj);
+  free(s->Tg_prev);
+  free(s->Cj_prev);
   free(s->divq);
   free(s->q);
   free(s->dE);
@@ -685,7 +696,9 @@ static void gas_pass(ora_state* s) {
    * K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T. The divergence is the compact
    * second-order conservative difference on the 4 axis neighbours (reading R8: face
    * coefficients are the mean of the two nodes; faces towards non-gas nodes carry no
-   * correction flux). */
+   * correction flux), evaluated on the g-temperature and concentrations of the previous
+   * time level (the moments every gas node computed in the previous step; the initial
+   * fields at the first step). The paper does not fix the time level of the gradients. */
   for (int y = 0; y < s->ny; ++y)
     for (int x = 0; x < s->nx; ++x) {
       int k = x + s->nx * y;
@@ -695,12 +708,12 @@ static void gas_pass(ora_state* s) {
         if (s->p.energy_correction) {
           double cp = 2.0 / s->M[j]; /* (D + 2) / (2 M_j), D = 2 */
           double coef = (2.0 * cp / Pr - 1.0 / s->M[j]) * s->p.tau1[j];
-          double Kc = coef * s->Cj[(size_t)j * n + k] * s->Tg[k];
+          double Kc = coef * s->Cj_prev[(size_t)j * n + k] * s->Tg_prev[k];
           for (int i = 1; i <= 4; ++i) {
             int kn = node_at(s, x + EX[i], y + EY[i]);
             if (kn < 0 || s->cls[kn] != CL_GAS) continue;
-            double Kn = coef * s->Cj[(size_t)j * n + kn] * s->Tg[kn];
-            dq += 0.5 * (Kc + Kn) * (s->Tg[kn] - s->Tg[k]);
+            double Kn = coef * s->Cj_prev[(size_t)j * n + kn] * s->Tg_prev[kn];
+            dq += 0.5 * (Kc + Kn) * (s->Tg_prev[kn] - s->Tg_prev[k]);
           }
         }
         s->divq[(size_t)j * n + k] = dq;
@@ -722,6 +735,9 @@ static void gas_pass(ora_state* s) {
     s->uy[k] = mom[ns + 1];
     s->T[k] = mom[ns + 2];
   }
+  /* The moments of this step become the previous time level of the next one. */
+  memcpy(s->Tg_prev, s->Tg, sizeof(double) * (size_t)n);
+  memcpy(s->Cj_prev, s->Cj, sizeof(double) * (size_t)ns * n);
   /* Outlet (reading R13; the paper fixes only the inlet): equilibrium at the inlet
    * pressure p = C_in T_in (C_in = 1) with the composition, velocity and temperature of
    * the upstream gas node, so that the outlet gives the open channel its pressure

@@ -366,17 +366,10 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     P.sqrtM[j] = (float)std::sqrt(M);
     P.c[j] = (float)c;
     P.c2[j] = (float)(1.0 / M);
-    const double a = 1.0 - c, aa = a * a;
+    const double a = 1.0 - c;
     P.a[j] = (float)a;
-    P.wc2[j] = (float)(0.5 * (aa - a));
-    P.wc1[j] = (float)(1.0 - aa);
-    P.wc0[j] = (float)(0.5 * (aa + a));
-    P.wf1[j] = (float)(1.0 - 1.5 * a + 0.5 * aa);
-    P.wf0[j] = (float)(2.0 * a - aa);
-    P.wfp[j] = (float)(0.5 * (aa - a));
-    P.wb1[j] = (float)(1.0 + 1.5 * a + 0.5 * aa);
-    P.wb2[j] = (float)(-2.0 * a - aa);
-    P.wb3[j] = (float)(0.5 * (a + aa));
+    P.ha[j] = (float)(0.5 * a);
+    P.ha2[j] = (float)(0.5 * a * a);
     P.onlattice[j] = (M == 1.0);
     P.rref[j] = (float)(species[j].X_inlet * M);
     P.Xin[j] = (float)species[j].X_inlet;
@@ -461,9 +454,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.mom, float, (size_t)(ns + 3) * n);
   ALLOC(S.Tgas, float, n);
   ALLOC(S.snap, float, (size_t)(ns + 4) * n);
-  ALLOC(S.ledger, double, LG_COUNT);
+  ALLOC(S.ledger, double, (size_t)LG_COUNT * ledger_slots(P));
   ALLOC(S.flags, int, 4);
-  ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + 8);
+  ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + LG_COUNT + 8);
   ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
 #undef ALLOC
   cudaError_t e = cudaMemcpyAsync(S.code, pcode.data(), sizeof(uint32_t) * pcode.size(), cudaMemcpyHostToDevice,
@@ -579,7 +572,8 @@ fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
   up(dC, C);
   up(dIn, inlet);
   if (e == cudaSuccess) e = launch_init(h->P, h->S, dX, du, dT, dTs, dC, dIn, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->S.ledger, 0, sizeof(double) * LG_COUNT, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->S.ledger, 0, sizeof(double) * LG_COUNT * ledger_slots(h->P), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->S.flags, 0, sizeof(int) * 4, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(d);
@@ -653,7 +647,10 @@ fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out) {
   fdlbm_status st = read_totals(h, tot.data());
   if (st != FDLBM_OK) return st;
   double lg[LG_COUNT];
-  CK(cudaMemcpy(lg, h->S.ledger, sizeof(lg), cudaMemcpyDeviceToHost), "read ledger");
+  double* lsum = h->S.red + totals_count(ns) + residual_count(ns);
+  CK(launch_ledger_sum(h->P, h->S, lsum, h->stream), "ledger sum");
+  CK(cudaMemcpyAsync(lg, lsum, sizeof(lg), cudaMemcpyDeviceToHost, h->stream), "read ledger");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
   std::memset(out, 0, sizeof(*out));
   out->steps = h->steps;
   out->E_gas = tot[0];

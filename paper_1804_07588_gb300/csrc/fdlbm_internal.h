@@ -44,10 +44,7 @@ struct DevParams {
   // species
   float M[MAX_NS], invM[MAX_NS], sqrtM[MAX_NS], c[MAX_NS], c2[MAX_NS];
   float a[MAX_NS];      // 1 - c_j
-  // interpolation weights (Sec. 4.2) of s2, s1, s0 (central), s1, s0, s+ (forward),
-  // s1, s2, s3 (backward)
-  float wc2[MAX_NS], wc1[MAX_NS], wc0[MAX_NS], wf1[MAX_NS], wf0[MAX_NS], wfp[MAX_NS];
-  float wb1[MAX_NS], wb2[MAX_NS], wb3[MAX_NS];
+  float ha[MAX_NS], ha2[MAX_NS];  // (1 - c_j) / 2 and (1 - c_j)^2 / 2 (interpolation)
   int onlattice[MAX_NS];
   float rref[MAX_NS];   // reference density X_inlet,j M_j of the stored deviations
   float omega[MAX_NS], t1t2[MAX_NS], wt1[MAX_NS], a2[MAX_NS], inv1a2[MAX_NS];
@@ -80,7 +77,7 @@ struct DevState {
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
   float* Tgas;          // gas temperature of the current time (lattice), [n]
   float* snap;          // residual snapshot [(ns + 4)][n]
-  double* ledger;       // device accumulators, see LEDGER_*
+  double* ledger;       // FP64 ledger accumulators, LG_COUNT per solid-kernel block
   int* flags;           // sticky error flags
   double* red;          // reduction scratch (doubles)
 };
@@ -101,6 +98,9 @@ cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool mom
 // The two kernels of a step, separately (for per-kernel timing).
 cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st);
 cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st);
+// Per-block ledger slots of the solid kernel and their sum (LG_COUNT doubles into out).
+int ledger_slots(const DevParams& P);
+cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st);
 cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst,
                                cudaStream_t st);
 cudaError_t launch_populations_out(const DevParams& P, const DevState& S, int cur, float* dst,

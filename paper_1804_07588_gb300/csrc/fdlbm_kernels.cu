@@ -32,6 +32,9 @@ constexpr int NT = TX * TY;
 constexpr int CW = TX + 2;                    // tile width with halo
 constexpr int NCELL = (TX + 2) * (TY + 2);
 constexpr int HALO_N = 2 * (TX + 2) + 2 * TY;
+// With the energy correction a block has 8 warps for the 32x8 interior cells plus 3 warps
+// that recompute the moments of the 84 halo cells concurrently.
+constexpr int NT_HALO = NT + 96;
 
 __host__ __device__ constexpr int EX(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
 __host__ __device__ constexpr int EY(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
@@ -62,29 +65,40 @@ __device__ __forceinline__ Ghost ghost_of(const DevParams& P, int x, int y) {
   if (P.periodic_y) g.dy = y < GHOST ? P.ny * P.pitch : (y >= P.ny - GHOST ? -P.ny * P.pitch : 0);
   return g;
 }
+// Populations are written once per step and read only by the next step: streaming
+// (evict-first) stores keep L2 for the current step's reads.
 __device__ __forceinline__ void store_with_ghosts(float* p, int k, const Ghost& g, float v) {
-  p[k] = v;
-  if (g.dx) p[k + g.dx] = v;
+  __stcs(p + k, v);
+  if (g.dx) __stcs(p + k + g.dx, v);
   if (g.dy) {
-    p[k + g.dy] = v;
-    if (g.dx) p[k + g.dx + g.dy] = v;
+    __stcs(p + k + g.dy, v);
+    if (g.dx) __stcs(p + k + g.dx + g.dy, v);
   }
 }
 
 // Pull one non-rest population into the node at padded index k along direction i, with
-// off = e_i on the padded lattice (Eqs. interpol_bulk, interpol_away, interpol_towards
-// expanded into weights of the streamed off-lattice values).
+// off = e_i on the padded lattice: the off-lattice value s1 streamed from x - e_i advanced
+// by (1 - c_j) with the first and second differences of Eqs. interpol_bulk (central),
+// interpol_away (forward) and interpol_towards (backward). The differences vanish
+// exactly on uniform data, so FP32 rounding adds no systematic mass or momentum.
 __device__ __forceinline__ float pull_one(const DevParams& P, const float* __restrict__ pl, int k, int off,
                                           uint32_t st, int j) {
   const float s1 = __ldg(pl + k - off);
   if (P.onlattice[j]) return s1;
+  const float ha = P.ha[j], ha2 = P.ha2[j];  // (1 - c) / 2, (1 - c)^2 / 2
   switch (st) {
-    case ST_CENTRAL:
-      return fmaf(P.wc2[j], __ldg(pl + k - 2 * off), fmaf(P.wc1[j], s1, P.wc0[j] * __ldg(pl + k)));
-    case ST_FORWARD:
-      return fmaf(P.wf1[j], s1, fmaf(P.wf0[j], __ldg(pl + k), P.wfp[j] * __ldg(pl + k + off)));
-    case ST_BACKWARD:
-      return fmaf(P.wb1[j], s1, fmaf(P.wb2[j], __ldg(pl + k - 2 * off), P.wb3[j] * __ldg(pl + k - 3 * off)));
+    case ST_CENTRAL: {
+      const float s2 = __ldg(pl + k - 2 * off), s0 = __ldg(pl + k);
+      return fmaf(ha, s0 - s2, fmaf(ha2, (s0 + s2) - 2.f * s1, s1));
+    }
+    case ST_FORWARD: {
+      const float s0 = __ldg(pl + k), sp = __ldg(pl + k + off);
+      return fmaf(ha, (4.f * s0 - sp) - 3.f * s1, fmaf(ha2, (s1 + sp) - 2.f * s0, s1));
+    }
+    case ST_BACKWARD: {
+      const float s2 = __ldg(pl + k - 2 * off), s3 = __ldg(pl + k - 3 * off);
+      return fmaf(ha, (3.f * s1 + s3) - 4.f * s2, fmaf(ha2, (s1 + s3) - 2.f * s2, s1));
+    }
     case ST_LIN_S0:
       return fmaf(P.a[j], __ldg(pl + k) - s1, s1);
     case ST_LIN_S2:
@@ -196,22 +210,23 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // MODE 0: full step (collide, write populations). MODE 1: moments only (no population
 // writes; writes mom[] at compact indices).
 template <int NS, bool PHI, int MODE>
-__global__ void __launch_bounds__(NT, 3) gas_kernel(DevParams P, const float* __restrict__ src,
-                                                    float* __restrict__ dst, const uint32_t* __restrict__ code,
-                                                    float* __restrict__ mom, float* __restrict__ Tgas,
-                                                    int* __restrict__ flags) {
+__global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
+    DevParams P, const float* __restrict__ src, float* __restrict__ dst, const uint32_t* __restrict__ code,
+    float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags) {
   extern __shared__ float smem[];
   float* s_h = smem;                                        // [NS * Q][NT] (MODE 0)
   float* s_dT = smem + (MODE == 0 ? NS * Q * NT : 0);       // [NCELL]
   float* s_K = s_dT + NCELL;                                // [NS][NCELL]
   unsigned char* s_g = reinterpret_cast<unsigned char*>(s_K + NS * NCELL);  // [NCELL]
 
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int tid = threadIdx.x;
+  const bool interior = tid < NT;
+  const int tx = tid & (TX - 1), ty = tid / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + tx, gy = y0 + ty;
-  const bool own = gx < P.nx && gy < P.ny;
+  const bool own = interior && gx < P.nx && gy < P.ny;
   // Cells one node past a ragged edge hold the ghost copy (periodic) or nothing.
-  const bool valid = gx <= P.nx && gy <= P.ny;
+  const bool valid = interior && gx <= P.nx && gy <= P.ny;
   const int k = pad_index(P, gx, gy);
   const uint32_t cw = valid ? __ldg(code + k) : uint32_t(OUTSIDE);
   const bool gas = node_class(cw) == GAS;
@@ -223,18 +238,20 @@ __global__ void __launch_bounds__(NT, 3) gas_kernel(DevParams P, const float* __
     finish_moments<NS>(P, acc, m);
   }
   if (PHI) {
-    const int c = (ty + 1) * CW + tx + 1;
-    s_dT[c] = gas ? m.dTg : 0.f;
-    s_g[c] = gas ? 1 : 0;
+    if (interior) {
+      const int c = (ty + 1) * CW + tx + 1;
+      s_dT[c] = gas ? m.dTg : 0.f;
+      s_g[c] = gas ? 1 : 0;
 #pragma unroll
-    for (int j = 0; j < NS; ++j)
-      s_K[j * NCELL + c] = gas ? P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg) : 0.f;
-    if (tid < HALO_N) {
+      for (int j = 0; j < NS; ++j)
+        s_K[j * NCELL + c] = gas ? P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg) : 0.f;
+    } else if (tid - NT < HALO_N) {
+      const int hid = tid - NT;
       int hx, hy;
-      if (tid < TX + 2) { hx = tid - 1; hy = -1; }
-      else if (tid < 2 * (TX + 2)) { hx = tid - (TX + 2) - 1; hy = TY; }
-      else if (tid < 2 * (TX + 2) + TY) { hx = -1; hy = tid - 2 * (TX + 2); }
-      else { hx = TX; hy = tid - 2 * (TX + 2) - TY; }
+      if (hid < TX + 2) { hx = hid - 1; hy = -1; }
+      else if (hid < 2 * (TX + 2)) { hx = hid - (TX + 2) - 1; hy = TY; }
+      else if (hid < 2 * (TX + 2) + TY) { hx = -1; hy = hid - 2 * (TX + 2); }
+      else { hx = TX; hy = hid - 2 * (TX + 2) - TY; }
       const int cx = x0 + hx, cy = y0 + hy;
       const bool hvalid = cx >= -1 && cy >= -1 && cx <= P.nx && cy <= P.ny;
       const int hk = pad_index(P, cx, cy);
@@ -336,9 +353,7 @@ __global__ void __launch_bounds__(NT, 3) gas_kernel(DevParams P, const float* __
       ps[e] = fmaf(dr, sx.w[e], rr * sx.dw[e]);
     }
     const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;  // rref w0(0), rref w0(+-1)
-    const float c1 = 1.f - P.omega[j];
-    const float cA = P.omega[j] * (1.f - P.t1t2[j]);
-    const float cB = P.omega[j] * P.t1t2[j];
+    const float om = P.omega[j], omt = P.omega[j] * P.t1t2[j];
     // w1 tau1 Psi_i = PSX_i gfx + PSY_i gfy with psi = PSX / (4 c_j), 1 / c_j = sqrt(M_j)
     const float gfs = P.wt1[j] * rho * P.invtau2[j] * 0.25f * P.sqrtM[j];
     const float gfx = gfs * Ucx, gfy = gfs * Ucy;
@@ -354,8 +369,9 @@ __global__ void __launch_bounds__(NT, 3) gas_kernel(DevParams P, const float* __
       if (i == 0) force -= gphi;
       else if (i <= 4) force += 0.25f * gphi;
       const float h = s_h[(j * Q + i) * NT + tid];
-      // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi)
-      const float hn = fmaf(c1, h, fmaf(cA, fst, fmaf(cB, feq, force)));
+      // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi); the two
+      // small differences are formed first so that FP32 keeps their precision.
+      const float hn = fmaf(-om, h - fst, fmaf(-omt, fst - feq, h + force));
       store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, hn);
     }
   }
@@ -554,19 +570,30 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
     }
     Ts_dst[n] = Tn;
   }
-  // Block-reduce the FP64 ledger increments, one atomic per block and term.
+  // Block-reduce the FP64 ledger increments into this block's own accumulator slots
+  // (no atomics; the slots are summed when the ledger is read).
   const double s_q = block_sum(acc_q, sh);
   const double s_w = block_sum(acc_w, sh);
   const double s_c = block_sum(acc_c, sh);
   const double s_f = block_sum(acc_f, sh);
   const double s_n = block_sum(acc_nc, sh);
   if (threadIdx.x == 0) {
-    if (s_q != 0.0) atomicAdd(ledger + LG_QRXN, s_q);
-    if (s_w != 0.0) atomicAdd(ledger + LG_QWALL, s_w);
-    if (s_c != 0.0) atomicAdd(ledger + LG_QCOUPLE, s_c);
-    if (s_f != 0.0) atomicAdd(ledger + LG_QFIXEDT, s_f);
-    if (s_n != 0.0) atomicAdd(ledger + LG_NOCONV, s_n);
+    double* slot = ledger + (long long)blockIdx.x * LG_COUNT;
+    if (s_q != 0.0) slot[LG_QRXN] += s_q;
+    if (s_w != 0.0) slot[LG_QWALL] += s_w;
+    if (s_c != 0.0) slot[LG_QCOUPLE] += s_c;
+    if (s_f != 0.0) slot[LG_QFIXEDT] += s_f;
+    if (s_n != 0.0) slot[LG_NOCONV] += s_n;
   }
+}
+
+// Sum of the per-block ledger slots.
+__global__ void ledger_sum_kernel(const double* __restrict__ slots, int nblocks, double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= LG_COUNT) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += slots[(long long)b * LG_COUNT + t];
+  out[t] = s;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -818,7 +845,7 @@ cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStrea
     configured |= 1ull << dev;
   }
   const int dstb = 1 - src;
-  dim3 block(TX, TY);
+  dim3 block(PHI ? NT_HALO : NT);
   dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
   float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas : nullptr;
   gas_kernel<NS, PHI, MODE><<<grid, block, smem, st>>>(P, S.h[src], S.h[dstb], S.code, MODE == 1 ? S.mom : nullptr,
@@ -883,6 +910,13 @@ cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStr
 
 cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
   return dispatch_gas(P, S, src, false, st);
+}
+
+int ledger_slots(const DevParams& P) { return P.n_solid_list > 0 ? (P.n_solid_list + SOLID_BLOCK - 1) / SOLID_BLOCK : 1; }
+
+cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st) {
+  ledger_sum_kernel<<<1, 32, 0, st>>>(S.ledger, ledger_slots(P), out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst, cudaStream_t st) {
