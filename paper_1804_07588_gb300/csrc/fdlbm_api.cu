@@ -306,6 +306,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       } else if (c == SOLID) {
         solids.push_back(k);
       }
+      if (c == GAS)
+        for (int i = 1; i <= 4; ++i)
+          if (G.cls_at(x + HEX[i], y + HEY[i]) == GAS) w |= 1u << (NBR_GAS_SHIFT + i - 1);
       h->code[k] = w;
       h->counts[c]++;
     }
@@ -321,6 +324,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.yoff = YOFF;
   P.pitch = (nx + XOFF + 2 * GHOST + 31) / 32 * 32;
   P.plane = ((long long)P.pitch * (ny + 2 * YOFF) + 63) / 64 * 64;
+  std::vector<int32_t> gas_list;
+  gas_list.reserve((size_t)h->counts[GAS]);
   // Code words on the padded lattice: ghost cells within GHOST of a periodic face carry
   // the wrapped node's word, everything else outside the lattice is OUTSIDE.
   std::vector<uint32_t> pcode((size_t)P.plane, uint32_t(OUTSIDE));
@@ -337,6 +342,10 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       }
       pcode[(size_t)px + (size_t)py * P.pitch] = h->code[x + nx * y];
     }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x)
+      if (G.cls[x + nx * y] == GAS) gas_list.push_back((x + XOFF) + (y + YOFF) * P.pitch);
+  P.n_gas = (int)gas_list.size();
   P.ns = ns;
   P.periodic_x = G.px;
   P.periodic_y = G.py;
@@ -451,6 +460,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   field = (type*)p;
   ALLOC(S.code, uint32_t, P.plane);
   ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
+  ALLOC(S.gas_list, int32_t, std::max<size_t>(gas_list.size(), 1));
+  ALLOC(S.F[0], float, (size_t)(ns + 1) * P.plane);
+  ALLOC(S.F[1], float, (size_t)(ns + 1) * P.plane);
   ALLOC(S.mom, float, (size_t)(ns + 3) * n);
   ALLOC(S.Tgas, float, n);
   ALLOC(S.snap, float, (size_t)(ns + 4) * n);
@@ -464,6 +476,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (e == cudaSuccess && !solid_list.empty())
     e = cudaMemcpyAsync(S.solid_list, solid_list.data(), sizeof(int32_t) * solid_list.size(),
                         cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !gas_list.empty())
+    e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int32_t) * gas_list.size(), cudaMemcpyHostToDevice,
+                        h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     release(h);

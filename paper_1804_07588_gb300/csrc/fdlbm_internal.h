@@ -25,6 +25,8 @@ enum Stencil : uint32_t { ST_NONE = 0, ST_CENTRAL = 1, ST_FORWARD = 2, ST_BACKWA
                           ST_LIN_S0 = 4, ST_LIN_S2 = 5, ST_NOT_ARRIVAL = 7 };
 constexpr uint32_t CATALYTIC_BIT = 1u << 3;
 constexpr int STENCIL_SHIFT = 4;
+// Bits 28..31: gas node has a gas neighbour along direction 1..4 (+x, +y, -x, -y).
+constexpr int NBR_GAS_SHIFT = 28;
 
 __host__ __device__ inline uint32_t node_class(uint32_t code) { return code & 7u; }
 __host__ __device__ inline uint32_t stencil_of(uint32_t code, int i) {
@@ -39,6 +41,7 @@ struct DevParams {
   int ns;
   int periodic_x, periodic_y;
   int n_solid_list, n_wall_list;  // solid list: wall nodes first
+  int n_gas;            // gas-node list length
   int energy_correction, coupling;
   int fixedT_face[4];   // x-, x+, y-, y+
   // species
@@ -73,7 +76,9 @@ struct DevState {
   float* h[2];          // populations (deviations from rref W0), [ns][Q][plane] padded
   float* Ts[2];         // solid temperature deviation from Tref, [n]
   uint32_t* code;       // node code words on the padded lattice, [plane]
-  int32_t* solid_list;  // wall nodes first, then interior solid nodes
+  int32_t* solid_list;  // wall nodes first, then interior solid nodes (compact indices)
+  int32_t* gas_list;    // gas nodes, row-major (padded indices)
+  float* F[2];          // moment fields [1 + ns][plane]: dTg, K_j (ping-pong with h)
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
   float* Tgas;          // gas temperature of the current time (lattice), [n]
   float* snap;          // residual snapshot [(ns + 4)][n]

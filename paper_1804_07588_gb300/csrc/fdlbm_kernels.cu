@@ -13,10 +13,11 @@
 //     iterate the wall density with the surface reaction (Sec. 4.3, Eq. BC_gji), emit the
 //     unknown populations and apply the FD heat step with the interface coupling and the
 //     reaction heat (Sec. 5); interior solid nodes apply the FD step only.
-//   gas_kernel: fused pull streaming with the off-lattice interpolation (Sec. 4.2) into
-//     shared memory, moments (Eq. moments_of_g), divergence of the energy-correction flux
-//     on the 32x8 tile with a recomputed one-node halo, two-step collision (Eq.
-//     final_kinetic_equation), outlet equilibrium.
+//   gas_kernel: one thread per entry of a compact list of gas nodes: fused pull streaming
+//     with the off-lattice interpolation (Sec. 4.2) into thread-private shared memory,
+//     moments (Eq. moments_of_g), divergence of the energy-correction flux from the
+//     moment field of the previous time level, two-step collision (Eq.
+//     final_kinetic_equation), outlet equilibrium; it writes this step's moment field.
 #include <cfloat>
 #include <cmath>
 
@@ -26,15 +27,10 @@ namespace fdlbm {
 
 namespace {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int NT = TX * TY;
-constexpr int CW = TX + 2;                    // tile width with halo
-constexpr int NCELL = (TX + 2) * (TY + 2);
-constexpr int HALO_N = 2 * (TX + 2) + 2 * TY;
-// With the energy correction a block has 8 warps for the 32x8 interior cells plus 3 warps
-// that recompute the moments of the 84 halo cells concurrently.
-constexpr int NT_HALO = NT + 96;
+constexpr int GB = 256;  // gas kernel block size (threads = gas nodes)
+#ifndef GAS_MIN_BLOCKS
+#define GAS_MIN_BLOCKS 3
+#endif
 
 __host__ __device__ constexpr int EX(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
 __host__ __device__ constexpr int EY(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0; }
@@ -81,28 +77,29 @@ __device__ __forceinline__ void store_with_ghosts(float* p, int k, const Ghost& 
 // by (1 - c_j) with the first and second differences of Eqs. interpol_bulk (central),
 // interpol_away (forward) and interpol_towards (backward). The differences vanish
 // exactly on uniform data, so FP32 rounding adds no systematic mass or momentum.
-__device__ __forceinline__ float pull_one(const DevParams& P, const float* __restrict__ pl, int k, int off,
+__device__ __forceinline__ float pull_one(const DevParams& P, const float* __restrict__ src, int b, int off,
                                           uint32_t st, int j) {
-  const float s1 = __ldg(pl + k - off);
+  // b: element index of this node in the (j, i) plane; 32-bit offsets from one base.
+  const float s1 = __ldg(src + (b - off));
   if (P.onlattice[j]) return s1;
   const float ha = P.ha[j], ha2 = P.ha2[j];  // (1 - c) / 2, (1 - c)^2 / 2
   switch (st) {
     case ST_CENTRAL: {
-      const float s2 = __ldg(pl + k - 2 * off), s0 = __ldg(pl + k);
+      const float s2 = __ldg(src + (b - 2 * off)), s0 = __ldg(src + b);
       return fmaf(ha, s0 - s2, fmaf(ha2, (s0 + s2) - 2.f * s1, s1));
     }
     case ST_FORWARD: {
-      const float s0 = __ldg(pl + k), sp = __ldg(pl + k + off);
+      const float s0 = __ldg(src + b), sp = __ldg(src + (b + off));
       return fmaf(ha, (4.f * s0 - sp) - 3.f * s1, fmaf(ha2, (s1 + sp) - 2.f * s0, s1));
     }
     case ST_BACKWARD: {
-      const float s2 = __ldg(pl + k - 2 * off), s3 = __ldg(pl + k - 3 * off);
+      const float s2 = __ldg(src + (b - 2 * off)), s3 = __ldg(src + (b - 3 * off));
       return fmaf(ha, (3.f * s1 + s3) - 4.f * s2, fmaf(ha2, (s1 + s3) - 2.f * s2, s1));
     }
     case ST_LIN_S0:
-      return fmaf(P.a[j], __ldg(pl + k) - s1, s1);
+      return fmaf(P.a[j], __ldg(src + b) - s1, s1);
     case ST_LIN_S2:
-      return fmaf(P.a[j], s1 - __ldg(pl + k - 2 * off), s1);
+      return fmaf(P.a[j], s1 - __ldg(src + (b - 2 * off)), s1);
     default:
       return s1;
   }
@@ -123,9 +120,9 @@ __device__ __forceinline__ void pull_dir_all(const DevParams& P, const float* __
   constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    const float* pl = src + (long long)(j * Q + I) * P.plane;
-    const float v = I == 0 ? __ldg(pl + k) : pull_one(P, pl, k, off, st, j);
-    if (STORE) s_h[(j * Q + I) * NT + tid] = v;
+    const int b = (j * Q + I) * (int)P.plane + k;
+    const float v = I == 0 ? __ldg(src + b) : pull_one(P, src, b, off, st, j);
+    if (STORE) s_h[(j * Q + I) * GB + tid] = v;
     a.dr[j] += v;
     if (EX(I) > 0) a.ax[j] += v;
     if (EX(I) < 0) a.ax[j] -= v;
@@ -207,94 +204,52 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // ---------------------------------------------------------------------------------------
 // Gas kernel
 // ---------------------------------------------------------------------------------------
-// MODE 0: full step (collide, write populations). MODE 1: moments only (no population
-// writes; writes mom[] at compact indices).
+// MODE 0: full step (collide, write populations and this step's moment field).
+// MODE 1: moments only (recomputes the pre-collision moments of the step that read
+// src / Fsrc into mom[] at compact indices; writes nothing else).
+// Moment field F: [1 + NS][plane]: dTg and K_j = kcoef_j C_j T_g of every gas node.
 template <int NS, bool PHI, int MODE>
-__global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
-    DevParams P, const float* __restrict__ src, float* __restrict__ dst, const uint32_t* __restrict__ code,
-    float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags) {
+__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, const float* __restrict__ src,
+                                                    float* __restrict__ dst, const uint32_t* __restrict__ code,
+                                                    const int32_t* __restrict__ gas_list,
+                                                    const float* __restrict__ Fsrc, float* __restrict__ Fdst,
+                                                    float* __restrict__ mom, float* __restrict__ Tgas,
+                                                    int* __restrict__ flags) {
   extern __shared__ float smem[];
-  float* s_h = smem;                                        // [NS * Q][NT] (MODE 0)
-  float* s_dT = smem + (MODE == 0 ? NS * Q * NT : 0);       // [NCELL]
-  float* s_K = s_dT + NCELL;                                // [NS][NCELL]
-  unsigned char* s_g = reinterpret_cast<unsigned char*>(s_K + NS * NCELL);  // [NCELL]
-
+  float* s_h = smem;  // [NS * Q][GB], thread-private columns (MODE 0)
   const int tid = threadIdx.x;
-  const bool interior = tid < NT;
-  const int tx = tid & (TX - 1), ty = tid / TX;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool own = interior && gx < P.nx && gy < P.ny;
-  // Cells one node past a ragged edge hold the ghost copy (periodic) or nothing.
-  const bool valid = interior && gx <= P.nx && gy <= P.ny;
-  const int k = pad_index(P, gx, gy);
-  const uint32_t cw = valid ? __ldg(code + k) : uint32_t(OUTSIDE);
-  const bool gas = node_class(cw) == GAS;
+  const int t = blockIdx.x * GB + tid;
+  if (t >= P.n_gas) return;
+  const int k = __ldg(gas_list + t);
+  const uint32_t cw = __ldg(code + k);
+  const int px = k % P.pitch;
+  const int gx = px - P.xoff, gy = k / P.pitch - P.yoff;
 
   Acc<NS> acc;
   Mom<NS> m;
-  if (gas) {
-    pull_node<NS, MODE == 0>(P, src, k, cw, acc, s_h, tid);
-    finish_moments<NS>(P, acc, m);
-  }
-  if (PHI) {
-    if (interior) {
-      const int c = (ty + 1) * CW + tx + 1;
-      s_dT[c] = gas ? m.dTg : 0.f;
-      s_g[c] = gas ? 1 : 0;
-#pragma unroll
-      for (int j = 0; j < NS; ++j)
-        s_K[j * NCELL + c] = gas ? P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg) : 0.f;
-    } else if (tid - NT < HALO_N) {
-      const int hid = tid - NT;
-      int hx, hy;
-      if (hid < TX + 2) { hx = hid - 1; hy = -1; }
-      else if (hid < 2 * (TX + 2)) { hx = hid - (TX + 2) - 1; hy = TY; }
-      else if (hid < 2 * (TX + 2) + TY) { hx = -1; hy = hid - 2 * (TX + 2); }
-      else { hx = TX; hy = hid - 2 * (TX + 2) - TY; }
-      const int cx = x0 + hx, cy = y0 + hy;
-      const bool hvalid = cx >= -1 && cy >= -1 && cx <= P.nx && cy <= P.ny;
-      const int hk = pad_index(P, cx, cy);
-      const uint32_t hcw = hvalid ? __ldg(code + hk) : uint32_t(OUTSIDE);
-      const bool hgas = node_class(hcw) == GAS;
-      const int hc = (hy + 1) * CW + hx + 1;
-      float hdT = 0.f;
-      if (hgas) {
-        Acc<NS> ha;
-        Mom<NS> hm;
-        pull_node<NS, false>(P, src, hk, hcw, ha, nullptr, 0);
-        finish_moments<NS>(P, ha, hm);
-        hdT = hm.dTg;
-#pragma unroll
-        for (int j = 0; j < NS; ++j)
-          s_K[j * NCELL + hc] = P.kcoef[j] * ((P.rref[j] + hm.drho[j]) * P.invM[j]) * (P.Tref + hm.dTg);
-      } else {
-#pragma unroll
-        for (int j = 0; j < NS; ++j) s_K[j * NCELL + hc] = 0.f;
-      }
-      s_dT[hc] = hdT;
-      s_g[hc] = hgas ? 1 : 0;
-    }
-    __syncthreads();
-  }
-  if (!own || !gas) return;
+  pull_node<NS, MODE == 0>(P, src, k, cw, acc, s_h, tid);
+  finish_moments<NS>(P, acc, m);
 
-  // Divergence of the energy-correction flux K_j grad T (4 axis neighbours; faces to
-  // non-gas nodes carry no flux).
+  // Divergence of the energy-correction flux K_j grad T on the 4 axis neighbours, from
+  // the moment field of the previous time level (reading R8); faces to non-gas nodes
+  // carry no flux.
   float divq[NS];
   float sdq = 0.f;
 #pragma unroll
   for (int j = 0; j < NS; ++j) divq[j] = 0.f;
   if (PHI) {
-    const int c = (ty + 1) * CW + tx + 1;
-    const float Tc = s_dT[c];
+    const float Tc = __ldg(Fsrc + k);
+    float Kc[NS];
 #pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const int cn = c + (d == 0 ? 1 : d == 1 ? -1 : d == 2 ? CW : -CW);
-      if (!s_g[cn]) continue;
-      const float dTn = s_dT[cn] - Tc;
+    for (int j = 0; j < NS; ++j) Kc[j] = __ldg(Fsrc + (long long)(1 + j) * P.plane + k);
 #pragma unroll
-      for (int j = 0; j < NS; ++j) divq[j] = fmaf(0.5f * (s_K[j * NCELL + c] + s_K[j * NCELL + cn]), dTn, divq[j]);
+    for (int d = 1; d <= 4; ++d) {
+      if (!((cw >> (NBR_GAS_SHIFT + d - 1)) & 1u)) continue;
+      const int kn = k + EX(d) + EY(d) * P.pitch;
+      const float dTn = __ldg(Fsrc + kn) - Tc;
+#pragma unroll
+      for (int j = 0; j < NS; ++j)
+        divq[j] = fmaf(0.5f * (Kc[j] + __ldg(Fsrc + (long long)(1 + j) * P.plane + kn)), dTn, divq[j]);
     }
 #pragma unroll
     for (int j = 0; j < NS; ++j) sdq += divq[j];
@@ -312,6 +267,14 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
     mom[(long long)(NS + 2) * P.n + n] = T;
     return;
   }
+  const Ghost gh = ghost_of(P, gx, gy);
+  if (PHI) {
+    store_with_ghosts(Fdst, k, gh, m.dTg);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+      store_with_ghosts(Fdst + (long long)(1 + j) * P.plane, k, gh,
+                        P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg));
+  }
   if (Tgas != nullptr) Tgas[n] = T;
   flag_bad<NS>(flags, m, T);
 
@@ -325,15 +288,26 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
     den = fmaf(P.uc_w[j], rho, den);
   }
   const float Ucx = ncx / den, Ucy = ncy / den;
-  const Ghost gh = ghost_of(P, gx, gy);
 
+  // Per-species inputs of the collision parked in this thread's shared-memory column so
+  // that the species loop below is not unrolled (keeps the live register set small).
+  float* s_m = s_h + NS * Q * GB;  // [4 NS][GB]
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    const float rho = P.rref[j] + m.drho[j];
+    s_m[(4 * j + 0) * GB + tid] = m.drho[j];
+    s_m[(4 * j + 1) * GB + tid] = m.Jx[j];
+    s_m[(4 * j + 2) * GB + tid] = m.Jy[j];
+    s_m[(4 * j + 3) * GB + tid] = divq[j];
+  }
+#pragma unroll 1
+  for (int j = 0; j < NS; ++j) {
+    const float drj = s_m[(4 * j + 0) * GB + tid], Jxj = s_m[(4 * j + 1) * GB + tid];
+    const float Jyj = s_m[(4 * j + 2) * GB + tid], dqj = s_m[(4 * j + 3) * GB + tid];
+    const float rho = P.rref[j] + drj;
     // f-momentum of the species (Eq. moments_of_g) and its velocity, limited for trace
     // species (reading R15).
-    const float Jfx = (m.Jx[j] + P.a2[j] * rho * (ux + Ucx)) * P.inv1a2[j];
-    const float Jfy = (m.Jy[j] + P.a2[j] * rho * (uy + Ucy)) * P.inv1a2[j];
+    const float Jfx = (Jxj + P.a2[j] * rho * (ux + Ucx)) * P.inv1a2[j];
+    const float Jfy = (Jyj + P.a2[j] * rho * (uy + Ucy)) * P.inv1a2[j];
     float ujx = ux, ujy = uy;
     if (rho != 0.f) {
       const float lim = sqrtf(fmaxf(1.f - T, 0.f) * P.invM[j]);
@@ -341,7 +315,7 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
       ujx = fminf(fmaxf(Jfx * ir, -lim), lim);
       ujy = fminf(fmaxf(Jfy * ir, -lim), lim);
     }
-    const float M = P.M[j], sM = P.sqrtM[j], dr = m.drho[j], rr = P.rref[j];
+    const float M = P.M[j], sM = P.sqrtM[j], dr = drj, rr = P.rref[j];
     const Axis ex = axis_factors(sM, M, ux, T, dT), ey = axis_factors(sM, M, uy, T, dT);
     const Axis sx = axis_factors(sM, M, ujx, T, dT), sy = axis_factors(sM, M, ujy, T, dT);
     // f(a, b) = (drho wx(a) + rref dwx(a)) wy(b) + rref w0(a) dwy(b): the deviation of
@@ -358,7 +332,7 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
     const float gfs = P.wt1[j] * rho * P.invtau2[j] * 0.25f * P.sqrtM[j];
     const float gfx = gfs * Ucx, gfy = gfs * Ucy;
     // w1 tau1 Phi_i with phi = M_j {-1, 1/4 on the axis links, 0 on diagonals}
-    const float gphi = P.wt1[j] * M * divq[j];
+    const float gphi = P.wt1[j] * M * dqj;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int a = EX(i) + 1, b = EY(i) + 1;
@@ -368,7 +342,7 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
       float force = PSX(i) * gfx + PSY(i) * gfy;
       if (i == 0) force -= gphi;
       else if (i <= 4) force += 0.25f * gphi;
-      const float h = s_h[(j * Q + i) * NT + tid];
+      const float h = s_h[(j * Q + i) * GB + tid];
       // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi); the two
       // small differences are formed first so that FP32 keeps their precision.
       const float hn = fmaf(-om, h - fst, fmaf(-omt, fst - feq, h + force));
@@ -400,7 +374,7 @@ __global__ void __launch_bounds__(PHI ? NT_HALO : NT, PHI ? 2 : 3) gas_kernel(
 
 template <int NS, int MODE>
 size_t gas_smem_bytes() {
-  return sizeof(float) * ((MODE == 0 ? NS * Q * NT : 0) + NCELL * (1 + NS)) + NCELL;
+  return sizeof(float) * (MODE == 0 ? (NS * Q + 4 * NS) * GB : 1);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -507,7 +481,7 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
         const uint32_t st = stencil_of(cw, i);
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          const float v = pull_one(P, src + (long long)(j * Q + i) * P.plane, k, off, st, j) + P.rref[j] * P.W0[i];
+          const float v = pull_one(P, src, (j * Q + i) * (int)P.plane + k, off, st, j) + P.rref[j] * P.W0[i];
           A[j] += v;
           Earr = fmaf(0.5f * P.c2[j] * float(EX(i) * EX(i) + EY(i) * EY(i)), v, Earr);
         }
@@ -605,6 +579,7 @@ __device__ double wfac_d(int e, double v, double M, double T) {
 }
 
 __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restrict__ h1,
+                            float* __restrict__ F0, float* __restrict__ F1,
                             float* __restrict__ Ts0, float* __restrict__ Ts1, float* __restrict__ mom,
                             float* __restrict__ Tgas, const uint32_t* __restrict__ code,
                             const double* __restrict__ X, const double* __restrict__ u,
@@ -619,6 +594,7 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
       h0[(long long)(j * Q + i) * P.plane + k] = 0.f;
       h1[(long long)(j * Q + i) * P.plane + k] = 0.f;
     }
+  for (int f = 0; f <= P.ns; ++f) F0[(long long)f * P.plane + k] = F1[(long long)f * P.plane + k] = 0.f;
   if (k >= P.pitch * (P.ny + 2 * P.yoff)) return;
   const int px = k % P.pitch, py = k / P.pitch;
   int x = px - P.xoff, y = py - P.yoff;
@@ -656,6 +632,12 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
         h0[(long long)(j * Q + i) * P.plane + k] = v;
         h1[(long long)(j * Q + i) * P.plane + k] = v;
       }
+    }
+    if (c == GAS) {
+      // Moment field of the time level before the first step: the initial fields.
+      F0[k] = F1[k] = float(T - Tref);
+      for (int j = 0; j < P.ns; ++j)
+        F0[(long long)(1 + j) * P.plane + k] = F1[(long long)(1 + j) * P.plane + k] = float(double(P.kcoef[j]) * C * Xn[j] * T);
     }
     if (c == GAS && real) {
       for (int j = 0; j < P.ns; ++j) mom[(long long)j * P.n + n] = float(C * Xn[j] * P.M[j]);
@@ -833,6 +815,7 @@ cudaError_t solid_ns(const DevParams& P, const DevState& S, int src, cudaStream_
 
 template <int NS, bool PHI, int MODE>
 cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+  if (P.n_gas <= 0) return cudaSuccess;
   const size_t smem = gas_smem_bytes<NS, MODE>();
   // Opt in to the dynamic shared memory once per device and instantiation.
   static unsigned long long configured = 0;
@@ -845,11 +828,10 @@ cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStrea
     configured |= 1ull << dev;
   }
   const int dstb = 1 - src;
-  dim3 block(PHI ? NT_HALO : NT);
-  dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  const int grid = (P.n_gas + GB - 1) / GB;
   float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas : nullptr;
-  gas_kernel<NS, PHI, MODE><<<grid, block, smem, st>>>(P, S.h[src], S.h[dstb], S.code, MODE == 1 ? S.mom : nullptr,
-                                                       Tg, S.flags);
+  gas_kernel<NS, PHI, MODE><<<grid, GB, smem, st>>>(P, S.h[src], S.h[dstb], S.code, S.gas_list, S.F[src], S.F[dstb],
+                                                    MODE == 1 ? S.mom : nullptr, Tg, S.flags);
   return cudaGetLastError();
 }
 
@@ -892,7 +874,7 @@ cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, 
   const double* X_inlet = inlet + P.ny;
   zero_solid_ts<<<(P.n + 255) / 256, 256, 0, st>>>(P, S.Ts[0], S.Ts[1]);
   const long long nb = (P.plane + 255) / 256;
-  init_kernel<<<(unsigned)nb, 256, 0, st>>>(P, S.h[0], S.h[1], S.Ts[0], S.Ts[1], S.mom, S.Tgas, S.code, X, u, T_lat,
+  init_kernel<<<(unsigned)nb, 256, 0, st>>>(P, S.h[0], S.h[1], S.F[0], S.F[1], S.Ts[0], S.Ts[1], S.mom, S.Tgas, S.code, X, u, T_lat,
                                             Ts_lat, C, inlet, X_inlet, double(P.Tref));
   return cudaGetLastError();
 }
