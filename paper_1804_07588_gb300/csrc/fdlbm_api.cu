@@ -342,6 +342,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       }
       pcode[(size_t)px + (size_t)py * P.pitch] = h->code[x + nx * y];
     }
+  // Gas nodes row-major: a warp writes contiguous runs of every population plane.
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x)
       if (G.cls[x + nx * y] == GAS) gas_list.push_back((x + XOFF) + (y + YOFF) * P.pitch);

@@ -111,17 +111,66 @@ struct Acc {
   float dr[NS], ax[NS], ay[NS], e[NS];
 };
 
+// Branch-free form of every streaming stencil: with s1 streamed from x - e_i and two more
+// sources sA, sB at x + mA e_i and x + mB e_i, the pulled value is
+//   s1 + (a/2) [(pA sA + pB sB) - (pA + pB) s1] + (a^2/2) [(qA sA + qB sB) - (qA + qB) s1]
+// (a = 1 - c_j): central (Eq. interpol_bulk) sA = s2, sB = s0; forward (Eq.
+// interpol_away) sA = s0, sB = s+; backward (Eq. interpol_towards) sA = s2, sB = s3;
+// linear and none as degenerate cases. The brackets vanish exactly on uniform data.
+struct StencilCoef {
+  int mA, mB;
+  float pA, pB, p1, qA, qB, q1;
+};
+__device__ __forceinline__ StencilCoef stencil_coef(uint32_t st) {
+  StencilCoef c;
+  const bool cen = st == ST_CENTRAL, fwd = st == ST_FORWARD, bwd = st == ST_BACKWARD;
+  const bool l0 = st == ST_LIN_S0, l2 = st == ST_LIN_S2;
+  c.mA = (cen || bwd || l2) ? -2 : 0;
+  c.mB = fwd ? 1 : (bwd ? -3 : (l2 ? -2 : 0));
+  c.pA = cen ? -1.f : fwd ? 4.f : bwd ? -4.f : l0 ? 2.f : l2 ? -2.f : 0.f;
+  c.pB = cen ? 1.f : fwd ? -1.f : bwd ? 1.f : 0.f;
+  c.p1 = cen ? 0.f : fwd ? 3.f : bwd ? -3.f : l0 ? 2.f : l2 ? -2.f : 0.f;
+  c.qA = cen ? 1.f : (fwd || bwd) ? -2.f : 0.f;
+  c.qB = (cen || fwd || bwd) ? 1.f : 0.f;
+  c.q1 = cen ? 2.f : (fwd || bwd) ? -1.f : 0.f;
+  return c;
+}
+
 template <int NS, int I, bool STORE>
 __device__ __forceinline__ void pull_dir_all(const DevParams& P, const float* __restrict__ src, int k,
                                              uint32_t cw, Acc<NS>& a, float* __restrict__ s_h, int tid,
                                              const float (&ecoef)[3]) {
-  const int off = I == 0 ? 0 : EX(I) + EY(I) * P.pitch;
-  const uint32_t st = I == 0 ? 0u : stencil_of(cw, I);
   constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
+  if (I == 0) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const float v = __ldg(src + ((j * Q) * (int)P.plane + k));
+      if (STORE) s_h[(j * Q) * GB + tid] = v;
+      a.dr[j] += v;
+      a.e[j] = fmaf(ecoef[0], v, a.e[j]);
+    }
+    return;
+  }
+  const int off = EX(I) + EY(I) * P.pitch;
+  const StencilCoef sc = stencil_coef(stencil_of(cw, I));
+  const int dA = sc.mA * off, dB = sc.mB * off;
+  // Issue the three loads of every species first so that all of them are in flight.
+  float v1[NS], vA[NS], vB[NS];
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     const int b = (j * Q + I) * (int)P.plane + k;
-    const float v = I == 0 ? __ldg(src + b) : pull_one(P, src, b, off, st, j);
+    v1[j] = __ldg(src + (b - off));
+    vA[j] = __ldg(src + (b + dA));
+    vB[j] = __ldg(src + (b + dB));
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    float v = v1[j];
+    if (!P.onlattice[j]) {
+      const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1[j];
+      const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1[j];
+      v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
+    }
     if (STORE) s_h[(j * Q + I) * GB + tid] = v;
     a.dr[j] += v;
     if (EX(I) > 0) a.ax[j] += v;
@@ -175,7 +224,7 @@ __device__ __forceinline__ void finish_moments(const DevParams& P, const Acc<NS>
     m.C = fmaf(rho, P.invM[j], m.C);
     de = fmaf(P.c2[j], a.e[j], de);
   }
-  m.dTg = (de - (m.jx * m.jx + m.jy * m.jy) / m.r) / (2.f * m.C);
+  m.dTg = (de - (m.jx * m.jx + m.jy * m.jy) / m.r) * (0.5f / m.C);
 }
 
 // One axis of the product-form equilibrium (Eq. eq_state_pop, positive-sign form) for
@@ -287,7 +336,8 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, co
     ncy = fmaf(P.uc_w[j], m.Jy[j] - rho * uy, ncy);
     den = fmaf(P.uc_w[j], rho, den);
   }
-  const float Ucx = ncx / den, Ucy = ncy / den;
+  const float iden = 1.f / den;
+  const float Ucx = ncx * iden, Ucy = ncy * iden;
 
   // Per-species inputs of the collision parked in this thread's shared-memory column so
   // that the species loop below is not unrolled (keeps the live register set small).
@@ -310,10 +360,15 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, co
     const float Jfy = (Jyj + P.a2[j] * rho * (uy + Ucy)) * P.inv1a2[j];
     float ujx = ux, ujy = uy;
     if (rho != 0.f) {
-      const float lim = sqrtf(fmaxf(1.f - T, 0.f) * P.invM[j]);
       const float ir = 1.f / rho;
-      ujx = fminf(fmaxf(Jfx * ir, -lim), lim);
-      ujy = fminf(fmaxf(Jfy * ir, -lim), lim);
+      ujx = Jfx * ir;
+      ujy = Jfy * ir;
+      const float lim2 = fmaxf(1.f - T, 0.f) * P.invM[j];
+      if (ujx * ujx > lim2 || ujy * ujy > lim2) {  // rare: trace species driven through zero
+        const float lim = sqrtf(lim2);
+        ujx = fminf(fmaxf(ujx, -lim), lim);
+        ujy = fminf(fmaxf(ujy, -lim), lim);
+      }
     }
     const float M = P.M[j], sM = P.sqrtM[j], dr = drj, rr = P.rref[j];
     const Axis ex = axis_factors(sM, M, ux, T, dT), ey = axis_factors(sM, M, uy, T, dT);
@@ -384,26 +439,28 @@ __device__ __forceinline__ float wrest(int i, float T) {
   return (EX(i) == 0 ? 1.f - T : 0.5f * T) * (EY(i) == 0 ? 1.f - T : 0.5f * T);
 }
 
+// Reaction rates (lattice moles per wall node per step) at wall densities rw, with the
+// Arrhenius factors k_r = k0_r exp(-Ea_r / (R T_w)) precomputed for this wall node.
 template <int NS>
-__device__ void rates(const DevParams& P, const float (&rw)[NS], float Tw, float* rate) {
+__device__ __forceinline__ void rates(const DevParams& P, const float (&rw)[NS], const float* kr, float* rate) {
   float Cw[NS], Ct = 0.f;
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     Cw[j] = rw[j] * P.invM[j];
     Ct += Cw[j];
   }
-  const float TK = P.T3T0 * Tw;
+  const float iCt = 1.f / Ct;
   for (int r = 0; r < P.nr; ++r) {
-    const float k = P.k0[r] * expf(-P.EaR[r] / TK);
     float fwd = 1.f, bwd = 1.f;
     const bool conc = P.rate_form[r] == FDLBM_RATE_CONC_BILINEAR;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-      const float v = conc ? Cw[j] : Cw[j] / Ct;
-      for (int q = 0; q < -P.nu[r][j]; ++q) fwd *= v;
-      for (int q = 0; q < P.nu[r][j]; ++q) bwd *= v;
+      const float v = conc ? Cw[j] : Cw[j] * iCt;
+      const int nu = P.nu[r][j];
+      for (int q = 0; q < -nu; ++q) fwd *= v;
+      for (int q = 0; q < nu; ++q) bwd *= v;
     }
-    rate[r] = conc ? k * fwd : k * (fwd - bwd * P.inv_Keq[r]);
+    rate[r] = conc ? kr[r] * fwd : kr[r] * (fwd - bwd * P.inv_Keq[r]);
   }
 }
 
@@ -463,27 +520,26 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       // Arrival directions carry a stencil code; the wall emits along the opposite
       // directions (towards its gas neighbours).
       uint32_t arr = 0;
-      float B = 0.f;
-#pragma unroll
       for (int i = 1; i < Q; ++i)
         if (stencil_of(cw, i) != ST_NOT_ARRIVAL) arr |= 1u << i;
-#pragma unroll
+      float B = 0.f;
       for (int i = 1; i < Q; ++i)
         if (arr & (1u << OPP(i))) B += wrest(i, Tw);
       float A[NS], rw[NS], mj[NS];
       float Earr = 0.f;
 #pragma unroll
       for (int j = 0; j < NS; ++j) A[j] = 0.f;
-#pragma unroll
+#pragma unroll 1
       for (int i = 1; i < Q; ++i) {
         if (!(arr & (1u << i))) continue;
         const int off = EX(i) + EY(i) * P.pitch;
         const uint32_t st = stencil_of(cw, i);
+        const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
           const float v = pull_one(P, src, (j * Q + i) * (int)P.plane + k, off, st, j) + P.rref[j] * P.W0[i];
           A[j] += v;
-          Earr = fmaf(0.5f * P.c2[j] * float(EX(i) * EX(i) + EY(i) * EY(i)), v, Earr);
+          Earr = fmaf(e2h * P.c2[j], v, Earr);
         }
       }
       const float iB = 1.f / B;
@@ -495,9 +551,12 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       float rate[MAX_NR] = {0.f, 0.f, 0.f, 0.f};
       const bool cat = (cw & CATALYTIC_BIT) && P.nr > 0;
       if (cat) {
+        float kr[MAX_NR];
+        const float TK = P.T3T0 * Tw;
+        for (int r = 0; r < P.nr; ++r) kr[r] = P.k0[r] * expf(-P.EaR[r] / TK);
         bool conv = false;
         for (int it = 0; it < P.rho_w_maxit; ++it) {
-          rates<NS>(P, rw, Tw, rate);
+          rates<NS>(P, rw, kr, rate);
           float d = 0.f, rmax = 0.f;
 #pragma unroll
           for (int j = 0; j < NS; ++j) {
@@ -511,7 +570,7 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
           if (d <= fmaxf(P.rho_w_tol, 4.f * FLT_EPSILON * rmax)) { conv = true; break; }
         }
         if (!conv) acc_nc += 1.0;
-        rates<NS>(P, rw, Tw, rate);
+        rates<NS>(P, rw, kr, rate);
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
           float mm = 0.f;
@@ -521,15 +580,19 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       }
       const Ghost gh = ghost_of(P, x, y);
       float Eout = 0.f;
+      float scale[NS];
 #pragma unroll
+      for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iB;
+#pragma unroll 1
       for (int i = 1; i < Q; ++i) {
         if (!(arr & (1u << OPP(i)))) continue;
         const float wr = wrest(i, Tw);
+        const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          const float w = wr * (A[j] + mj[j]) * iB;
+          const float w = wr * scale[j];
           store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, w - P.rref[j] * P.W0[i]);
-          Eout = fmaf(0.5f * P.c2[j] * float(EX(i) * EX(i) + EY(i) * EY(i)), w, Eout);
+          Eout = fmaf(e2h * P.c2[j], w, Eout);
         }
       }
       float q = 0.f;
