@@ -3,8 +3,8 @@
 (D2Q9, 1024 x 512 nodes, catalytic FD-solid disks r ~ U[6, 12], porosity 0.6, five
 species CO/H2O/CO2/H2/N2 with water-gas shift on the disk surfaces, FP32 storage).
 
-A step is one time step of the whole scheme: the wall + solid kernel and the fused gas
-kernel. Timing: W untimed warm-up steps, then K timed steps, each preceded by an L2
+A step is one time step of the whole scheme: one launch of the step kernel, whose
+blocks run the gas update and the wall + solid update. Timing: W untimed warm-up steps, then K timed steps, each preceded by an L2
 flush (a 256 MB write, untimed) and bracketed by CUDA events on the solver's stream.
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle instead
 on a bounded crop of the same bed.
@@ -68,9 +68,9 @@ def kernel_source_hash():
 
 
 def ncu_traffic():
-    """DRAM bytes per gas-kernel launch from the committed ncu summary, or None when the
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "gas_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -238,7 +238,7 @@ def run_fdlbm(args, rank, world, local_rank):
     if dist is not None:
         dist.barrier()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    ms_solid, ms_gas, timed = s.kernel_times()
+    ms_step, timed = s.kernel_times()
     s.profile(False)
     s.sync()
     if dist is not None:
@@ -247,9 +247,9 @@ def run_fdlbm(args, rank, world, local_rank):
         total_ms = float(t.item())
     units = ns * n_gas * args.steps * world
     value = units / (total_ms * 1e-3) / 1e6
-    gas_ms = ms_gas / max(timed, 1)
+    step_kernel_ms = ms_step / max(timed, 1)
     alg_bytes = BYTES_PER_SPECIES_NODE * ns * n_gas
-    achieved = alg_bytes / (gas_ms * 1e-3) / 1e9
+    achieved = alg_bytes / (step_kernel_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
 
     e2e = None
@@ -287,14 +287,13 @@ def run_fdlbm(args, rank, world, local_rank):
                        "species": ns, "gas_nodes": n_gas, "wall_nodes": info["n_wall"],
                        "solid_nodes": info["n_solid"], "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
-            "roofline": {"bound": "hbm", "kernel": "gas_kernel", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(),
                          "peak_kind": peak_kind + " copy bandwidth",
-                         "alg_bytes_per_launch": alg_bytes, "gas_ms_per_launch": gas_ms,
-                         "solid_ms_per_launch": ms_solid / max(timed, 1)},
+                         "alg_bytes_per_launch": alg_bytes, "kernel_ms_per_launch": step_kernel_ms},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": args.steps,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -201,9 +201,9 @@ fdlbm_status fdlbm_set_fields(fdlbm_handle* h, const fdlbm_fields* f);
 fdlbm_status fdlbm_info(const fdlbm_handle* h, fdlbm_info_t* out);
 
 /* Kernel timing for benchmarks. With enable != 0, fdlbm_step records CUDA events on the
- * handle's stream around the solid kernel and the gas kernel of each step (at most
+ * handle's stream around the step kernel of each step (one launch per step; at most
  * 65536 steps are kept). fdlbm_kernel_times waits for the stream, writes the summed
- * milliseconds {solid, gas} and the number of timed steps, and clears the record. */
+ * milliseconds {step kernel, 0} and the number of timed steps, and clears the record. */
 fdlbm_status fdlbm_profile(fdlbm_handle* h, int enable);
 fdlbm_status fdlbm_kernel_times(fdlbm_handle* h, double* ms_out2, int64_t* steps_out);
 

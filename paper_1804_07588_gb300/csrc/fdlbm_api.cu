@@ -5,6 +5,7 @@
 // classifies nodes, precomputes the streaming stencil of every pull (Sec. 4.2 and the
 // near-wall readings), builds the solid-node list (interface wall nodes first) and
 // initialises the device state. Kernels live in fdlbm_kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -347,6 +348,32 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     for (int x = 0; x < nx; ++x)
       if (G.cls[x + nx * y] == GAS) gas_list.push_back((x + XOFF) + (y + YOFF) * P.pitch);
   P.n_gas = (int)gas_list.size();
+  // Step-kernel blocks, interleaved by bands of 8 rows: the gas blocks of a band, then
+  // the wall blocks of the same band; the interior solid blocks come last.
+  std::vector<int4> blocks;
+  {
+    std::vector<int> gas_row(ny + 1, 0), wall_row(ny + 1, 0);
+    for (int y = 0, g = 0, w = 0; y <= ny; ++y) {
+      gas_row[y] = g;
+      wall_row[y] = w;
+      if (y == ny) break;
+      for (int x = 0; x < nx; ++x) {
+        g += G.cls[x + nx * y] == GAS;
+        w += G.cls[x + nx * y] == WALL;
+      }
+    }
+    auto chunks = [&](int role, int first, int last) {
+      for (int s0 = first; s0 < last; s0 += STEP_BLOCK) blocks.push_back(make_int4(role, s0, std::min(STEP_BLOCK, last - s0), 0));
+    };
+    const int band = 8;
+    for (int y0 = 0; y0 < ny; y0 += band) {
+      const int y1 = std::min(ny, y0 + band);
+      chunks(0, gas_row[y0], gas_row[y1]);
+      chunks(1, wall_row[y0], wall_row[y1]);
+    }
+    chunks(1, (int)walls.size(), (int)solid_list.size());
+  }
+  P.n_blocks = (int)blocks.size();
   P.ns = ns;
   P.periodic_x = G.px;
   P.periodic_y = G.py;
@@ -462,10 +489,11 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.code, uint32_t, P.plane);
   ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
   ALLOC(S.gas_list, int32_t, std::max<size_t>(gas_list.size(), 1));
+  ALLOC(S.blocks, int4, std::max<size_t>(blocks.size(), 1));
   ALLOC(S.F[0], float, (size_t)(ns + 1) * P.plane);
   ALLOC(S.F[1], float, (size_t)(ns + 1) * P.plane);
   ALLOC(S.mom, float, (size_t)(ns + 3) * n);
-  ALLOC(S.Tgas, float, n);
+  ALLOC(S.Tgas, float, 2 * (size_t)n);
   ALLOC(S.snap, float, (size_t)(ns + 4) * n);
   ALLOC(S.ledger, double, (size_t)LG_COUNT * ledger_slots(P));
   ALLOC(S.flags, int, 4);
@@ -477,6 +505,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (e == cudaSuccess && !solid_list.empty())
     e = cudaMemcpyAsync(S.solid_list, solid_list.data(), sizeof(int32_t) * solid_list.size(),
                         cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !blocks.empty())
+    e = cudaMemcpyAsync(S.blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && !gas_list.empty())
     e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int32_t) * gas_list.size(), cudaMemcpyHostToDevice,
                         h->stream);
@@ -499,14 +529,12 @@ fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n) {
   if (!h || n < 0) return fail(FDLBM_EINVAL, "bad handle or step count");
   DeviceGuard guard(h->device);
   for (int64_t k = 0; k < n; ++k) {
-    if (h->profiling && h->events_used + 3 <= h->events.size()) {
+    if (h->profiling && h->events_used + 2 <= h->events.size()) {
       cudaEvent_t* ev = h->events.data() + h->events_used;
       CK(cudaEventRecord(ev[0], h->stream), "event record");
-      CK(launch_solid(h->P, h->S, h->cur, h->stream), "solid launch");
+      CK(launch_step(h->P, h->S, h->cur, false, h->stream), "step launch");
       CK(cudaEventRecord(ev[1], h->stream), "event record");
-      CK(launch_gas(h->P, h->S, h->cur, h->stream), "gas launch");
-      CK(cudaEventRecord(ev[2], h->stream), "event record");
-      h->events_used += 3;
+      h->events_used += 2;
     } else {
       CK(launch_step(h->P, h->S, h->cur, false, h->stream), "step launch");
     }
@@ -743,7 +771,7 @@ fdlbm_status fdlbm_profile(fdlbm_handle* h, int enable) {
   if (!h) return fail(FDLBM_EINVAL, "bad handle");
   DeviceGuard guard(h->device);
   if (enable && h->events.empty()) {
-    h->events.resize(3 * 65536);
+    h->events.resize(2 * 65536);
     for (auto& e : h->events) CK(cudaEventCreate(&e), "event create");
   }
   h->profiling = enable != 0;
@@ -755,17 +783,15 @@ fdlbm_status fdlbm_kernel_times(fdlbm_handle* h, double* ms_out2, int64_t* steps
   if (!h || !ms_out2) return fail(FDLBM_EINVAL, "bad handle or output");
   DeviceGuard guard(h->device);
   CK(cudaStreamSynchronize(h->stream), "stream sync");
-  double solid = 0.0, gas = 0.0;
-  for (size_t k = 0; k + 3 <= h->events_used; k += 3) {
-    float a = 0.f, b = 0.f;
+  double step = 0.0;
+  for (size_t k = 0; k + 2 <= h->events_used; k += 2) {
+    float a = 0.f;
     CK(cudaEventElapsedTime(&a, h->events[k], h->events[k + 1]), "event time");
-    CK(cudaEventElapsedTime(&b, h->events[k + 1], h->events[k + 2]), "event time");
-    solid += a;
-    gas += b;
+    step += a;
   }
-  ms_out2[0] = solid;
-  ms_out2[1] = gas;
-  if (steps_out) *steps_out = (int64_t)(h->events_used / 3);
+  ms_out2[0] = step;
+  ms_out2[1] = 0.0;
+  if (steps_out) *steps_out = (int64_t)(h->events_used / 2);
   h->events_used = 0;
   return FDLBM_OK;
 }

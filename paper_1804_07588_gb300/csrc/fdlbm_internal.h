@@ -42,6 +42,7 @@ struct DevParams {
   int periodic_x, periodic_y;
   int n_solid_list, n_wall_list;  // solid list: wall nodes first
   int n_gas;            // gas-node list length
+  int n_blocks;         // blocks of the fused step kernel
   int energy_correction, coupling;
   int fixedT_face[4];   // x-, x+, y-, y+
   // species
@@ -79,8 +80,9 @@ struct DevState {
   int32_t* solid_list;  // wall nodes first, then interior solid nodes (compact indices)
   int32_t* gas_list;    // gas nodes, row-major (padded indices)
   float* F[2];          // moment fields [1 + ns][plane]: dTg, K_j (ping-pong with h)
+  int4* blocks;         // step-kernel block descriptors {role (0 gas, 1 solid), first, count, 0}
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
-  float* Tgas;          // gas temperature of the current time (lattice), [n]
+  float* Tgas;          // gas temperature (lattice) for the paper coupling, [2][n] ping-pong with h
   float* snap;          // residual snapshot [(ns + 4)][n]
   double* ledger;       // FP64 ledger accumulators, LG_COUNT per solid-kernel block
   int* flags;           // sticky error flags
@@ -100,10 +102,9 @@ cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, 
 // recomputes the pre-collision moments of the step that read src into S.mom instead.
 cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only,
                         cudaStream_t st);
-// The two kernels of a step, separately (for per-kernel timing).
-cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st);
-cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st);
-// Per-block ledger slots of the solid kernel and their sum (LG_COUNT doubles into out).
+// Gas-role block size of the step kernel (threads per block).
+constexpr int STEP_BLOCK = 256;
+// Per-block ledger slots of the step kernel and their sum (LG_COUNT doubles into out).
 int ledger_slots(const DevParams& P);
 cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st);
 cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst,

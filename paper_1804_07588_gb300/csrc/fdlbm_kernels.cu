@@ -8,12 +8,13 @@
 // nodes: a node within GHOST of a periodic face also writes its populations into the
 // ghost copy on the other side, so every pull is a plain linear offset.
 //
-// Per time step (both kernels read time level t only):
-//   solid_kernel: interface (wall) nodes stream in the populations arriving from the gas,
+// One time step is one launch of step_kernel, whose blocks take a gas or a solid role
+// (both read time level t only):
+//   solid role: interface (wall) nodes stream in the populations arriving from the gas,
 //     iterate the wall density with the surface reaction (Sec. 4.3, Eq. BC_gji), emit the
 //     unknown populations and apply the FD heat step with the interface coupling and the
 //     reaction heat (Sec. 5); interior solid nodes apply the FD step only.
-//   gas_kernel: one thread per entry of a compact list of gas nodes: fused pull streaming
+//   gas role: one thread per entry of a compact list of gas nodes: fused pull streaming
 //     with the off-lattice interpolation (Sec. 4.2) into thread-private shared memory,
 //     moments (Eq. moments_of_g), divergence of the energy-correction flux from the
 //     moment field of the previous time level, two-step collision (Eq.
@@ -258,18 +259,11 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // src / Fsrc into mom[] at compact indices; writes nothing else).
 // Moment field F: [1 + NS][plane]: dTg and K_j = kcoef_j C_j T_g of every gas node.
 template <int NS, bool PHI, int MODE>
-__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, const float* __restrict__ src,
-                                                    float* __restrict__ dst, const uint32_t* __restrict__ code,
-                                                    const int32_t* __restrict__ gas_list,
-                                                    const float* __restrict__ Fsrc, float* __restrict__ Fdst,
-                                                    float* __restrict__ mom, float* __restrict__ Tgas,
-                                                    int* __restrict__ flags) {
-  extern __shared__ float smem[];
-  float* s_h = smem;  // [NS * Q][GB], thread-private columns (MODE 0)
-  const int tid = threadIdx.x;
-  const int t = blockIdx.x * GB + tid;
-  if (t >= P.n_gas) return;
-  const int k = __ldg(gas_list + t);
+__device__ __forceinline__ void gas_node(const DevParams& P, const float* __restrict__ src, float* __restrict__ dst,
+                                         const uint32_t* __restrict__ code, int k,
+                                         const float* __restrict__ Fsrc, float* __restrict__ Fdst,
+                                         float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags,
+                                         float* __restrict__ s_h, int tid) {
   const uint32_t cw = __ldg(code + k);
   const int px = k % P.pitch;
   const int gx = px - P.xoff, gy = k / P.pitch - P.yoff;
@@ -427,6 +421,20 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, co
   }
 }
 
+template <int NS, bool PHI, int MODE>
+__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, const float* __restrict__ src,
+                                                                 float* __restrict__ dst,
+                                                                 const uint32_t* __restrict__ code,
+                                                                 const int32_t* __restrict__ gas_list,
+                                                                 const float* __restrict__ Fsrc,
+                                                                 float* __restrict__ Fdst, float* __restrict__ mom,
+                                                                 float* __restrict__ Tgas, int* __restrict__ flags) {
+  extern __shared__ float smem[];
+  const int t = blockIdx.x * GB + threadIdx.x;
+  if (t >= P.n_gas) return;
+  gas_node<NS, PHI, MODE>(P, src, dst, code, __ldg(gas_list + t), Fsrc, Fdst, mom, Tgas, flags, smem, threadIdx.x);
+}
+
 template <int NS, int MODE>
 size_t gas_smem_bytes() {
   return sizeof(float) * (MODE == 0 ? (NS * Q + 4 * NS) * GB : 1);
@@ -476,22 +484,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-constexpr int SOLID_BLOCK = 128;
-
+// One solid node (compact index n): FD heat step; interface wall nodes also run the
+// reactive diffusive wall. Ledger increments accumulate into acc (Q_rxn, Q_wall,
+// Q_couple, Q_fixedT, non-converged iterations).
 template <int NS>
-__global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const float* __restrict__ src,
-                                                            float* __restrict__ dst,
-                                                            const float* __restrict__ Ts_src,
-                                                            float* __restrict__ Ts_dst,
-                                                            const uint32_t* __restrict__ code,
-                                                            const int32_t* __restrict__ list,
-                                                            const float* __restrict__ Tgas,
-                                                            double* __restrict__ ledger) {
-  __shared__ double sh[SOLID_BLOCK / 32];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc_q = 0.0, acc_w = 0.0, acc_c = 0.0, acc_f = 0.0, acc_nc = 0.0;
-  if (t < P.n_solid_list) {
-    const int n = __ldg(list + t);  // compact index
+__device__ __forceinline__ void solid_node(const DevParams& P, const float* __restrict__ src, float* __restrict__ dst,
+                                           const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
+                                           const uint32_t* __restrict__ code, const float* __restrict__ Tgas, int n,
+                                           double (&acc)[LG_COUNT]) {
+  {
     const int x = n % P.nx, y = n / P.nx;
     const int k = pad_index(P, x, y);
     const uint32_t cw = __ldg(code + k);
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
         const int face = d == 0 ? 1 : d == 1 ? 0 : d == 2 ? 3 : 2;
         if (P.fixedT_face[face]) {
           lap += P.dTout - Tx;
-          acc_f += double(P.rhocp_s) * double(P.alpha_s) * double(P.dTout - Tx);
+          acc[LG_QFIXEDT] += double(P.rhocp_s) * double(P.alpha_s) * double(P.dTout - Tx);
         }
         continue;
       }
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
           }
           if (d <= fmaxf(P.rho_w_tol, 4.f * FLT_EPSILON * rmax)) { conv = true; break; }
         }
-        if (!conv) acc_nc += 1.0;
+        if (!conv) acc[LG_NOCONV] += 1.0;
         rates<NS>(P, rw, kr, rate);
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
@@ -601,27 +602,59 @@ __global__ void __launch_bounds__(SOLID_BLOCK) solid_kernel(DevParams P, const f
       const float dE = Eout - Earr;
       const float couple = P.coupling == FDLBM_COUPLING_PAPER ? P.kappa_f * gas_term : -dE;
       Tn += (q + couple) * P.inv_rhocp_s;
-      acc_q = q;
-      acc_w = dE;
-      acc_c = couple;
+      acc[LG_QRXN] += q;
+      acc[LG_QWALL] += dE;
+      acc[LG_QCOUPLE] += couple;
     }
     Ts_dst[n] = Tn;
   }
-  // Block-reduce the FP64 ledger increments into this block's own accumulator slots
-  // (no atomics; the slots are summed when the ledger is read).
-  const double s_q = block_sum(acc_q, sh);
-  const double s_w = block_sum(acc_w, sh);
-  const double s_c = block_sum(acc_c, sh);
-  const double s_f = block_sum(acc_f, sh);
-  const double s_n = block_sum(acc_nc, sh);
-  if (threadIdx.x == 0) {
-    double* slot = ledger + (long long)blockIdx.x * LG_COUNT;
-    if (s_q != 0.0) slot[LG_QRXN] += s_q;
-    if (s_w != 0.0) slot[LG_QWALL] += s_w;
-    if (s_c != 0.0) slot[LG_QCOUPLE] += s_c;
-    if (s_f != 0.0) slot[LG_QFIXEDT] += s_f;
-    if (s_n != 0.0) slot[LG_NOCONV] += s_n;
+}
+
+// Block-level sum of the LG_COUNT ledger increments into this block's own slot (no
+// atomics; the slots are summed when the ledger is read).
+__device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], double* __restrict__ slot) {
+  __shared__ double sh[LG_COUNT][GB / 32];
+#pragma unroll
+  for (int q = 0; q < LG_COUNT; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < LG_COUNT; ++q) sh[q][warp] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < LG_COUNT) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
+    if (v != 0.0) slot[threadIdx.x] += v;
   }
+}
+
+// One time step in one launch. Every block takes a role from its descriptor {role,
+// first list entry, count}: gas blocks run the gas update of consecutive gas nodes,
+// solid blocks the wall + FD update of consecutive solid nodes. The host interleaves
+// the descriptors by row bands so that wall blocks follow the gas blocks of the same
+// rows and find their neighbours' populations in L2.
+template <int NS, bool PHI>
+__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
+    DevParams P, const float* __restrict__ src, float* __restrict__ dst, const uint32_t* __restrict__ code,
+    const int32_t* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
+    const float* __restrict__ Fsrc, float* __restrict__ Fdst, const float* __restrict__ Ts_src,
+    float* __restrict__ Ts_dst, const float* __restrict__ Tgas_src, float* __restrict__ Tgas_dst,
+    double* __restrict__ ledger, int* __restrict__ flags) {
+  extern __shared__ float smem[];
+  const int4 d = __ldg(blocks + blockIdx.x);
+  const int tid = threadIdx.x;
+  if (d.x == 0) {
+    if (tid < d.z)
+      gas_node<NS, PHI, 0>(P, src, dst, code, __ldg(gas_list + d.y + tid), Fsrc, Fdst, nullptr, Tgas_dst, flags,
+                           smem, tid);
+    return;
+  }
+  double acc[LG_COUNT];
+#pragma unroll
+  for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
+  if (tid < d.z) solid_node<NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc);
+  ledger_block_store(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
 // Sum of the per-block ledger slots.
@@ -707,7 +740,7 @@ __global__ void init_kernel(DevParams P, float* __restrict__ h0, float* __restri
       mom[(long long)P.ns * P.n + n] = float(ux);
       mom[(long long)(P.ns + 1) * P.n + n] = float(uy);
       mom[(long long)(P.ns + 2) * P.n + n] = float(T);
-      Tgas[n] = float(T);
+      Tgas[n] = Tgas[P.n + n] = float(T);
     }
   } else if (c == WALL || c == SOLID) {
     const double Ts = Tsl[n];
@@ -865,17 +898,6 @@ __global__ void residual_kernel(DevParams P, const float* __restrict__ mom, cons
     for (int f = 0; f < nf; ++f) snap[f * N + n] = cur[f];
 }
 
-template <int NS>
-cudaError_t solid_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  if (P.n_solid_list <= 0) return cudaSuccess;
-  const int dstb = 1 - src;
-  float* Tg = P.coupling == FDLBM_COUPLING_PAPER ? S.Tgas : nullptr;
-  const int nb = (P.n_solid_list + SOLID_BLOCK - 1) / SOLID_BLOCK;
-  solid_kernel<NS><<<nb, SOLID_BLOCK, 0, st>>>(P, S.h[src], S.h[dstb], S.Ts[src], S.Ts[dstb], S.code,
-                                               S.solid_list, Tg, S.ledger);
-  return cudaGetLastError();
-}
-
 template <int NS, bool PHI, int MODE>
 cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
   if (P.n_gas <= 0) return cudaSuccess;
@@ -892,7 +914,7 @@ cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStrea
   }
   const int dstb = 1 - src;
   const int grid = (P.n_gas + GB - 1) / GB;
-  float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas : nullptr;
+  float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas + (long long)dstb * P.n : nullptr;
   gas_kernel<NS, PHI, MODE><<<grid, GB, smem, st>>>(P, S.h[src], S.h[dstb], S.code, S.gas_list, S.F[src], S.F[dstb],
                                                     MODE == 1 ? S.mom : nullptr, Tg, S.flags);
   return cudaGetLastError();
@@ -917,14 +939,37 @@ cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, bool mo
   }
 }
 
-cudaError_t dispatch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+template <int NS, bool PHI>
+cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+  if (P.n_blocks <= 0) return cudaSuccess;
+  const size_t smem = gas_smem_bytes<NS, 0>();
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    e = cudaFuncSetAttribute(step_kernel<NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  const int dstb = 1 - src;
+  const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
+  step_kernel<NS, PHI><<<P.n_blocks, GB, smem, st>>>(
+      P, S.h[src], S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
+      paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
+      S.flags);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_step(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
+  const bool phi = P.energy_correction != 0;
   switch (P.ns) {
-    case 1: return solid_ns<1>(P, S, src, st);
-    case 2: return solid_ns<2>(P, S, src, st);
-    case 3: return solid_ns<3>(P, S, src, st);
-    case 4: return solid_ns<4>(P, S, src, st);
-    case 5: return solid_ns<5>(P, S, src, st);
-    case 6: return solid_ns<6>(P, S, src, st);
+    case 1: return phi ? step_launch<1, true>(P, S, src, st) : step_launch<1, false>(P, S, src, st);
+    case 2: return phi ? step_launch<2, true>(P, S, src, st) : step_launch<2, false>(P, S, src, st);
+    case 3: return phi ? step_launch<3, true>(P, S, src, st) : step_launch<3, false>(P, S, src, st);
+    case 4: return phi ? step_launch<4, true>(P, S, src, st) : step_launch<4, false>(P, S, src, st);
+    case 5: return phi ? step_launch<5, true>(P, S, src, st) : step_launch<5, false>(P, S, src, st);
+    case 6: return phi ? step_launch<6, true>(P, S, src, st) : step_launch<6, false>(P, S, src, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -944,20 +989,10 @@ cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, 
 
 cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st) {
   if (moments_only) return dispatch_gas(P, S, src, true, st);
-  cudaError_t e = dispatch_solid(P, S, src, st);
-  if (e != cudaSuccess) return e;
-  return dispatch_gas(P, S, src, false, st);
+  return dispatch_step(P, S, src, st);
 }
 
-cudaError_t launch_solid(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  return dispatch_solid(P, S, src, st);
-}
-
-cudaError_t launch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  return dispatch_gas(P, S, src, false, st);
-}
-
-int ledger_slots(const DevParams& P) { return P.n_solid_list > 0 ? (P.n_solid_list + SOLID_BLOCK - 1) / SOLID_BLOCK : 1; }
+int ledger_slots(const DevParams& P) { return P.n_blocks > 0 ? P.n_blocks : 1; }
 
 cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st) {
   ledger_sum_kernel<<<1, 32, 0, st>>>(S.ledger, ledger_slots(P), out);

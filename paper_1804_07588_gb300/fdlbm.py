@@ -286,11 +286,11 @@ class Solver:
         _check(load().fdlbm_profile(self._h, int(bool(enable))))
 
     def kernel_times(self):
-        """(ms solid kernel, ms gas kernel, timed steps) summed since profile()."""
+        """(ms of the step kernel summed since profile(), timed steps)."""
         ms = (C.c_double * 2)()
         n = C.c_int64()
         _check(load().fdlbm_kernel_times(self._h, ms, C.byref(n)))
-        return ms[0], ms[1], n.value
+        return ms[0], n.value
 
     def info(self) -> dict:
         i = Info()
