@@ -307,9 +307,16 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       } else if (c == SOLID) {
         solids.push_back(k);
       }
+      // Bits 28..31: gas nodes flag gas neighbours, solid nodes flag solid neighbours,
+      // along directions 1..4.
       if (c == GAS)
         for (int i = 1; i <= 4; ++i)
           if (G.cls_at(x + HEX[i], y + HEY[i]) == GAS) w |= 1u << (NBR_GAS_SHIFT + i - 1);
+      if (c == WALL || c == SOLID)
+        for (int i = 1; i <= 4; ++i) {
+          const uint32_t cn = G.cls_at(x + HEX[i], y + HEY[i]);
+          if (cn == WALL || cn == SOLID) w |= 1u << (NBR_GAS_SHIFT + i - 1);
+        }
       h->code[k] = w;
       h->counts[c]++;
     }

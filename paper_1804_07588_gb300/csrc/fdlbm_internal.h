@@ -25,7 +25,8 @@ enum Stencil : uint32_t { ST_NONE = 0, ST_CENTRAL = 1, ST_FORWARD = 2, ST_BACKWA
                           ST_LIN_S0 = 4, ST_LIN_S2 = 5, ST_NOT_ARRIVAL = 7 };
 constexpr uint32_t CATALYTIC_BIT = 1u << 3;
 constexpr int STENCIL_SHIFT = 4;
-// Bits 28..31: gas node has a gas neighbour along direction 1..4 (+x, +y, -x, -y).
+// Bits 28..31: a gas node has a gas neighbour, a solid (wall or interior) node a solid
+// neighbour, along direction 1..4 (+x, +y, -x, -y).
 constexpr int NBR_GAS_SHIFT = 28;
 
 __host__ __device__ inline uint32_t node_class(uint32_t code) { return code & 7u; }

@@ -502,6 +502,13 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
     for (int d = 0; d < 4; ++d) {
       const int ox = d == 0 ? 1 : d == 1 ? -1 : 0;
       const int oy = d == 2 ? 1 : d == 3 ? -1 : 0;
+      // neighbour class bits of solid nodes: bit NBR_GAS_SHIFT + (i - 1) set for a solid
+      // neighbour along direction i = 1..4 (+x, +y, -x, -y)
+      const int i = d == 0 ? 1 : d == 1 ? 3 : d == 2 ? 2 : 4;
+      if ((cw >> (NBR_GAS_SHIFT + i - 1)) & 1u) {
+        lap += Ts_src[lat_index(P, x + ox, y + oy)] - Tx;
+        continue;
+      }
       const int nb = lat_index(P, x + ox, y + oy);
       if (nb < 0) {
         const int face = d == 0 ? 1 : d == 1 ? 0 : d == 2 ? 3 : 2;
@@ -511,9 +518,8 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
         }
         continue;
       }
-      const uint32_t c = node_class(__ldg(code + k + ox + oy * P.pitch));
-      if (c == WALL || c == SOLID) lap += Ts_src[nb] - Tx;
-      else if (c == GAS && Tgas != nullptr) gas_term += Tgas[nb] - (P.Tref + Tx);
+      if (Tgas != nullptr && node_class(__ldg(code + k + ox + oy * P.pitch)) == GAS)
+        gas_term += Tgas[nb] - (P.Tref + Tx);
     }
     float Tn = fmaf(P.alpha_s, lap, Tx);
     if (node_class(cw) == WALL) {
@@ -530,15 +536,33 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
       float Earr = 0.f;
 #pragma unroll
       for (int j = 0; j < NS; ++j) A[j] = 0.f;
+      // Populations arriving from the gas: all lanes of a warp step through the directions
+      // together, so that their loads of one direction plane coalesce; branch-free
+      // stencils, loads of all species issued together.
 #pragma unroll 1
       for (int i = 1; i < Q; ++i) {
         if (!(arr & (1u << i))) continue;
         const int off = EX(i) + EY(i) * P.pitch;
-        const uint32_t st = stencil_of(cw, i);
+        const StencilCoef sc = stencil_coef(stencil_of(cw, i));
+        const int dA = sc.mA * off, dB = sc.mB * off;
         const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
+        float v1[NS], vA[NS], vB[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          const float v = pull_one(P, src, (j * Q + i) * (int)P.plane + k, off, st, j) + P.rref[j] * P.W0[i];
+          const int b = (j * Q + i) * (int)P.plane + k;
+          v1[j] = __ldg(src + (b - off));
+          vA[j] = __ldg(src + (b + dA));
+          vB[j] = __ldg(src + (b + dB));
+        }
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          float v = v1[j];
+          if (!P.onlattice[j]) {
+            const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1[j];
+            const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1[j];
+            v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
+          }
+          v += P.rref[j] * P.W0[i];
           A[j] += v;
           Earr = fmaf(e2h * P.c2[j], v, Earr);
         }
@@ -584,6 +608,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
       float scale[NS];
 #pragma unroll
       for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iB;
+      // Emissions towards the gas neighbours (the directions opposite to the arrivals).
 #pragma unroll 1
       for (int i = 1; i < Q; ++i) {
         if (!(arr & (1u << OPP(i)))) continue;
