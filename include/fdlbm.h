@@ -194,6 +194,39 @@ fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out);
  * then; synchronous. */
 fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out);
 
+/* Allocation-free totals. The paper has no counterpart: this is a library facility.
+ *
+ * Writes the conserved totals of the current time to the host array out (out_len >=
+ * 2 + 2 n_species doubles): {E_gas, H_solid, mass[ns], moles[ns]}, the same quantities
+ * and units as the members of fdlbm_balance filled by fdlbm_enthalpy_balance, which
+ * sums them through the handle's own scratch with atomics. This call reduces in a fixed
+ * order (per-block partial sums, then one pass over the blocks), so repeated calls on
+ * the same state return identical bits.
+ *
+ * It allocates no device memory: the partial sums live in one library-wide device
+ * array of FDLBM_STATIC_SCRATCH_BYTES, reserved when the library is loaded. It is for
+ * callers that must not allocate at the point of the call: a monitor that polls the
+ * totals while every free byte of the device is held by resident lattices; a caller
+ * that must not stall its other streams, since freeing device memory waits for the
+ * whole device; and code that runs on a thread where the Python caching allocator
+ * must not be entered. A call issues one moments relaunch (if the moments are stale),
+ * two reduction kernels and one device-to-host copy on the handle's stream, then
+ * waits for that stream.
+ *
+ * Limit: the lattice must satisfy (ceil(nx ny / 256) + 1)(2 + 2 ns) x 8 bytes <=
+ * FDLBM_STATIC_SCRATCH_BYTES, e.g. nx ny <= 698,368 for 5 species; larger lattices are
+ * rejected with EINVAL and a message giving both sizes. Nothing in the scratch has to
+ * start at zero: every slot the call reads was written earlier in the same call.
+ *
+ * The first call on a device looks up the scratch address on that device; make that
+ * first call before any stream capture on the device. The scratch is shared by all
+ * handles on a device, so calls that overlap in time (from several host threads, or on
+ * several streams whose work is not ordered) race on it and may return wrong totals:
+ * serialise them. Errors: EINVAL (NULL arguments, out_len too small, lattice over the
+ * limit), ECUDA. */
+#define FDLBM_STATIC_SCRATCH_BYTES 262144
+fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len);
+
 /* Re-initialise the gas (and solid) state from fields (warm start); NULL members keep
  * the defaults of fdlbm_create. The ledger is reset. */
 fdlbm_status fdlbm_set_fields(fdlbm_handle* h, const fdlbm_fields* f);

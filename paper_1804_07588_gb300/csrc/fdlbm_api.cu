@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -754,6 +755,48 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out) {
   h->have_snap = true;
   h->steps_at_residual = h->steps;
   *out = r;
+  return FDLBM_OK;
+}
+
+// Address of the static totals scratch, looked up once per device (with that device
+// current) and kept for the life of the process.
+namespace {
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mu;
+double* g_static_scratch[STATIC_MAX_DEVICES] = {};
+}  // namespace
+
+fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
+  if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
+  const int ns = h->ns, cnt = totals_count(ns);
+  if (out_len < cnt) return fail(FDLBM_EINVAL, "out_len %d < %d (2 + 2 n_species)", out_len, cnt);
+  const long long need = totals_static_doubles((long long)h->nx * h->ny, ns) * (long long)sizeof(double);
+  if (need > FDLBM_STATIC_SCRATCH_BYTES)
+    return fail(FDLBM_EINVAL,
+                "lattice %dx%d with %d species needs %lld bytes of static totals scratch, limit %d "
+                "(FDLBM_STATIC_SCRATCH_BYTES); use fdlbm_enthalpy_balance",
+                h->nx, h->ny, ns, need, FDLBM_STATIC_SCRATCH_BYTES);
+  if (h->device < 0 || h->device >= STATIC_MAX_DEVICES)
+    return fail(FDLBM_EINVAL, "device %d outside the %d devices the static scratch serves", h->device,
+                STATIC_MAX_DEVICES);
+  DeviceGuard guard(h->device);
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_scratch[h->device]) {
+      double* p = nullptr;
+      CK(totals_static_scratch(&p), "static totals scratch address");
+      g_static_scratch[h->device] = p;
+    }
+    scratch = g_static_scratch[h->device];
+  }
+  fdlbm_status st = ensure_moments(h);
+  if (st != FDLBM_OK) return st;
+  CK(launch_totals_static(h->P, h->S, h->cur, scratch, h->stream), "static totals launch");
+  const long long rows = (totals_static_doubles((long long)h->nx * h->ny, ns) / cnt) - 1;
+  CK(cudaMemcpyAsync(out, scratch + rows * cnt, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream),
+     "read static totals");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
   return FDLBM_OK;
 }
 

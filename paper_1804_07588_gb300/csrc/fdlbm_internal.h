@@ -121,4 +121,17 @@ inline int totals_count(int ns) { return 2 + 2 * ns; }
 // per field: ||F - snap||^2 and ||F - ref||^2 for fields ux, uy, X_j, T, Ts.
 inline int residual_count(int ns) { return 2 * (ns + 4); }
 
+// Allocation-free totals: the same sums as launch_totals, reduced in a fixed order
+// through the library's static device scratch of FDLBM_STATIC_SCRATCH_BYTES.
+constexpr int TOTALS_STATIC_BLOCK = 256;
+// Doubles of scratch the reduction needs: one partial row per block plus the totals.
+inline long long totals_static_doubles(long long n_nodes, int ns) {
+  return ((n_nodes + TOTALS_STATIC_BLOCK - 1) / TOTALS_STATIC_BLOCK + 1) * totals_count(ns);
+}
+// Device address of the static scratch on the current device (cudaGetSymbolAddress).
+cudaError_t totals_static_scratch(double** out);
+// Partial sums into scratch[0, blocks * count), totals into the next count doubles.
+cudaError_t launch_totals_static(const DevParams& P, const DevState& S, int cur, double* scratch,
+                                 cudaStream_t st);
+
 }  // namespace fdlbm

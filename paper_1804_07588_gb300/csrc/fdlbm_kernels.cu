@@ -1054,4 +1054,106 @@ cudaError_t launch_residual(const DevParams& P, const DevState& S, int cur, cuda
   return cudaGetLastError();
 }
 
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free totals. The per-node sums are those of totals_kernel; each block
+// writes its partial sums to its own row of a fixed static scratch array (no atomics,
+// nothing to clear beforehand), and one block then adds the rows in block order, so the
+// result does not depend on the order in which blocks ran.
+
+// Partial sums of block b: E_gas, H_solid, mass[ns], moles[ns] at row b.
+__global__ void __launch_bounds__(TOTALS_STATIC_BLOCK)
+totals_partial_kernel(DevParams P, const float* __restrict__ mom, const float* __restrict__ h,
+                      const float* __restrict__ Ts, const uint32_t* __restrict__ code,
+                      double* __restrict__ part) {
+  __shared__ double sh[TOTALS_STATIC_BLOCK / 32];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ns = P.ns, cnt = 2 + 2 * ns;  // E_gas, H_solid, mass[ns], moles[ns]
+  const long long N = P.n;
+  double E = 0.0, H = 0.0, mass[MAX_NS], moles[MAX_NS];
+  for (int j = 0; j < ns; ++j) mass[j] = moles[j] = 0.0;
+  if (n < P.n) {
+    const int k = pad_index(P, n % P.nx, n / P.nx);
+    const uint32_t cw = code[k];
+    const uint32_t c = node_class(cw);
+    if (c == GAS) {
+      double C = 0.0, r = 0.0;
+      for (int j = 0; j < ns; ++j) {
+        const double rj = mom[j * N + n];
+        mass[j] = rj;
+        moles[j] = rj * double(P.invM[j]);
+        C += rj / double(P.M[j]);
+        r += rj;
+      }
+      const double ux = mom[ns * N + n], uy = mom[(ns + 1) * N + n], T = mom[(ns + 2) * N + n];
+      E = C * T + 0.5 * r * (ux * ux + uy * uy);
+    } else if (c == WALL || c == SOLID) {
+      H = double(P.rhocp_s) * (double(P.Tref) + double(Ts[n]));
+      if (c == WALL) {
+        // populations emitted by the wall and not yet streamed into the gas
+        for (int i = 1; i < Q; ++i) {
+          if (stencil_of(cw, OPP(i)) == ST_NOT_ARRIVAL) continue;
+          for (int j = 0; j < ns; ++j) {
+            const double w = double(h[(long long)(j * Q + i) * P.plane + k]) + double(P.rref[j]) * double(P.W0[i]);
+            mass[j] += w;
+            moles[j] += w / double(P.M[j]);
+            E += 0.5 * double(P.c2[j]) * double(EX(i) * EX(i) + EY(i) * EY(i)) * w;
+          }
+        }
+      }
+    }
+  }
+  double* row = part + (long long)blockIdx.x * cnt;
+  double s = block_sum(E, sh);
+  if (threadIdx.x == 0) row[0] = s;
+  s = block_sum(H, sh);
+  if (threadIdx.x == 0) row[1] = s;
+  for (int j = 0; j < ns; ++j) {
+    s = block_sum(mass[j], sh);
+    if (threadIdx.x == 0) row[2 + j] = s;
+    s = block_sum(moles[j], sh);
+    if (threadIdx.x == 0) row[2 + ns + j] = s;
+  }
+}
+
+static_assert(2 + 2 * MAX_NS <= 64, "one thread per totals column in a 64-thread block");
+
+// Column q of the partial rows summed in block order into out[q] (one thread per column).
+__global__ void totals_rows_kernel(const double* __restrict__ part, int rows, int cnt,
+                                   double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= cnt) return;
+  double s = 0.0;
+  for (int b = 0; b < rows; ++b) s += part[(long long)b * cnt + q];
+  out[q] = s;
+}
+
+}  // namespace
+
+// The scratch itself: FDLBM_STATIC_SCRATCH_BYTES reserved with the library's device
+// code, one copy per device. Reached only through totals_static_scratch.
+static __device__ __align__(256) double g_totals_static[FDLBM_STATIC_SCRATCH_BYTES / sizeof(double)];
+
+cudaError_t totals_static_scratch(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_totals_static);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
+  return cudaSuccess;
+}
+
+cudaError_t launch_totals_static(const DevParams& P, const DevState& S, int cur, double* scratch,
+                                 cudaStream_t st) {
+  const int cnt = totals_count(P.ns);
+  const int nb = (P.n + TOTALS_STATIC_BLOCK - 1) / TOTALS_STATIC_BLOCK;
+  if (totals_static_doubles(P.n, P.ns) * (long long)sizeof(double) > FDLBM_STATIC_SCRATCH_BYTES)
+    return cudaErrorInvalidValue;
+  if (nb > 0)
+    totals_partial_kernel<<<nb, TOTALS_STATIC_BLOCK, 0, st>>>(P, S.mom, S.h[cur], S.Ts[cur], S.code, scratch);
+  totals_rows_kernel<<<1, 64, 0, st>>>(scratch, nb, cnt, scratch + (long long)nb * cnt);
+  return cudaGetLastError();
+}
+
 }  // namespace fdlbm

@@ -89,7 +89,8 @@ class Balance(C.Structure):
 _lib = None
 EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_populations",
            "fdlbm_enthalpy_balance", "fdlbm_residual", "fdlbm_set_fields", "fdlbm_info",
-           "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_destroy", "fdlbm_last_error")
+           "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_totals_static", "fdlbm_destroy",
+           "fdlbm_last_error")
 
 
 def library_path() -> str:
@@ -118,6 +119,7 @@ def load(build_if_missing: bool = True):
     L.fdlbm_info.argtypes = [C.c_void_p, P(Info)]
     L.fdlbm_profile.argtypes = [C.c_void_p, C.c_int]
     L.fdlbm_kernel_times.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int64)]
+    L.fdlbm_totals_static.argtypes = [C.c_void_p, P(C.c_double), C.c_int]
     L.fdlbm_destroy.argtypes = [C.c_void_p]
     L.fdlbm_destroy.restype = None
     L.fdlbm_last_error.restype = C.c_char_p
@@ -276,6 +278,16 @@ class Solver:
         r = C.c_double()
         _check(load().fdlbm_residual(self._h, C.byref(r)))
         return r.value
+
+    def totals_static(self) -> dict:
+        """E_gas, H_solid, mass[ns], moles[ns] of the current time through the
+        allocation-free reduction (fixed-order sums in the library's static device
+        scratch); same quantities as balance(). Calls must not overlap in time."""
+        ns = self.ns
+        out = np.empty(2 + 2 * ns, np.float64)
+        _check(load().fdlbm_totals_static(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
+        return {"E_gas": float(out[0]), "H_solid": float(out[1]),
+                "mass": out[2:2 + ns].copy(), "moles": out[2 + ns:].copy()}
 
     def set_fields(self, init: dict):
         keep = []
