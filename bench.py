@@ -169,6 +169,21 @@ def oracle_throughput(seconds: float = 10.0, n_target: int = 16384, max_steps=No
     return ns * n_gas * steps / el / 1e6, f"{desc}, {steps} steps, {n_gas} gas nodes", el
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ns: int, n_gas: int, steps: int, world: int, total_ms: float) -> float:
+    """species-MLUPS of all replicas: every rank advances its own lattice `steps` times."""
+    return ns * n_gas * steps * world / (total_ms * 1e-3) / 1e6
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -241,12 +256,8 @@ def run_fdlbm(args, rank, world, local_rank):
     ms_step, timed = s.kernel_times()
     s.profile(False)
     s.sync()
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    units = ns * n_gas * args.steps * world
-    value = units / (total_ms * 1e-3) / 1e6
+    total_ms = max_over_ranks(total_ms, dist, device=f"cuda:{dev}")
+    value = whole_job_value(ns, n_gas, args.steps, world, total_ms)
     step_kernel_ms = ms_step / max(timed, 1)
     alg_bytes = BYTES_PER_SPECIES_NODE * ns * n_gas
     achieved = alg_bytes / (step_kernel_ms * 1e-3) / 1e9

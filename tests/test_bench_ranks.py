@@ -1,0 +1,69 @@
+"""The multi-rank logic of bench.py on CPU: two gloo ranks (replicas) agree on the
+slowest rank's time and report the whole job's throughput; the reference arm runs on
+rank 0 only."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    my_ms = [40.0, 55.0][rank]
+    t = bench.max_over_ranks(my_ms, dist)
+    v = bench.whole_job_value(5, 1000, 100, world, t)
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, t, v))
+
+
+def test_two_gloo_ranks_max_time_and_whole_job_value():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, v in res:
+        assert t == 55.0
+        # 2 ranks x 5 species x 1000 gas nodes x 100 steps in 55 ms
+        assert v == pytest.approx(2 * 5 * 1000 * 100 / 0.055 / 1e6)
+
+
+def test_single_rank_value_has_no_collective():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5) == 12.5
+    assert bench.whole_job_value(5, 313539, 1000, 1, 119.0) == pytest.approx(13173.9, rel=1e-4)
+
+
+def test_reference_arm_other_ranks_do_nothing(capsys):
+    import sys
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    args = argparse.Namespace(steps=1, warmup=0, gpus=2)
+    bench.run_reference(args, rank=1, world=2)
+    assert capsys.readouterr().out == ""
