@@ -49,7 +49,8 @@ typedef enum {
   FDLBM_EUNSTABLE = -4, /* the gas kernel saw a non-finite or non-positive density/temperature */
   FDLBM_ENOCONV = -5,   /* reserved: wall-density iteration cap reached (counted, see balance) */
   FDLBM_ETIMEOUT = -6,  /* reserved for bounded device waits */
-  FDLBM_ENOMEM = -7     /* device allocation failed */
+  FDLBM_ENOMEM = -7,    /* device allocation failed */
+  FDLBM_EIO = -8        /* checkpoint file missing, unreadable, truncated or not written */
 } fdlbm_status;
 
 enum { FDLBM_D2Q9 = 9 };
@@ -171,8 +172,10 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
                           const fdlbm_transport* tr, const fdlbm_kinetics* kin,
                           const fdlbm_fields* init, const fdlbm_options* opts, fdlbm_handle** out);
 
-/* Enqueue n >= 0 time steps on the handle's stream (asynchronous). Each step is the
- * wall + solid kernel (Sec. 4.3, Sec. 5) followed by the fused gas kernel (Sec. 4). */
+/* Enqueue n >= 0 time steps on the handle's stream (asynchronous). Each step is one
+ * launch of the fused step kernel: gas nodes (streaming, moments, corrections and
+ * collision, Sec. 4), interface wall nodes (reactive diffusive wall, Sec. 4.3) and
+ * solid nodes (FD heat step and coupling, Sec. 5) in one grid. */
 fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n);
 
 /* Wait for the handle's stream and report sticky device errors (EUNSTABLE). */
@@ -226,6 +229,17 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out);
  * limit), ECUDA. */
 #define FDLBM_STATIC_SCRATCH_BYTES 262144
 fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len);
+
+/* Checkpoint and restore (the paper has none: a library facility). fdlbm_save writes
+ * the state the next step reads (current populations, lagged moment field, solid
+ * temperature, moments, residual snapshot, ledger, step count) to the file at path;
+ * fdlbm_load restores it into a handle created from the same geometry, species,
+ * transport and kinetics (checked by a fingerprint of the node codes and device
+ * parameters: EINVAL otherwise). Steps after a load give the same bits as steps after
+ * the save on the saving handle. Both are synchronous; the file is host-endian.
+ * Errors: EINVAL, EIO, ECUDA. */
+fdlbm_status fdlbm_save(fdlbm_handle* h, const char* path);
+fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path);
 
 /* Re-initialise the gas (and solid) state from fields (warm start); NULL members keep
  * the defaults of fdlbm_create. The ledger is reset. */

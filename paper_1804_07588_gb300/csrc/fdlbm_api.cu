@@ -13,6 +13,7 @@
 #include <limits>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fdlbm_internal.h"
@@ -797,6 +798,143 @@ fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
   CK(cudaMemcpyAsync(out, scratch + rows * cnt, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream),
      "read static totals");
   CK(cudaStreamSynchronize(h->stream), "stream sync");
+  return FDLBM_OK;
+}
+
+// Checkpoint file: a fixed header, then the state the next step reads. Layout (native
+// little-endian): char magic[8] "FDLBMCK1"; u64 fingerprint; i32 nx, ny, ns, n_blocks;
+// i64 plane, steps, steps_at_residual; i32 have_snap, flags; f64 E0, H0, mass0[MAX_NS],
+// moles0[MAX_NS]; then FP32 h[cur] [ns][9][plane], F[cur] [1 + ns][plane], Ts[cur] [n],
+// Tgas[cur] [n], mom [ns + 3][n], snap [ns + 4][n], FP64 ledger [n_blocks][LG_COUNT].
+namespace {
+
+constexpr char CK_MAGIC[8] = {'F', 'D', 'L', 'B', 'M', 'C', 'K', '1'};
+
+// FNV-1a over the node code words and the device parameters: a checkpoint loads only
+// into a handle built from the same geometry, species, transport and kinetics.
+uint64_t fingerprint(const fdlbm_handle* h) {
+  uint64_t f = 1469598103934665603ull;
+  auto mix = [&f](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) f = (f ^ b[i]) * 1099511628211ull;
+  };
+  mix(h->code.data(), sizeof(uint32_t) * h->code.size());
+  mix(&h->P, sizeof(DevParams));
+  return f;
+}
+
+struct CkHeader {
+  char magic[8];
+  uint64_t fp;
+  int32_t nx, ny, ns, n_blocks;
+  int64_t plane, steps, steps_at_residual;
+  int32_t have_snap, flags;
+  double E0, H0, mass0[MAX_NS], moles0[MAX_NS];
+};
+
+// The device buffers of a checkpoint, in file order: {device pointer, bytes}.
+std::vector<std::pair<void*, size_t>> ck_buffers(fdlbm_handle* h) {
+  const DevParams& P = h->P;
+  const size_t n = (size_t)P.n, ns = (size_t)P.ns, plane = (size_t)P.plane;
+  return {{h->S.h[h->cur], sizeof(float) * ns * Q * plane},
+          {h->S.F[h->cur], sizeof(float) * (1 + ns) * plane},
+          {h->S.Ts[h->cur], sizeof(float) * n},
+          {h->S.Tgas + (size_t)h->cur * n, sizeof(float) * n},
+          {h->S.mom, sizeof(float) * (ns + 3) * n},
+          {h->S.snap, sizeof(float) * (ns + 4) * n},
+          {h->S.ledger, sizeof(double) * LG_COUNT * (size_t)ledger_slots(P)}};
+}
+
+}  // namespace
+
+fdlbm_status fdlbm_save(fdlbm_handle* h, const char* path) {
+  if (!h || !path) return fail(FDLBM_EINVAL, "bad handle or path");
+  DeviceGuard guard(h->device);
+  fdlbm_status st = ensure_moments(h);
+  if (st != FDLBM_OK) return st;
+  CkHeader hd{};
+  std::memcpy(hd.magic, CK_MAGIC, 8);
+  hd.fp = fingerprint(h);
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.ns = h->ns;
+  hd.n_blocks = ledger_slots(h->P);
+  hd.plane = h->P.plane;
+  hd.steps = h->steps;
+  hd.steps_at_residual = h->steps_at_residual;
+  hd.have_snap = h->have_snap ? 1 : 0;
+  CK(cudaMemcpyAsync(&hd.flags, h->S.flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
+  hd.E0 = h->E0;
+  hd.H0 = h->H0;
+  std::memcpy(hd.mass0, h->mass0, sizeof(hd.mass0));
+  std::memcpy(hd.moles0, h->moles0, sizeof(hd.moles0));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(FDLBM_EIO, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  std::vector<unsigned char> buf;
+  for (const auto& b : ck_buffers(h)) {
+    if (!ok) break;
+    buf.resize(b.second);
+    const cudaError_t e = cudaMemcpyAsync(buf.data(), b.first, b.second, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && cudaStreamSynchronize(h->stream) == cudaSuccess) {
+      ok = std::fwrite(buf.data(), 1, b.second, f) == b.second;
+    } else {
+      std::fclose(f);
+      return cuda_fail(e != cudaSuccess ? e : cudaGetLastError(), "read state for checkpoint");
+    }
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(FDLBM_EIO, "short write to %s", path);
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path) {
+  if (!h || !path) return fail(FDLBM_EINVAL, "bad handle or path");
+  DeviceGuard guard(h->device);
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(FDLBM_EIO, "cannot open %s", path);
+  CkHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, CK_MAGIC, 8) != 0) {
+    std::fclose(f);
+    return fail(FDLBM_EIO, "%s is not a solver checkpoint", path);
+  }
+  if (hd.fp != fingerprint(h) || hd.nx != h->nx || hd.ny != h->ny || hd.ns != h->ns ||
+      hd.n_blocks != ledger_slots(h->P) || hd.plane != h->P.plane) {
+    std::fclose(f);
+    return fail(FDLBM_EINVAL,
+                "checkpoint %s was written by a solver with another geometry or parameters "
+                "(%dx%d, %d species)", path, hd.nx, hd.ny, hd.ns);
+  }
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  std::vector<unsigned char> buf;
+  for (const auto& b : ck_buffers(h)) {
+    buf.resize(b.second);
+    if (std::fread(buf.data(), 1, b.second, f) != b.second) {
+      std::fclose(f);
+      return fail(FDLBM_EIO, "%s is truncated", path);
+    }
+    const cudaError_t e = cudaMemcpyAsync(b.first, buf.data(), b.second, cudaMemcpyHostToDevice, h->stream);
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamSynchronize(h->stream) : e;
+    if (e2 != cudaSuccess) {
+      std::fclose(f);
+      return cuda_fail(e2, "write checkpoint state");
+    }
+  }
+  std::fclose(f);
+  // The other population copy: nodes the step never rewrites (inlet) keep their values.
+  const size_t pop_bytes = sizeof(float) * (size_t)h->ns * Q * (size_t)h->P.plane;
+  CK(cudaMemcpyAsync(h->S.h[h->cur ^ 1], h->S.h[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream),
+     "copy populations");
+  CK(cudaMemcpyAsync(h->S.flags, &hd.flags, sizeof(int), cudaMemcpyHostToDevice, h->stream), "write flags");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  h->steps = hd.steps;
+  h->steps_at_residual = hd.steps_at_residual;
+  h->have_snap = hd.have_snap != 0;
+  h->mom_fresh = true;
+  h->E0 = hd.E0;
+  h->H0 = hd.H0;
+  std::memcpy(h->mass0, hd.mass0, sizeof(hd.mass0));
+  std::memcpy(h->moles0, hd.moles0, sizeof(hd.moles0));
   return FDLBM_OK;
 }
 

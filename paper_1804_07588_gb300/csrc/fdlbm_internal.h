@@ -41,7 +41,7 @@ struct DevParams {
   long long plane;      // elements of one padded plane (>= pitch * (ny + 2 yoff))
   int ns;
   int periodic_x, periodic_y;
-  int n_solid_list, n_wall_list;  // solid list: wall nodes first
+  int n_solid_list, n_wall_list;  // solid-list length, number of wall nodes
   int n_gas;            // gas-node list length
   int n_blocks;         // blocks of the fused step kernel
   int energy_correction, coupling;

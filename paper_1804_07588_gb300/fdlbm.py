@@ -18,7 +18,8 @@ MAX_NS = 6
 MAX_NR = 4
 Q = 9
 STATUS = {0: "FDLBM_OK", -1: "FDLBM_EINVAL", -2: "FDLBM_EGEOM", -3: "FDLBM_ECUDA",
-          -4: "FDLBM_EUNSTABLE", -5: "FDLBM_ENOCONV", -6: "FDLBM_ETIMEOUT", -7: "FDLBM_ENOMEM"}
+          -4: "FDLBM_EUNSTABLE", -5: "FDLBM_ENOCONV", -6: "FDLBM_ETIMEOUT", -7: "FDLBM_ENOMEM",
+          -8: "FDLBM_EIO"}
 
 
 class FdlbmError(RuntimeError):
@@ -89,8 +90,8 @@ class Balance(C.Structure):
 _lib = None
 EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_populations",
            "fdlbm_enthalpy_balance", "fdlbm_residual", "fdlbm_set_fields", "fdlbm_info",
-           "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_totals_static", "fdlbm_destroy",
-           "fdlbm_last_error")
+           "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_totals_static", "fdlbm_save",
+           "fdlbm_load", "fdlbm_destroy", "fdlbm_last_error")
 
 
 def library_path() -> str:
@@ -120,6 +121,8 @@ def load(build_if_missing: bool = True):
     L.fdlbm_profile.argtypes = [C.c_void_p, C.c_int]
     L.fdlbm_kernel_times.argtypes = [C.c_void_p, P(C.c_double), P(C.c_int64)]
     L.fdlbm_totals_static.argtypes = [C.c_void_p, P(C.c_double), C.c_int]
+    L.fdlbm_save.argtypes = [C.c_void_p, C.c_char_p]
+    L.fdlbm_load.argtypes = [C.c_void_p, C.c_char_p]
     L.fdlbm_destroy.argtypes = [C.c_void_p]
     L.fdlbm_destroy.restype = None
     L.fdlbm_last_error.restype = C.c_char_p
@@ -288,6 +291,14 @@ class Solver:
         _check(load().fdlbm_totals_static(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
         return {"E_gas": float(out[0]), "H_solid": float(out[1]),
                 "mass": out[2:2 + ns].copy(), "moles": out[2 + ns:].copy()}
+
+    def save(self, path: str):
+        """Checkpoint the state the next step reads to the file at path."""
+        _check(load().fdlbm_save(self._h, os.fsencode(path)))
+
+    def load_state(self, path: str):
+        """Restore a checkpoint written by a solver of the same problem."""
+        _check(load().fdlbm_load(self._h, os.fsencode(path)))
 
     def set_fields(self, init: dict):
         keep = []
