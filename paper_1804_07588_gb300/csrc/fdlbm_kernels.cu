@@ -201,6 +201,93 @@ __device__ __forceinline__ void pull_node(const DevParams& P, const float* __res
   pull_dir_all<NS, 8, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
 }
 
+// Asynchronous form of the pull for the full step: every thread first issues the 9 NS
+// loads of its upstream populations s1 = h_i(x - e_i) as cp.async copies into its own
+// shared-memory column (no registers held while they are in flight), then, once they
+// have landed, applies the interpolation with the two further stencil points of each
+// off-lattice species and accumulates the moments.
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int NS>
+__device__ __forceinline__ void issue_pulls(const DevParams& P, const float* __restrict__ src, int k,
+                                            float* __restrict__ s_h, int tid) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int off = EX(i) + EY(i) * P.pitch;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) cp_async4(s_h + (j * Q + i) * GB + tid, src + ((j * Q + i) * (int)P.plane + k - off));
+  }
+  cp_async_commit();
+}
+
+template <int NS, int I>
+__device__ __forceinline__ void interp_dir(const DevParams& P, const float* __restrict__ src, int k, uint32_t cw,
+                                           Acc<NS>& a, float* __restrict__ s_h, int tid,
+                                           const float (&ecoef)[3]) {
+  constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
+  if (I == 0) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const float v = s_h[(j * Q) * GB + tid];
+      a.dr[j] += v;
+      a.e[j] = fmaf(ecoef[0], v, a.e[j]);
+    }
+    return;
+  }
+  const int off = EX(I) + EY(I) * P.pitch;
+  const StencilCoef sc = stencil_coef(stencil_of(cw, I));
+  const int dA = sc.mA * off, dB = sc.mB * off;
+  float vA[NS], vB[NS];
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    vA[j] = vB[j] = 0.f;
+    if (!P.onlattice[j]) {
+      const int b = (j * Q + I) * (int)P.plane + k;
+      vA[j] = __ldg(src + (b + dA));
+      vB[j] = __ldg(src + (b + dB));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NS; ++j) {
+    const float v1 = s_h[(j * Q + I) * GB + tid];
+    float v = v1;
+    if (!P.onlattice[j]) {
+      const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1;
+      const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1;
+      v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1));
+      s_h[(j * Q + I) * GB + tid] = v;
+    }
+    a.dr[j] += v;
+    if (EX(I) > 0) a.ax[j] += v;
+    if (EX(I) < 0) a.ax[j] -= v;
+    if (EY(I) > 0) a.ay[j] += v;
+    if (EY(I) < 0) a.ay[j] -= v;
+    a.e[j] = fmaf(ecoef[e2], v, a.e[j]);
+  }
+}
+
+template <int NS>
+__device__ __forceinline__ void interp_node(const DevParams& P, const float* __restrict__ src, int k, uint32_t cw,
+                                            Acc<NS>& a, float* __restrict__ s_h, int tid) {
+  const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
+#pragma unroll
+  for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
+  interp_dir<NS, 0>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 1>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 2>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 3>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 4>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 5>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 6>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 7>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<NS, 8>(P, src, k, cw, a, s_h, tid, ecoef);
+}
+
 // Mixture moments from the species accumulators (Eq. moments_of_g, Eq. moments_of_f):
 // densities, momenta, C and the g-temperature deviation dTg = T_g - T_ref.
 template <int NS>
@@ -270,12 +357,15 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
 
   Acc<NS> acc;
   Mom<NS> m;
-  pull_node<NS, MODE == 0>(P, src, k, cw, acc, s_h, tid);
-  finish_moments<NS>(P, acc, m);
+  if (MODE == 0)
+    issue_pulls<NS>(P, src, k, s_h, tid);
+  else
+    pull_node<NS, false>(P, src, k, cw, acc, s_h, tid);
 
   // Divergence of the energy-correction flux K_j grad T on the 4 axis neighbours, from
   // the moment field of the previous time level (reading R8); faces to non-gas nodes
-  // carry no flux.
+  // carry no flux. Independent of this step's populations: computed while the pulls
+  // are in flight.
   float divq[NS];
   float sdq = 0.f;
 #pragma unroll
@@ -297,6 +387,11 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
 #pragma unroll
     for (int j = 0; j < NS; ++j) sdq += divq[j];
   }
+  if (MODE == 0) {
+    cp_async_wait_all();
+    interp_node<NS>(P, src, k, cw, acc, s_h, tid);
+  }
+  finish_moments<NS>(P, acc, m);
 
   const float ux = m.jx / m.r, uy = m.jy / m.r;
   const float dT = m.dTg + sdq / (4.f * m.C);
