@@ -41,6 +41,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nv = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
+    # extra nvcc flags, e.g. -DFDLBM_THREADS_PER_SM=1024 to change the register budget
+    flags += os.environ.get("FDLBM_NVCC_FLAGS", "").split()
     if verbose:
         flags += ["-Xptxas", "-v"]
 

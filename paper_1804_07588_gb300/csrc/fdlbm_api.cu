@@ -184,7 +184,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     return fail(FDLBM_EINVAL, "geometry, species, transport, kinetics and mask are required");
   if (geom->lattice != FDLBM_D2Q9) return fail(FDLBM_EINVAL, "only the D2Q9 lattice is supported");
   if (geom->nx < 4 || geom->ny < 4) return fail(FDLBM_EINVAL, "lattice must be at least 4x4 (got %dx%d)", geom->nx, geom->ny);
-  if ((long long)geom->nx * geom->ny > (1LL << 30)) return fail(FDLBM_EINVAL, "lattice too large");
+  if ((long long)geom->nx * geom->ny > (1LL << 29)) return fail(FDLBM_EINVAL, "lattice too large (at most 2^29 nodes)");
   if (n_species < 1 || n_species > MAX_NS) return fail(FDLBM_EINVAL, "n_species must be 1..%d", MAX_NS);
   if (kin->n_react < 0 || kin->n_react > MAX_NR) return fail(FDLBM_EINVAL, "n_react must be 0..%d", MAX_NR);
   const int* fb = geom->face_bc;
@@ -334,7 +334,13 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.yoff = YOFF;
   P.pitch = (nx + XOFF + 2 * GHOST + 31) / 32 * 32;
   P.plane = ((long long)P.pitch * (ny + 2 * YOFF) + 63) / 64 * 64;
-  std::vector<int32_t> gas_list;
+  // Kernels address populations with 32-bit element offsets.
+  if ((long long)ns * Q * P.plane >= (1LL << 31)) {
+    delete h;
+    return fail(FDLBM_EINVAL, "lattice too large: %d species x 9 x %lld padded cells exceed 2^31 elements",
+                ns, (long long)P.plane);
+  }
+  std::vector<int2> gas_list;
   gas_list.reserve((size_t)h->counts[GAS]);
   // Code words on the padded lattice: ghost cells within GHOST of a periodic face carry
   // the wrapped node's word, everything else outside the lattice is OUTSIDE.
@@ -355,7 +361,13 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   // Gas nodes row-major: a warp writes contiguous runs of every population plane.
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x)
-      if (G.cls[x + nx * y] == GAS) gas_list.push_back((x + XOFF) + (y + YOFF) * P.pitch);
+      if (G.cls[x + nx * y] == GAS) {
+        const bool near_x = G.px && (x < GHOST || x >= nx - GHOST);
+        const bool near_y = G.py && (y < GHOST || y >= ny - GHOST);
+        const bool outlet = x + 1 == nx - 1 && G.cls[x + 1 + nx * y] == OUTLET;
+        const int aux = (x + nx * y) | (outlet ? GAS_AUX_OUTLET : 0) | (near_x || near_y ? GAS_AUX_GHOST : 0);
+        gas_list.push_back(make_int2((x + XOFF) + (y + YOFF) * P.pitch, aux));
+      }
   P.n_gas = (int)gas_list.size();
   // Step-kernel blocks, interleaved by bands of 8 rows: the gas blocks of a band, then
   // the wall blocks of the same band; the interior solid blocks come last.
@@ -497,7 +509,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   field = (type*)p;
   ALLOC(S.code, uint32_t, P.plane);
   ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
-  ALLOC(S.gas_list, int32_t, std::max<size_t>(gas_list.size(), 1));
+  ALLOC(S.gas_list, int2, std::max<size_t>(gas_list.size(), 1));
   ALLOC(S.blocks, int4, std::max<size_t>(blocks.size(), 1));
   ALLOC(S.F[0], float, (size_t)(ns + 1) * P.plane);
   ALLOC(S.F[1], float, (size_t)(ns + 1) * P.plane);
@@ -517,7 +529,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (e == cudaSuccess && !blocks.empty())
     e = cudaMemcpyAsync(S.blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && !gas_list.empty())
-    e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int32_t) * gas_list.size(), cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int2) * gas_list.size(), cudaMemcpyHostToDevice,
                         h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {

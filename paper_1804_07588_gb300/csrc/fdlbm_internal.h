@@ -79,7 +79,7 @@ struct DevState {
   float* Ts[2];         // solid temperature deviation from Tref, [n]
   uint32_t* code;       // node code words on the padded lattice, [plane]
   int32_t* solid_list;  // wall nodes first, then interior solid nodes (compact indices)
-  int32_t* gas_list;    // gas nodes, row-major (padded indices)
+  int2* gas_list;       // gas nodes, row-major: {padded index, aux} (aux: GAS_AUX_*)
   float* F[2];          // moment fields [1 + ns][plane]: dTg, K_j (ping-pong with h)
   int4* blocks;         // step-kernel block descriptors {role (0 gas, 1 solid), first, count, 0}
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
@@ -103,8 +103,15 @@ cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, 
 // recomputes the pre-collision moments of the step that read src into S.mom instead.
 cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only,
                         cudaStream_t st);
-// Gas-role block size of the step kernel (threads per block).
+// Step-kernel block size: one gas, wall or solid node per thread.
 constexpr int STEP_BLOCK = 256;
+// Second word of a gas-list entry: the compact lattice index n = x + nx y in the low 29
+// bits; GAS_AUX_GHOST marks a node (or its outlet neighbour) within GHOST of a periodic
+// face, which also writes ghost copies; GAS_AUX_OUTLET a node whose +x neighbour is an
+// outlet node.
+constexpr int GAS_AUX_N = (1 << 29) - 1;
+constexpr int GAS_AUX_OUTLET = 1 << 29;
+constexpr int GAS_AUX_GHOST = 1 << 30;
 // Per-block ledger slots of the step kernel and their sum (LG_COUNT doubles into out).
 int ledger_slots(const DevParams& P);
 cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st);

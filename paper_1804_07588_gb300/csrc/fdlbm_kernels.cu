@@ -73,39 +73,6 @@ __device__ __forceinline__ void store_with_ghosts(float* p, int k, const Ghost& 
   }
 }
 
-// Pull one non-rest population into the node at padded index k along direction i, with
-// off = e_i on the padded lattice: the off-lattice value s1 streamed from x - e_i advanced
-// by (1 - c_j) with the first and second differences of Eqs. interpol_bulk (central),
-// interpol_away (forward) and interpol_towards (backward). The differences vanish
-// exactly on uniform data, so FP32 rounding adds no systematic mass or momentum.
-__device__ __forceinline__ float pull_one(const DevParams& P, const float* __restrict__ src, int b, int off,
-                                          uint32_t st, int j) {
-  // b: element index of this node in the (j, i) plane; 32-bit offsets from one base.
-  const float s1 = __ldg(src + (b - off));
-  if (P.onlattice[j]) return s1;
-  const float ha = P.ha[j], ha2 = P.ha2[j];  // (1 - c) / 2, (1 - c)^2 / 2
-  switch (st) {
-    case ST_CENTRAL: {
-      const float s2 = __ldg(src + (b - 2 * off)), s0 = __ldg(src + b);
-      return fmaf(ha, s0 - s2, fmaf(ha2, (s0 + s2) - 2.f * s1, s1));
-    }
-    case ST_FORWARD: {
-      const float s0 = __ldg(src + b), sp = __ldg(src + (b + off));
-      return fmaf(ha, (4.f * s0 - sp) - 3.f * s1, fmaf(ha2, (s1 + sp) - 2.f * s0, s1));
-    }
-    case ST_BACKWARD: {
-      const float s2 = __ldg(src + (b - 2 * off)), s3 = __ldg(src + (b - 3 * off));
-      return fmaf(ha, (3.f * s1 + s3) - 4.f * s2, fmaf(ha2, (s1 + s3) - 2.f * s2, s1));
-    }
-    case ST_LIN_S0:
-      return fmaf(P.a[j], __ldg(src + b) - s1, s1);
-    case ST_LIN_S2:
-      return fmaf(P.a[j], s1 - __ldg(src + (b - 2 * off)), s1);
-    default:
-      return s1;
-  }
-}
-
 // Running species moments of pulled deviations.
 template <int NS>
 struct Acc {
@@ -206,6 +173,15 @@ __device__ __forceinline__ void pull_node(const DevParams& P, const float* __res
 // shared-memory column (no registers held while they are in flight), then, once they
 // have landed, applies the interpolation with the two further stencil points of each
 // off-lattice species and accumulates the moments.
+// Streaming stencil coefficients by stencil code (the values of stencil_coef): {pA, pB,
+// p1, qA}, {qB, q1} and the integer offsets {mA, mB} in units of e_i.
+__constant__ float4 c_st_p[8] = {{0.f, 0.f, 0.f, 0.f},   {-1.f, 1.f, 0.f, 1.f}, {4.f, -1.f, 3.f, -2.f},
+                                 {-4.f, 1.f, -3.f, -2.f}, {2.f, 0.f, 2.f, 0.f},  {-2.f, 0.f, -2.f, 0.f},
+                                 {0.f, 0.f, 0.f, 0.f},    {0.f, 0.f, 0.f, 0.f}};
+__constant__ float2 c_st_q[8] = {{0.f, 0.f}, {1.f, 2.f}, {1.f, -1.f}, {1.f, -1.f},
+                                 {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f},  {0.f, 0.f}};
+__constant__ int2 c_st_m[8] = {{0, 0}, {-2, 0}, {0, 1}, {-2, -3}, {0, 0}, {-2, -2}, {0, 0}, {0, 0}};
+
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
@@ -240,8 +216,11 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const float* __re
     return;
   }
   const int off = EX(I) + EY(I) * P.pitch;
-  const StencilCoef sc = stencil_coef(stencil_of(cw, I));
-  const int dA = sc.mA * off, dB = sc.mB * off;
+  const uint32_t st = stencil_of(cw, I);
+  const float4 cp = c_st_p[st];
+  const float2 cq = c_st_q[st];
+  const int2 cm = c_st_m[st];
+  const int dA = cm.x * off, dB = cm.y * off;
   float vA[NS], vB[NS];
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
@@ -257,8 +236,8 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const float* __re
     const float v1 = s_h[(j * Q + I) * GB + tid];
     float v = v1;
     if (!P.onlattice[j]) {
-      const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1;
-      const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1;
+      const float d1 = fmaf(cp.x, vA[j], cp.y * vB[j]) - cp.z * v1;
+      const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1;
       v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1));
       s_h[(j * Q + I) * GB + tid] = v;
     }
@@ -347,13 +326,12 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // Moment field F: [1 + NS][plane]: dTg and K_j = kcoef_j C_j T_g of every gas node.
 template <int NS, bool PHI, int MODE>
 __device__ __forceinline__ void gas_node(const DevParams& P, const float* __restrict__ src, float* __restrict__ dst,
-                                         const uint32_t* __restrict__ code, int k,
+                                         const uint32_t* __restrict__ code, int k, int aux,
                                          const float* __restrict__ Fsrc, float* __restrict__ Fdst,
                                          float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags,
                                          float* __restrict__ s_h, int tid) {
   const uint32_t cw = __ldg(code + k);
-  const int px = k % P.pitch;
-  const int gx = px - P.xoff, gy = k / P.pitch - P.yoff;
+  const int n = aux & GAS_AUX_N;
 
   Acc<NS> acc;
   Mom<NS> m;
@@ -396,7 +374,6 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
   const float ux = m.jx / m.r, uy = m.jy / m.r;
   const float dT = m.dTg + sdq / (4.f * m.C);
   const float T = P.Tref + dT;
-  const int n = gx + P.nx * gy;
   if (MODE == 1) {
 #pragma unroll
     for (int j = 0; j < NS; ++j) mom[(long long)j * P.n + n] = P.rref[j] + m.drho[j];
@@ -405,7 +382,8 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
     mom[(long long)(NS + 2) * P.n + n] = T;
     return;
   }
-  const Ghost gh = ghost_of(P, gx, gy);
+  Ghost gh{0, 0};
+  if (aux & GAS_AUX_GHOST) gh = ghost_of(P, n % P.nx, n / P.nx);
   if (PHI) {
     store_with_ghosts(Fdst, k, gh, m.dTg);
 #pragma unroll
@@ -477,6 +455,7 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
     const float gfx = gfs * Ucx, gfy = gfs * Ucy;
     // w1 tau1 Phi_i with phi = M_j {-1, 1/4 on the axis links, 0 on diagonals}
     const float gphi = P.wt1[j] * M * dqj;
+    float hn[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int a = EX(i) + 1, b = EY(i) + 1;
@@ -489,16 +468,26 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const float* __rest
       const float h = s_h[(j * Q + i) * GB + tid];
       // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi); the two
       // small differences are formed first so that FP32 keeps their precision.
-      const float hn = fmaf(-om, h - fst, fmaf(-omt, fst - feq, h + force));
-      store_with_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, hn);
+      hn[i] = fmaf(-om, h - fst, fmaf(-omt, fst - feq, h + force));
+    }
+    // 32-bit element offsets: the host keeps ns Q plane below 2^31.
+    const int pl = (int)P.plane;
+    float* out = dst + j * Q * pl;
+    if (!(aux & GAS_AUX_GHOST)) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) __stcs(out + (i * pl + k), hn[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) store_with_ghosts(out + i * pl, k, gh, hn[i]);
     }
   }
 
   // Outlet (reading R13): equilibrium at the outlet pressure with this node's
   // composition, velocity and temperature.
-  if (gx + 1 == P.nx - 1 && node_class(__ldg(code + k + 1)) == OUTLET) {
+  if (aux & GAS_AUX_OUTLET) {
     const float Cout = P.p_out / T;
-    const Ghost go = ghost_of(P, gx + 1, gy);
+    Ghost go{0, 0};
+    if (aux & GAS_AUX_GHOST) go = ghost_of(P, n % P.nx + 1, n / P.nx);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       const float rj = (P.rref[j] + m.drho[j]) * P.invM[j] / m.C * Cout * P.M[j];
@@ -520,14 +509,15 @@ template <int NS, bool PHI, int MODE>
 __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, const float* __restrict__ src,
                                                                  float* __restrict__ dst,
                                                                  const uint32_t* __restrict__ code,
-                                                                 const int32_t* __restrict__ gas_list,
+                                                                 const int2* __restrict__ gas_list,
                                                                  const float* __restrict__ Fsrc,
                                                                  float* __restrict__ Fdst, float* __restrict__ mom,
                                                                  float* __restrict__ Tgas, int* __restrict__ flags) {
   extern __shared__ float smem[];
   const int t = blockIdx.x * GB + threadIdx.x;
   if (t >= P.n_gas) return;
-  gas_node<NS, PHI, MODE>(P, src, dst, code, __ldg(gas_list + t), Fsrc, Fdst, mom, Tgas, flags, smem, threadIdx.x);
+  const int2 g = __ldg(gas_list + t);
+  gas_node<NS, PHI, MODE>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, mom, Tgas, flags, smem, threadIdx.x);
 }
 
 template <int NS, int MODE>
@@ -757,7 +747,7 @@ __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], doub
 template <int NS, bool PHI>
 __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     DevParams P, const float* __restrict__ src, float* __restrict__ dst, const uint32_t* __restrict__ code,
-    const int32_t* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
+    const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
     const float* __restrict__ Fsrc, float* __restrict__ Fdst, const float* __restrict__ Ts_src,
     float* __restrict__ Ts_dst, const float* __restrict__ Tgas_src, float* __restrict__ Tgas_dst,
     double* __restrict__ ledger, int* __restrict__ flags) {
@@ -765,9 +755,10 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
   if (d.x == 0) {
-    if (tid < d.z)
-      gas_node<NS, PHI, 0>(P, src, dst, code, __ldg(gas_list + d.y + tid), Fsrc, Fdst, nullptr, Tgas_dst, flags,
-                           smem, tid);
+    if (tid < d.z) {
+      const int2 g = __ldg(gas_list + d.y + tid);
+      gas_node<NS, PHI, 0>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid);
+    }
     return;
   }
   double acc[LG_COUNT];
