@@ -517,6 +517,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.Tgas, float, 2 * (size_t)n);
   ALLOC(S.snap, float, (size_t)(ns + 4) * n);
   ALLOC(S.ledger, double, (size_t)LG_COUNT * ledger_slots(P));
+  ALLOC(S.rw, float, (size_t)ns * std::max<size_t>(walls.size(), 1));
   ALLOC(S.flags, int, 4);
   ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + LG_COUNT + 8);
   ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
@@ -640,6 +641,9 @@ fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->S.ledger, 0, sizeof(double) * LG_COUNT * ledger_slots(h->P), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->S.flags, 0, sizeof(int) * 4, h->stream);
+  // no previous wall densities yet: all-ones bytes are a NaN
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->S.rw, 0xFF, sizeof(float) * (size_t)ns * std::max(h->P.n_wall_list, 1), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "initialise state");
@@ -817,7 +821,8 @@ fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
 // little-endian): char magic[8] "FDLBMCK1"; u64 fingerprint; i32 nx, ny, ns, n_blocks;
 // i64 plane, steps, steps_at_residual; i32 have_snap, flags; f64 E0, H0, mass0[MAX_NS],
 // moles0[MAX_NS]; then FP32 h[cur] [ns][9][plane], F[cur] [1 + ns][plane], Ts[cur] [n],
-// Tgas[cur] [n], mom [ns + 3][n], snap [ns + 4][n], FP64 ledger [n_blocks][LG_COUNT].
+// Tgas[cur] [n], mom [ns + 3][n], snap [ns + 4][n], FP64 ledger [n_blocks][LG_COUNT],
+// FP32 wall densities [ns][n_wall_list].
 namespace {
 
 constexpr char CK_MAGIC[8] = {'F', 'D', 'L', 'B', 'M', 'C', 'K', '1'};
@@ -854,7 +859,8 @@ std::vector<std::pair<void*, size_t>> ck_buffers(fdlbm_handle* h) {
           {h->S.Tgas + (size_t)h->cur * n, sizeof(float) * n},
           {h->S.mom, sizeof(float) * (ns + 3) * n},
           {h->S.snap, sizeof(float) * (ns + 4) * n},
-          {h->S.ledger, sizeof(double) * LG_COUNT * (size_t)ledger_slots(P)}};
+          {h->S.ledger, sizeof(double) * LG_COUNT * (size_t)ledger_slots(P)},
+          {h->S.rw, sizeof(float) * ns * (size_t)std::max(P.n_wall_list, 1)}};
 }
 
 }  // namespace

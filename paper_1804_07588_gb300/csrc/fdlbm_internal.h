@@ -87,6 +87,7 @@ struct DevState {
   float* snap;          // residual snapshot [(ns + 4)][n]
   double* ledger;       // FP64 ledger accumulators, LG_COUNT per solid-kernel block
   int* flags;           // sticky error flags
+  float* rw;            // converged wall densities of the last step, [ns][n_wall_list] (NaN: none)
   double* red;          // reduction scratch (doubles)
 };
 

@@ -569,14 +569,16 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return s;
 }
 
-// One solid node (compact index n): FD heat step; interface wall nodes also run the
-// reactive diffusive wall. Ledger increments accumulate into acc (Q_rxn, Q_wall,
-// Q_couple, Q_fixedT, non-converged iterations).
+// One solid node (compact index n, entry idx of the solid list): FD heat step;
+// interface wall nodes also run the reactive diffusive wall. Ledger increments accumulate
+// into acc (Q_rxn, Q_wall, Q_couple, Q_fixedT, non-converged iterations). rw_prev
+// [ns][n_wall_list] holds each catalytic wall's converged density of the previous step
+// (NaN before the first step), the start of its iteration.
 template <int NS>
 __device__ __forceinline__ void solid_node(const DevParams& P, const float* __restrict__ src, float* __restrict__ dst,
                                            const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
                                            const uint32_t* __restrict__ code, const float* __restrict__ Tgas, int n,
-                                           double (&acc)[LG_COUNT]) {
+                                           double (&acc)[LG_COUNT], float* __restrict__ rw_prev, int idx) {
   {
     const int x = n % P.nx, y = n / P.nx;
     const int k = pad_index(P, x, y);
@@ -664,6 +666,14 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
         float kr[MAX_NR];
         const float TK = P.T3T0 * Tw;
         for (int r = 0; r < P.nr; ++r) kr[r] = P.k0[r] * expf(-P.EaR[r] / TK);
+        // Start from the previous step's converged density when there is one (the fixed
+        // point moves little between steps); the converged value does not depend on the
+        // start.
+        float* rp = rw_prev + idx;
+        if (rp[0] == rp[0]) {
+#pragma unroll
+          for (int j = 0; j < NS; ++j) rw[j] = rp[(long long)j * P.n_wall_list];
+        }
         bool conv = false;
         for (int it = 0; it < P.rho_w_maxit; ++it) {
           rates<NS>(P, rw, kr, rate);
@@ -680,6 +690,8 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
           if (d <= fmaxf(P.rho_w_tol, 4.f * FLT_EPSILON * rmax)) { conv = true; break; }
         }
         if (!conv) acc[LG_NOCONV] += 1.0;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) rp[(long long)j * P.n_wall_list] = rw[j];
         rates<NS>(P, rw, kr, rate);
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
@@ -724,9 +736,12 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const float* __re
 // atomics; the slots are summed when the ledger is read).
 __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], double* __restrict__ slot) {
   __shared__ double sh[LG_COUNT][GB / 32];
+  // FP64 arithmetic is slow on this part: quantities that are zero in the whole warp
+  // (interior solid nodes away from fixed-T faces contribute nothing) skip the shuffles.
 #pragma unroll
   for (int q = 0; q < LG_COUNT; ++q)
-    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+    if (__any_sync(0xffffffffu, acc[q] != 0.0))
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
@@ -750,7 +765,7 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
     const float* __restrict__ Fsrc, float* __restrict__ Fdst, const float* __restrict__ Ts_src,
     float* __restrict__ Ts_dst, const float* __restrict__ Tgas_src, float* __restrict__ Tgas_dst,
-    double* __restrict__ ledger, int* __restrict__ flags) {
+    double* __restrict__ ledger, int* __restrict__ flags, float* __restrict__ rw_prev) {
   extern __shared__ float smem[];
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
@@ -764,7 +779,9 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   double acc[LG_COUNT];
 #pragma unroll
   for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
-  if (tid < d.z) solid_node<NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc);
+  if (tid < d.z)
+    solid_node<NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
+                   d.y + tid);
   ledger_block_store(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
@@ -1068,7 +1085,7 @@ cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStre
   step_kernel<NS, PHI><<<P.n_blocks, GB, smem, st>>>(
       P, S.h[src], S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
       paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
-      S.flags);
+      S.flags, S.rw);
   return cudaGetLastError();
 }
 
