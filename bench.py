@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="fdlbm", choices=["fdlbm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
     return ap.parse_args()
 
 
@@ -184,6 +185,48 @@ def whole_job_value(ns: int, n_gas: int, steps: int, world: int, total_ms: float
     return ns * n_gas * steps * world / (total_ms * 1e-3) / 1e6
 
 
+def run_to_steady(fdlbm, p, init=None, tol=1e-6, every=500, max_steps=400_000, device=0):
+    """Steps and wall time (host clock around the whole loop, synchronised) for the solver
+    to reach the steady-state residual tol, checked every `every` steps."""
+    import torch
+    s = fdlbm.Solver(p, device=device)
+    if init is not None:
+        s.set_fields(init)
+    s.residual()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    steps, r = 0, float("inf")
+    while steps < max_steps:
+        s.step(every)
+        steps += every
+        r = s.residual()
+        if r < tol:
+            break
+    s.sync()
+    el = time.perf_counter() - t0
+    return s, {"steps": steps, "seconds": el, "residual": r, "converged": r < tol}
+
+
+def time_to_steady(fdlbm, workloads, device=0):
+    """Cold start vs warm start on the catalytic channel (128x32 gas, 8-node walls): cold
+    from the uniform initial fields, warm from the steady state of a neighbouring
+    operating point (inlet velocity 0.018 instead of 0.02) passed through
+    fdlbm_set_fields."""
+    p = workloads.config0()
+    near = workloads.config0(u_inlet=0.018)
+    s_near, _ = run_to_steady(fdlbm, near, device=device)
+    warm_init = s_near.restart_fields()
+    s_near.close()
+    s, cold = run_to_steady(fdlbm, p, device=device)
+    s.close()
+    s, warm = run_to_steady(fdlbm, p, init=warm_init, device=device)
+    s.close()
+    return {"workload": "catalytic channel 128x32 gas + 2x8 solid rows, 5 species", "tol": 1e-6,
+            "check_every": 500, "cold": cold, "warm": warm,
+            "warm_start": "steady state of the channel at inlet velocity 0.018 (a neighbouring "
+                          "operating point); the learned warm start is not built"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -283,6 +326,10 @@ def run_fdlbm(args, rank, world, local_rank):
         s2.close()
         del np
 
+    tts = None
+    if rank == 0 and not args.no_steady:
+        tts = time_to_steady(fdlbm, workloads, device=dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, el = oracle_throughput(seconds=10.0)
@@ -305,6 +352,7 @@ def run_fdlbm(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
+            "time_to_steady": tts,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

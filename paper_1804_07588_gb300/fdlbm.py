@@ -223,6 +223,10 @@ class Solver:
         self.ns = ns
         self.nx, self.ny = p["nx"], p["ny"]
         self.n = self.nx * self.ny
+        m = np.array([d["M_gmol"] for d in sp], np.float64)
+        self._M_lat = m / m.min()
+        self._X_init = np.array([d["X_init"] for d in sp], np.float64)
+        self._T_init = float(p["T_init_K"])
 
     # -- life cycle ---------------------------------------------------------------
     def close(self):
@@ -299,6 +303,22 @@ class Solver:
     def load_state(self, path: str):
         """Restore a checkpoint written by a solver of the same problem."""
         _check(load().fdlbm_load(self._h, os.fsencode(path)))
+
+    def restart_fields(self) -> dict:
+        """The current state as initial fields for set_fields (or for another solver of
+        the same geometry): mole fractions, velocity, gas and solid temperature (K) and
+        molar concentration, with the create-time defaults where a field is undefined
+        (gas fields on solid nodes and the reverse)."""
+        ns = self.ns
+        m = self.moments_host().astype(np.float64)
+        rho, X = m[:ns], m[ns:2 * ns]
+        T, Ts = m[2 * ns + 2], m[2 * ns + 3]
+        gas = T > 0
+        C_lat = (rho / self._M_lat[:, None]).sum(axis=0)
+        X = np.where(gas[None, :], X, self._X_init[:, None])
+        return {"X": X, "u": np.where(gas[None, :], m[2 * ns:2 * ns + 2], 0.0),
+                "T_K": np.where(gas, T, self._T_init), "Ts_K": np.where(Ts > 0, Ts, self._T_init),
+                "C": np.where(gas, C_lat, 1.0)}
 
     def set_fields(self, init: dict):
         keep = []

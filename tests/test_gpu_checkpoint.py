@@ -64,3 +64,23 @@ def test_load_rejects_other_problem_and_missing_file(tmp_path):
     assert ei.value.status == -8
     a.close()
     other.close()
+
+
+def test_restart_fields_warm_start():
+    """The state of one solver as initial fields of another (fdlbm_set_fields): the new
+    solver starts from the same moment fields (equilibrium populations of them)."""
+    fdlbm = _fdlbm()
+    p = W.channel(nx=64, n_gas=16, wall=4)
+    a = fdlbm.Solver(p)
+    a.step(120)
+    f = a.restart_fields()
+    ma = a.moments_host().astype(np.float64)
+    b = fdlbm.Solver(p)
+    b.set_fields(f)
+    mb = b.moments_host().astype(np.float64)
+    ns = a.ns
+    for row in list(range(ns, 2 * ns)) + [2 * ns, 2 * ns + 1, 2 * ns + 2, 2 * ns + 3]:
+        scale = np.abs(ma[row]).max()
+        assert np.abs(ma[row] - mb[row]).max() <= 2e-6 * scale, row
+    a.close()
+    b.close()
