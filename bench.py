@@ -30,8 +30,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "species-MLUPS & % HBM roofline; time-to-steady (res 1e-6) warm vs cold"
 UNIT = "species-MLUPS"
-BYTES_PER_SPECIES_NODE = 72  # D2Q9 FP32: read 9 + write 9 populations
+# D2Q9: read 9 + write 9 populations per species-node, 4 bytes each in FP32 storage, 2 in
+# BF16 / FP16 storage
+BYTES_PER_VALUE = {"fp32": 4, "bf16": 2, "fp16": 2}
 WORKLOAD = "porous-bed-d2q9-1024x512-5species-fp32"
+
+
+def workload_name(storage):
+    return WORKLOAD if storage == "fp32" else WORKLOAD.replace("-fp32", f"-{storage}-storage")
 
 
 def parse():
@@ -43,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="population storage (FP32 arithmetic in every case)")
     return ap.parse_args()
 
 
@@ -268,7 +276,7 @@ def run_fdlbm(args, rank, world, local_rank):
     dev = local_rank
     torch.cuda.set_device(dev)
     p = workloads.config1()
-    s = fdlbm.Solver(p, device=dev)
+    s = fdlbm.Solver(p, device=dev, storage=args.storage)
     info = s.info()
     ns = info["ns"]
     n_gas = info["n_gas"]
@@ -302,7 +310,7 @@ def run_fdlbm(args, rank, world, local_rank):
     total_ms = max_over_ranks(total_ms, dist, device=f"cuda:{dev}")
     value = whole_job_value(ns, n_gas, args.steps, world, total_ms)
     step_kernel_ms = ms_step / max(timed, 1)
-    alg_bytes = BYTES_PER_SPECIES_NODE * ns * n_gas
+    alg_bytes = 18 * BYTES_PER_VALUE[args.storage] * ns * n_gas
     achieved = alg_bytes / (step_kernel_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
 
@@ -311,7 +319,7 @@ def run_fdlbm(args, rank, world, local_rank):
         import numpy as np
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        s2 = fdlbm.Solver(p, device=dev)
+        s2 = fdlbm.Solver(p, device=dev, storage=args.storage)
         s2.step(args.steps)
         m = s2.moments_host()
         s2.sync()
@@ -341,12 +349,16 @@ def run_fdlbm(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": p["nx"], "ny": p["ny"], "porosity": 0.6,
+            "config": {"workload": workload_name(args.storage), "nx": p["nx"], "ny": p["ny"], "porosity": 0.6,
+                       "storage": {"fp32": "FP32 deviations", "bf16": "BF16 deviations, stochastic rounding",
+                                   "fp16": "FP16 deviations (power-of-two scale per species), stochastic "
+                                           "rounding"}[args.storage],
                        "species": ns, "gas_nodes": n_gas, "wall_nodes": info["n_wall"],
                        "solid_nodes": info["n_solid"], "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(),
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": ncu_traffic() if args.storage == "fp32" else None,
                          "peak_kind": peak_kind + " copy bandwidth",
                          "alg_bytes_per_launch": alg_bytes, "kernel_ms_per_launch": step_kernel_ms},
             "cpu_baseline": cpu,

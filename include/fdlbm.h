@@ -67,7 +67,12 @@ enum { FDLBM_COUPLING_CONSERVATIVE = 0, FDLBM_COUPLING_PAPER = 1 };
 /* Surface rate laws: k C_a C_b of Eq. showcase_Sj, or the reversible mole-fraction
  * law k (prod x_reactants - prod x_products / Keq). */
 enum { FDLBM_RATE_CONC_BILINEAR = 0, FDLBM_RATE_XFRAC_REVERSIBLE = 1 };
-enum { FDLBM_STORAGE_FP32 = 0 };
+/* Population storage. Every population is stored as its deviation from the rest
+ * equilibrium of the inlet state, g - rho_ref,j w_i(T_ref); the arithmetic is FP32 for
+ * every storage type. BF16 rounds each stored deviation to 8 significant bits; FP16 to
+ * 11, after scaling it by a power of two per species chosen from the species' molar
+ * mass so that deviations up to twice its molar mass stay in FP16's range. */
+enum { FDLBM_STORAGE_FP32 = 0, FDLBM_STORAGE_BF16 = 1, FDLBM_STORAGE_FP16 = 2 };
 
 /* Lattice and geometry (Sec. 4.3: walls sit on the solid nodes next to the gas). */
 typedef struct {
@@ -125,7 +130,7 @@ typedef struct {
 /* Device memory and stream. alloc/free may be NULL (cudaMalloc / cudaFree). stream is a
  * cudaStream_t (NULL: the legacy default stream). */
 typedef struct {
-  int storage;             /* FDLBM_STORAGE_FP32 */
+  int storage;             /* FDLBM_STORAGE_* (FP32 default) */
   int device;              /* CUDA device ordinal */
   void* stream;
   void* (*alloc)(size_t bytes, void* ctx);

@@ -205,7 +205,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     return fail(FDLBM_EINVAL, "unknown coupling");
   if (kin->rho_w_maxit < 1 || !(kin->rho_w_tol > 0)) return fail(FDLBM_EINVAL, "rho_w_tol > 0 and rho_w_maxit >= 1 required");
   const int storage = opts ? opts->storage : FDLBM_STORAGE_FP32;
-  if (storage != FDLBM_STORAGE_FP32) return fail(FDLBM_EINVAL, "unsupported storage %d", storage);
+  if (storage != FDLBM_STORAGE_FP32 && storage != FDLBM_STORAGE_BF16 && storage != FDLBM_STORAGE_FP16)
+    return fail(FDLBM_EINVAL, "unsupported storage %d", storage);
 
   double Mmin = 1e300;
   for (int j = 0; j < n_species; ++j) {
@@ -440,9 +441,21 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     P.invtau2[j] = (float)(1.0 / t2);
     // Energy-correction flux K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T, c_pj = 2 / M_j (2D).
     P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.0 / M) / tr->Pr - 1.0 / M) * t1) : 0.f;
+    // FP16 storage: deviations |g - rref W0| stay below 2 M_j + rref_j (a population never
+    // exceeds its species density, bounded by the molar mass at twice the inlet molar
+    // concentration); the largest power of two that maps that bound below 2^15 keeps
+    // them inside FP16's range (max 65504) with a factor 2 to spare.
+    P.hs[j] = P.hsi[j] = 1.f;
+    if (storage == FDLBM_STORAGE_FP16) {
+      const double bound = 2.0 * M + species[j].X_inlet * M;
+      const int e = (int)std::floor(std::log2(32768.0 / bound));
+      P.hs[j] = (float)std::ldexp(1.0, e);
+      P.hsi[j] = (float)std::ldexp(1.0, -e);
+    }
     h->X_init[j] = species[j].X_init;
     h->X_inlet[j] = species[j].X_inlet;
   }
+  P.storage = storage;
   for (int i = 0; i < Q; ++i) {
     const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
     const double wy = HEY[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
@@ -492,11 +505,11 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   // Device state.
   fdlbm_status st;
   DevState& S = h->S;
-  const size_t pop_bytes = sizeof(float) * (size_t)ns * Q * (size_t)P.plane;
+  const size_t pop_bytes = pop_bytes_per_value(storage) * (size_t)ns * Q * (size_t)P.plane;
   void* p;
   for (int b = 0; b < 2; ++b) {
     if ((st = dalloc(h, pop_bytes, &p)) != FDLBM_OK) { release(h); delete h; return st; }
-    S.h[b] = (float*)p;
+    S.h[b] = p;
     if ((st = dalloc(h, sizeof(float) * n, &p)) != FDLBM_OK) { release(h); delete h; return st; }
     S.Ts[b] = (float*)p;
   }
@@ -554,11 +567,11 @@ fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n) {
     if (h->profiling && h->events_used + 2 <= h->events.size()) {
       cudaEvent_t* ev = h->events.data() + h->events_used;
       CK(cudaEventRecord(ev[0], h->stream), "event record");
-      CK(launch_step(h->P, h->S, h->cur, false, h->stream), "step launch");
+      CK(launch_step(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
       CK(cudaEventRecord(ev[1], h->stream), "event record");
       h->events_used += 2;
     } else {
-      CK(launch_step(h->P, h->S, h->cur, false, h->stream), "step launch");
+      CK(launch_step(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
     }
     h->cur ^= 1;
   }
@@ -820,7 +833,7 @@ fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
 // Checkpoint file: a fixed header, then the state the next step reads. Layout (native
 // little-endian): char magic[8] "FDLBMCK1"; u64 fingerprint; i32 nx, ny, ns, n_blocks;
 // i64 plane, steps, steps_at_residual; i32 have_snap, flags; f64 E0, H0, mass0[MAX_NS],
-// moles0[MAX_NS]; then FP32 h[cur] [ns][9][plane], F[cur] [1 + ns][plane], Ts[cur] [n],
+// moles0[MAX_NS]; then h[cur] [ns][9][plane] in the storage type, FP32 F[cur] [1 + ns][plane], Ts[cur] [n],
 // Tgas[cur] [n], mom [ns + 3][n], snap [ns + 4][n], FP64 ledger [n_blocks][LG_COUNT],
 // FP32 wall densities [ns][n_wall_list].
 namespace {
@@ -853,7 +866,7 @@ struct CkHeader {
 std::vector<std::pair<void*, size_t>> ck_buffers(fdlbm_handle* h) {
   const DevParams& P = h->P;
   const size_t n = (size_t)P.n, ns = (size_t)P.ns, plane = (size_t)P.plane;
-  return {{h->S.h[h->cur], sizeof(float) * ns * Q * plane},
+  return {{h->S.h[h->cur], pop_bytes_per_value(P.storage) * ns * Q * plane},
           {h->S.F[h->cur], sizeof(float) * (1 + ns) * plane},
           {h->S.Ts[h->cur], sizeof(float) * n},
           {h->S.Tgas + (size_t)h->cur * n, sizeof(float) * n},
@@ -940,7 +953,7 @@ fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path) {
   }
   std::fclose(f);
   // The other population copy: nodes the step never rewrites (inlet) keep their values.
-  const size_t pop_bytes = sizeof(float) * (size_t)h->ns * Q * (size_t)h->P.plane;
+  const size_t pop_bytes = pop_bytes_per_value(h->P.storage) * (size_t)h->ns * Q * (size_t)h->P.plane;
   CK(cudaMemcpyAsync(h->S.h[h->cur ^ 1], h->S.h[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream),
      "copy populations");
   CK(cudaMemcpyAsync(h->S.flags, &hd.flags, sizeof(int), cudaMemcpyHostToDevice, h->stream), "write flags");

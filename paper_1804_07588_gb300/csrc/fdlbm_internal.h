@@ -56,6 +56,8 @@ struct DevParams {
   float uc_w[MAX_NS], invtau2[MAX_NS];
   float kcoef[MAX_NS];  // energy-correction flux coefficient K_j / (C_j T)
   float W0[Q];          // rest-equilibrium weights at T_ref
+  int storage;          // FDLBM_STORAGE_*: population storage type
+  float hs[MAX_NS], hsi[MAX_NS];  // FP16 storage: power-of-two scale per species and inverse (else 1)
   float Tref, p_out;    // lattice reference temperature, outlet pressure
   float u_inlet;
   // solid and coupling
@@ -75,7 +77,8 @@ struct DevParams {
 
 // Device state of one handle.
 struct DevState {
-  float* h[2];          // populations (deviations from rref W0), [ns][Q][plane] padded
+  void* h[2];           // populations (deviations from rref W0), [ns][Q][plane] padded, of the
+                        // storage type (float, __nv_bfloat16 or __half)
   float* Ts[2];         // solid temperature deviation from Tref, [n]
   uint32_t* code;       // node code words on the padded lattice, [plane]
   int32_t* solid_list;  // wall nodes first, then interior solid nodes (compact indices)
@@ -100,10 +103,12 @@ enum Ledger { LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV, LG_COUNT
 cudaError_t launch_init(const DevParams& P, const DevState& S, const double* X, const double* u,
                         const double* T_lat, const double* Ts_lat, const double* C,
                         const double* inlet, cudaStream_t st);
-// One time step reading buffer src and writing 1 - src; with moments_only the gas kernel
-// recomputes the pre-collision moments of the step that read src into S.mom instead.
+// One time step reading buffer src and writing 1 - src (step: the step's index, which
+// seeds the stochastic rounding of 16-bit population storage); with moments_only the gas
+// kernel recomputes the pre-collision moments of the step that read src into S.mom
+// instead.
 cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool moments_only,
-                        cudaStream_t st);
+                        cudaStream_t st, uint32_t step = 0);
 // Step-kernel block size: one gas, wall or solid node per thread.
 constexpr int STEP_BLOCK = 256;
 // Second word of a gas-list entry: the compact lattice index n = x + nx y in the low 29
@@ -122,6 +127,9 @@ cudaError_t launch_populations_out(const DevParams& P, const DevState& S, int cu
                                    cudaStream_t st);
 cudaError_t launch_totals(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 cudaError_t launch_residual(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
+
+// Bytes of one stored population.
+inline size_t pop_bytes_per_value(int storage) { return storage == FDLBM_STORAGE_FP32 ? 4 : 2; }
 
 // Number of doubles written by launch_totals into S.red: E_gas, H_solid, mass[ns], moles[ns].
 inline int totals_count(int ns) { return 2 + 2 * ns; }

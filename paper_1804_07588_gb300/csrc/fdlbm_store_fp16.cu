@@ -1,0 +1,7 @@
+// FP16 population storage: instantiates the solver's storage-dependent kernels and
+// entry points for __half (values rounded once per store; FP32 arithmetic).
+#include "fdlbm_device.cuh"
+
+namespace fdlbm {
+FDLBM_STORAGE_ENTRY_POINTS(, __half)
+}  // namespace fdlbm

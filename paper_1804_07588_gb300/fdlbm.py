@@ -155,9 +155,12 @@ def _fields(init, keep):
 
 class Solver:
     """One coupled FD-LBM problem on one GPU, built from a problem dict (see
-    ``paper_1804_07588_gb300.workloads``)."""
+    ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
+    storage (FP32 arithmetic in every case)."""
 
-    def __init__(self, p: dict, device: int = 0, stream=None):
+    STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+    def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
@@ -215,7 +218,11 @@ class Solver:
 
         self._alloc_cb = ALLOC_FN(_alloc)
         self._free_cb = FREE_FN(_free)
-        opts = Options(0, device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb, self._free_cb, None)
+        if storage not in self.STORAGE:
+            raise FdlbmError(-1, f"storage must be one of {sorted(self.STORAGE)}")
+        self.storage = storage
+        opts = Options(self.STORAGE[storage], device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
+                       self._free_cb, None)
         h = C.c_void_p()
         _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
                               C.byref(opts), C.byref(h)))
