@@ -70,7 +70,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fdlbm_kernels.cu", "fdlbm_internal.h"):
+    for f in ("fdlbm_device.cuh", "fdlbm_kernels.cu", "fdlbm_internal.h"):
         with open(os.path.join(ROOT, "paper_1804_07588_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
