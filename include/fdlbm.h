@@ -235,6 +235,28 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out);
 #define FDLBM_STATIC_SCRATCH_BYTES 262144
 fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len);
 
+/* Batched stepping (the paper has none: a library facility). A batch advances several
+ * independent handles together, one kernel launch per time step covering every member's
+ * gas, wall and solid blocks, with the per-step launches captured in a CUDA graph of 16
+ * steps that is replayed. Members must share the device, the species count, the storage
+ * type and the energy-correction switch; lattices, geometries and all other parameters
+ * may differ. A member advanced by a batch gives the same results, bit for bit, as when
+ * stepped alone; the handle stays usable on its own (outputs, residual, fdlbm_step) and
+ * the batch notices when a member was stepped outside it. The batch does not own its
+ * members: destroy the batch before them.
+ * fdlbm_batch_create: EINVAL (NULL or repeated handles, incompatible members), ECUDA.
+ * fdlbm_batch_step: enqueue n >= 0 steps of every member on the batch's own stream,
+ *   ordered after the work already queued on the members' streams and before any work
+ *   queued on them afterwards. The batch also holds a few small device tables of its own
+ *   (cudaMalloc), rewritten when members change.
+ * fdlbm_batch_remove: stop advancing member h (e.g. once it reached steady state). */
+typedef struct fdlbm_batch fdlbm_batch;
+fdlbm_status fdlbm_batch_create(fdlbm_handle* const* handles, int n, fdlbm_batch** out);
+fdlbm_status fdlbm_batch_step(fdlbm_batch* b, int64_t n);
+fdlbm_status fdlbm_batch_remove(fdlbm_batch* b, fdlbm_handle* h);
+int fdlbm_batch_size(const fdlbm_batch* b);
+void fdlbm_batch_destroy(fdlbm_batch* b);
+
 /* Checkpoint and restore (the paper has none: a library facility). fdlbm_save writes
  * the state the next step reads (current populations, lagged moment field, solid
  * temperature, moments, residual snapshot, ledger, step count) to the file at path;

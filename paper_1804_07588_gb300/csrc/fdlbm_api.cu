@@ -70,6 +70,7 @@ struct fdlbm_handle {
   int eps_species = -1, eps_nu = 0;
   double E0 = 0, H0 = 0, mass0[MAX_NS] = {}, moles0[MAX_NS] = {};
   int64_t counts[5] = {};
+  std::vector<int4> blocks_host;  // step-kernel block descriptors (for batches)
   int64_t stencil_counts[6] = {};
   // optional kernel timing: three events per step (before solid, between, after gas)
   bool profiling = false;
@@ -396,6 +397,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     chunks(1, (int)walls.size(), (int)solid_list.size());
   }
   P.n_blocks = (int)blocks.size();
+  h->blocks_host = blocks;
   P.ns = ns;
   P.periodic_x = G.px;
   P.periodic_y = G.py;
@@ -1013,6 +1015,240 @@ fdlbm_status fdlbm_kernel_times(fdlbm_handle* h, double* ms_out2, int64_t* steps
   if (steps_out) *steps_out = (int64_t)(h->events_used / 2);
   h->events_used = 0;
   return FDLBM_OK;
+}
+
+}  // extern "C"
+
+// A batch steps several handles in one launch per step; see fdlbm.h.
+struct fdlbm_batch {
+  std::vector<fdlbm_handle*> members;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int ns = 0, energy_correction = 0, storage = 0;
+  DevParams* d_params = nullptr;
+  DevState* d_states = nullptr;
+  int2* d_members = nullptr;
+  int4* d_blocks = nullptr;
+  uint32_t* d_counter = nullptr;
+  int n_blocks = 0;
+  int64_t counter = 0;                       // steps since d_members was written
+  std::vector<int> cur0;                     // member buffers of time level t at counter 0
+  std::vector<int64_t> step0;                // member step counts at counter 0
+  cudaGraphExec_t graph = nullptr;           // BATCH_GRAPH_STEPS batched steps
+  cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+constexpr int BATCH_GRAPH_STEPS = 16;
+
+void batch_free_device(fdlbm_batch* b) {
+  cudaFree(b->d_params);
+  cudaFree(b->d_states);
+  cudaFree(b->d_members);
+  cudaFree(b->d_blocks);
+  cudaFree(b->d_counter);
+  b->d_params = nullptr;
+  b->d_states = nullptr;
+  b->d_members = nullptr;
+  b->d_blocks = nullptr;
+  b->d_counter = nullptr;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+// (Re)build the device tables of the batch from its members' current state: parameters,
+// buffers, the members' time levels and step counts, and the concatenated block tables.
+fdlbm_status batch_upload(fdlbm_batch* b) {
+  batch_free_device(b);
+  const size_t m = b->members.size();
+  std::vector<DevParams> params(m);
+  std::vector<DevState> states(m);
+  std::vector<int2> mem(m);
+  std::vector<int4> blocks;
+  b->cur0.resize(m);
+  b->step0.resize(m);
+  for (size_t i = 0; i < m; ++i) {
+    fdlbm_handle* h = b->members[i];
+    params[i] = h->P;
+    states[i] = h->S;
+    b->cur0[i] = h->cur;
+    b->step0[i] = h->steps;
+    mem[i] = make_int2(h->cur, int(uint32_t(h->steps)));
+    for (size_t q = 0; q < h->blocks_host.size(); ++q) {
+      const int4 d = h->blocks_host[q];
+      blocks.push_back(make_int4(int(2 * i) + d.x, d.y, d.z, int(q)));
+    }
+  }
+  b->n_blocks = (int)blocks.size();
+  b->counter = 0;
+  CK(cudaMalloc(&b->d_params, sizeof(DevParams) * std::max<size_t>(m, 1)), "batch allocation");
+  CK(cudaMalloc(&b->d_states, sizeof(DevState) * std::max<size_t>(m, 1)), "batch allocation");
+  CK(cudaMalloc(&b->d_members, sizeof(int2) * std::max<size_t>(m, 1)), "batch allocation");
+  CK(cudaMalloc(&b->d_blocks, sizeof(int4) * std::max<size_t>(blocks.size(), 1)), "batch allocation");
+  CK(cudaMalloc(&b->d_counter, sizeof(uint32_t)), "batch allocation");
+  if (m) {
+    CK(cudaMemcpy(b->d_params, params.data(), sizeof(DevParams) * m, cudaMemcpyHostToDevice), "batch upload");
+    CK(cudaMemcpy(b->d_states, states.data(), sizeof(DevState) * m, cudaMemcpyHostToDevice), "batch upload");
+    CK(cudaMemcpy(b->d_members, mem.data(), sizeof(int2) * m, cudaMemcpyHostToDevice), "batch upload");
+  }
+  if (!blocks.empty())
+    CK(cudaMemcpy(b->d_blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice), "batch upload");
+  CK(cudaMemset(b->d_counter, 0, sizeof(uint32_t)), "batch upload");
+  return FDLBM_OK;
+}
+
+BatchLaunch batch_launch_args(const fdlbm_batch* b) {
+  BatchLaunch B;
+  B.params = b->d_params;
+  B.states = b->d_states;
+  B.members = b->d_members;
+  B.blocks = b->d_blocks;
+  B.counter = b->d_counter;
+  B.n_blocks = b->n_blocks;
+  B.ns = b->ns;
+  B.energy_correction = b->energy_correction;
+  B.storage = b->storage;
+  return B;
+}
+
+// The members' streams wait for `from`'s work so far.
+fdlbm_status streams_wait(cudaStream_t from, cudaEvent_t ev, const std::vector<fdlbm_handle*>& to) {
+  CK(cudaEventRecord(ev, from), "event record");
+  for (fdlbm_handle* h : to) CK(cudaStreamWaitEvent(h->stream, ev, 0), "stream wait");
+  return FDLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fdlbm_status fdlbm_batch_create(fdlbm_handle* const* handles, int n, fdlbm_batch** out) {
+  if (!out || !handles || n < 1) return fail(FDLBM_EINVAL, "need an output pointer and at least one handle");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return fail(FDLBM_EINVAL, "handle %d is NULL", i);
+    for (int q = 0; q < i; ++q)
+      if (handles[q] == handles[i]) return fail(FDLBM_EINVAL, "handle %d appears twice", i);
+    const fdlbm_handle* h = handles[i];
+    const fdlbm_handle* h0 = handles[0];
+    if (h->device != h0->device || h->ns != h0->ns || h->P.storage != h0->P.storage ||
+        h->P.energy_correction != h0->P.energy_correction)
+      return fail(FDLBM_EINVAL,
+                  "handle %d differs from handle 0 in device, species count, storage or energy correction", i);
+  }
+  DeviceGuard guard(handles[0]->device);
+  fdlbm_batch* b = new fdlbm_batch;
+  b->members.assign(handles, handles + n);
+  b->device = handles[0]->device;
+  b->ns = handles[0]->ns;
+  b->energy_correction = handles[0]->P.energy_correction;
+  b->storage = handles[0]->P.storage;
+  // Its own stream: graphs cannot be captured on the legacy default stream the members
+  // may use; events order it against the members' streams.
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return cuda_fail(e, "batch stream");
+  }
+  for (fdlbm_handle* h : b->members) {
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(b->done);
+      cudaStreamDestroy(b->stream);
+      delete b;
+      return cuda_fail(e, "stream sync");
+    }
+  }
+  fdlbm_status st = batch_upload(b);
+  if (st != FDLBM_OK) {
+    fdlbm_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_batch_step(fdlbm_batch* b, int64_t n) {
+  if (!b || n < 0) return fail(FDLBM_EINVAL, "bad batch or step count");
+  if (n == 0 || b->members.empty()) return FDLBM_OK;
+  DeviceGuard guard(b->device);
+  // A member stepped on its own since the tables were written: write them again.
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    const fdlbm_handle* h = b->members[i];
+    if (h->steps != b->step0[i] + b->counter || h->cur != (b->cur0[i] ^ int(b->counter & 1))) {
+      for (fdlbm_handle* m : b->members) CK(cudaStreamSynchronize(m->stream), "stream sync");
+      CK(cudaStreamSynchronize(b->stream), "stream sync");
+      fdlbm_status st = batch_upload(b);
+      if (st != FDLBM_OK) return st;
+      break;
+    }
+  }
+  // The batch's stream waits for work queued on the members' streams.
+  for (fdlbm_handle* h : b->members) {
+    CK(cudaEventRecord(b->done, h->stream), "event record");
+    CK(cudaStreamWaitEvent(b->stream, b->done, 0), "stream wait");
+  }
+  const BatchLaunch B = batch_launch_args(b);
+  int64_t left = n;
+  if (left >= BATCH_GRAPH_STEPS) {
+    if (!b->graph) {
+      // one plain launch first: it sets the kernel's shared-memory attribute outside
+      // the capture
+      CK(launch_batch_step(B, b->stream), "batch step");
+      --left;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cudaError_t e = cudaSuccess;
+      for (int q = 0; q < BATCH_GRAPH_STEPS && e == cudaSuccess; ++q) e = launch_batch_step(B, b->stream);
+      const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e != cudaSuccess ? e : e2, "capture batch steps");
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_fail(e, "instantiate batch graph");
+      }
+    }
+    for (; left >= BATCH_GRAPH_STEPS; left -= BATCH_GRAPH_STEPS) CK(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+  }
+  for (; left > 0; --left) CK(launch_batch_step(B, b->stream), "batch step");
+  b->counter += n;
+  for (fdlbm_handle* h : b->members) {
+    h->steps += n;
+    h->cur ^= int(n & 1);
+    h->mom_fresh = false;
+  }
+  return streams_wait(b->stream, b->done, b->members);
+}
+
+fdlbm_status fdlbm_batch_remove(fdlbm_batch* b, fdlbm_handle* h) {
+  if (!b || !h) return fail(FDLBM_EINVAL, "bad batch or handle");
+  auto it = std::find(b->members.begin(), b->members.end(), h);
+  if (it == b->members.end()) return fail(FDLBM_EINVAL, "handle is not a member of the batch");
+  DeviceGuard guard(b->device);
+  CK(cudaStreamSynchronize(b->stream), "stream sync");
+  b->members.erase(it);
+  return batch_upload(b);
+}
+
+int fdlbm_batch_size(const fdlbm_batch* b) { return b ? (int)b->members.size() : 0; }
+
+void fdlbm_batch_destroy(fdlbm_batch* b) {
+  if (!b) return;
+  {
+    DeviceGuard guard(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_free_device(b);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+  }
+  delete b;
 }
 
 void fdlbm_destroy(fdlbm_handle* h) {

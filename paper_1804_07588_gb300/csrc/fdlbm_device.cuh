@@ -845,6 +845,55 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   ledger_block_store(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
+// Batched time step: several independent lattices (members of a batch) advance in one
+// launch. A descriptor {2 member + role, first, count, member-local block index} selects
+// the member; the block copies the member's parameters into shared memory and takes its
+// buffers from the member's device state. members[m] = {buffer holding time level t when
+// counter = 0, step index when counter = 0}; counter counts the batch's steps (advanced
+// by batch_advance after every step), so one captured launch sequence serves every step.
+template <class PT, int NS, bool PHI>
+__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel_batch(
+    const DevParams* __restrict__ params, const DevState* __restrict__ states, const int2* __restrict__ members,
+    const int4* __restrict__ blocks, const uint32_t* __restrict__ counter) {
+  extern __shared__ float smem[];
+  __shared__ DevParams sP;
+  const int4 d = __ldg(blocks + blockIdx.x);
+  const int m = d.x >> 1;
+  {
+    const int* from = reinterpret_cast<const int*>(params + m);
+    int* to = reinterpret_cast<int*>(&sP);
+    for (int w = threadIdx.x; w < int(sizeof(DevParams) / sizeof(int)); w += blockDim.x) to[w] = __ldg(from + w);
+  }
+  __syncthreads();
+  const DevParams& P = sP;
+  const DevState& S = states[m];
+  const uint32_t c = *counter;
+  const int2 mm = __ldg(members + m);
+  const int src = (mm.x + int(c & 1U)) & 1, dstb = src ^ 1;
+  const uint32_t step = uint32_t(mm.y) + c;
+  const PT* hs = static_cast<const PT*>(S.h[src]);
+  PT* hd = static_cast<PT*>(S.h[dstb]);
+  const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
+  const int tid = threadIdx.x;
+  if ((d.x & 1) == 0) {
+    if (tid < d.z) {
+      const int2 g = __ldg(S.gas_list + d.y + tid);
+      gas_node<PT, NS, PHI, 0>(P, hs, hd, S.code, g.x, g.y, S.F[src], S.F[dstb], nullptr,
+                               paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.flags, smem, tid, step);
+    }
+    return;
+  }
+  double acc[LG_COUNT];
+#pragma unroll
+  for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
+  if (tid < d.z)
+    solid_node<PT, NS>(P, hs, hd, S.Ts[src], S.Ts[dstb], S.code, paper ? S.Tgas + (long long)src * P.n : nullptr,
+                       __ldg(S.solid_list + d.y + tid), acc, S.rw, d.y + tid, step);
+  ledger_block_store(acc, S.ledger + (long long)d.w * LG_COUNT);
+}
+
+__global__ void batch_advance(uint32_t* counter) { *counter += 1U; }
+
 // ---------------------------------------------------------------------------------------
 // Initialisation (FP64 arithmetic, then rounded), over every padded cell so that ghost
 // copies start consistent.
@@ -1148,6 +1197,38 @@ totals_partial_kernel(DevParams P, const float* __restrict__ mom, const PT* __re
   }
 }
 
+template <class PT, int NS, bool PHI>
+cudaError_t batch_launch(const BatchLaunch& B, cudaStream_t st) {
+  if (B.n_blocks <= 0) return cudaSuccess;
+  const size_t smem = gas_smem_bytes<NS, 0>();
+  static unsigned long long configured = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    e = cudaFuncSetAttribute(step_kernel_batch<PT, NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  step_kernel_batch<PT, NS, PHI><<<B.n_blocks, GB, smem, st>>>(B.params, B.states, B.members, B.blocks, B.counter);
+  batch_advance<<<1, 1, 0, st>>>(B.counter);
+  return cudaGetLastError();
+}
+
+template <class PT>
+cudaError_t dispatch_batch(const BatchLaunch& B, cudaStream_t st) {
+  const bool phi = B.energy_correction != 0;
+  switch (B.ns) {
+    case 1: return phi ? batch_launch<PT, 1, true>(B, st) : batch_launch<PT, 1, false>(B, st);
+    case 2: return phi ? batch_launch<PT, 2, true>(B, st) : batch_launch<PT, 2, false>(B, st);
+    case 3: return phi ? batch_launch<PT, 3, true>(B, st) : batch_launch<PT, 3, false>(B, st);
+    case 4: return phi ? batch_launch<PT, 4, true>(B, st) : batch_launch<PT, 4, false>(B, st);
+    case 5: return phi ? batch_launch<PT, 5, true>(B, st) : batch_launch<PT, 5, false>(B, st);
+    case 6: return phi ? batch_launch<PT, 6, true>(B, st) : batch_launch<PT, 6, false>(B, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 // Entry points of one storage type (explicitly instantiated once per type).
@@ -1168,6 +1249,11 @@ cudaError_t storage_step(const DevParams& P, const DevState& S, int src, bool mo
                          uint32_t step) {
   if (moments_only) return dispatch_gas<PT>(P, S, src, st);
   return dispatch_step<PT>(P, S, src, st, step);
+}
+
+template <class PT>
+cudaError_t storage_batch_step(const BatchLaunch& B, cudaStream_t st) {
+  return dispatch_batch<PT>(B, st);
 }
 
 template <class PT>
@@ -1198,6 +1284,7 @@ cudaError_t storage_totals_partial(const DevParams& P, const DevState& S, int cu
                                               cudaStream_t);                                                     \
   PREFIX template cudaError_t storage_step<PT>(const DevParams&, const DevState&, int, bool, cudaStream_t,       \
                                               uint32_t);                                                         \
+  PREFIX template cudaError_t storage_batch_step<PT>(const BatchLaunch&, cudaStream_t);                          \
   PREFIX template cudaError_t storage_populations_out<PT>(const DevParams&, const DevState&, int, float*,         \
                                                          cudaStream_t);                                          \
   PREFIX template cudaError_t storage_totals<PT>(const DevParams&, const DevState&, int, cudaStream_t);           \

@@ -128,6 +128,18 @@ cudaError_t launch_populations_out(const DevParams& P, const DevState& S, int cu
 cudaError_t launch_totals(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 cudaError_t launch_residual(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 
+// Batched stepping of several handles' lattices in one launch per step.
+struct BatchLaunch {
+  const DevParams* params;  // [members] device parameters
+  const DevState* states;   // [members] device buffers
+  const int2* members;      // [members] {buffer of time level t at counter 0, step index at counter 0}
+  const int4* blocks;       // {2 member + role, first, count, member-local block}
+  uint32_t* counter;        // steps taken since members[] was written
+  int n_blocks, ns, energy_correction, storage;
+};
+// One batched step (the step kernel, then the counter advance) on stream st.
+cudaError_t launch_batch_step(const BatchLaunch& B, cudaStream_t st);
+
 // Bytes of one stored population.
 inline size_t pop_bytes_per_value(int storage) { return storage == FDLBM_STORAGE_FP32 ? 4 : 2; }
 

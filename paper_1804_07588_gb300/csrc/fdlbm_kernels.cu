@@ -150,6 +150,15 @@ cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool mom
   }
 }
 
+cudaError_t launch_batch_step(const BatchLaunch& B, cudaStream_t st) {
+  switch (B.storage) {
+    case FDLBM_STORAGE_FP32: return storage_batch_step<float>(B, st);
+    case FDLBM_STORAGE_BF16: return storage_batch_step<__nv_bfloat16>(B, st);
+    case FDLBM_STORAGE_FP16: return storage_batch_step<__half>(B, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int ledger_slots(const DevParams& P) { return P.n_blocks > 0 ? P.n_blocks : 1; }
 
 cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st) {

@@ -91,7 +91,8 @@ _lib = None
 EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_populations",
            "fdlbm_enthalpy_balance", "fdlbm_residual", "fdlbm_set_fields", "fdlbm_info",
            "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_totals_static", "fdlbm_save",
-           "fdlbm_load", "fdlbm_destroy", "fdlbm_last_error")
+           "fdlbm_load", "fdlbm_batch_create", "fdlbm_batch_step", "fdlbm_batch_remove",
+           "fdlbm_batch_size", "fdlbm_batch_destroy", "fdlbm_destroy", "fdlbm_last_error")
 
 
 def library_path() -> str:
@@ -123,11 +124,17 @@ def load(build_if_missing: bool = True):
     L.fdlbm_totals_static.argtypes = [C.c_void_p, P(C.c_double), C.c_int]
     L.fdlbm_save.argtypes = [C.c_void_p, C.c_char_p]
     L.fdlbm_load.argtypes = [C.c_void_p, C.c_char_p]
+    L.fdlbm_batch_create.argtypes = [P(C.c_void_p), C.c_int, P(C.c_void_p)]
+    L.fdlbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
+    L.fdlbm_batch_remove.argtypes = [C.c_void_p, C.c_void_p]
+    L.fdlbm_batch_size.argtypes = [C.c_void_p]
+    L.fdlbm_batch_destroy.argtypes = [C.c_void_p]
     L.fdlbm_destroy.argtypes = [C.c_void_p]
     L.fdlbm_destroy.restype = None
     L.fdlbm_last_error.restype = C.c_char_p
     for name in EXPORTS[:-2]:
         getattr(L, name).restype = C.c_int
+    L.fdlbm_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -348,3 +355,38 @@ class Solver:
         d = {k: getattr(i, k) for k, _ in Info._fields_}
         d["stencil_counts"] = list(i.stencil_counts)
         return d
+
+
+class Batch:
+    """Several Solvers (same device, species count, storage and energy-correction switch)
+    advanced together: one kernel launch per time step for all of them, replayed from a
+    captured CUDA graph. Destroy (close) the batch before its solvers."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        b = C.c_void_p()
+        _check(load().fdlbm_batch_create(arr, len(self.solvers), C.byref(b)))
+        self._b = b
+
+    def step(self, n: int = 1):
+        _check(load().fdlbm_batch_step(self._b, int(n)))
+
+    def remove(self, solver):
+        _check(load().fdlbm_batch_remove(self._b, solver._h))
+        self.solvers = [s for s in self.solvers if s is not solver]
+
+    def __len__(self):
+        return load().fdlbm_batch_size(self._b)
+
+    def close(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            load().fdlbm_batch_destroy(b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
