@@ -149,9 +149,13 @@ def disk_mask(nx: int, ny: int, porosity: float, rmin: float, rmax: float, seed:
     target = (1.0 - porosity) * nx * ny
     n_solid = 0
     disks = []
-    cx_arr = np.zeros(0)
-    cy_arr = np.zeros(0)
-    r_arr = np.zeros(0)
+    # Overlap test against the disks of the neighbouring cells of a grid of cell size
+    # >= 2 rmax + gap (any disk closer than r + r' + gap has its centre there).
+    cell = 2.0 * rmax + gap
+    ncx = max(1, int(nx // cell))
+    ncy = max(1, int(ny // cell))
+    wx, wy = nx / ncx, ny / ncy
+    grid = {}
     tries = 0
     while n_solid < target:
         tries += 1
@@ -162,16 +166,24 @@ def disk_mask(nx: int, ny: int, porosity: float, rmin: float, rmax: float, seed:
         hi = nx - 1 - free_cols - r - 1
         cx = rng.uniform(lo, hi)
         cy = rng.uniform(0, ny)
-        if len(disks):
-            dy = np.abs(cy_arr - cy)
-            dy = np.minimum(dy, ny - dy)
-            d = np.hypot(cx_arr - cx, dy)
-            if np.any(d < r_arr + r + gap):
-                continue
+        gx, gy = min(int(cx // wx), ncx - 1), min(int(cy // wy), ncy - 1)
+        hit = False
+        for ix in range(max(gx - 1, 0), min(gx + 2, ncx)):
+            for iy in {(gy + o) % ncy for o in (-1, 0, 1)}:
+                for (ox, oy, orr) in grid.get((ix, iy), ()):
+                    dy = abs(oy - cy)
+                    dy = min(dy, ny - dy)
+                    if math.hypot(ox - cx, dy) < orr + r + gap:
+                        hit = True
+                        break
+                if hit:
+                    break
+            if hit:
+                break
+        if hit:
+            continue
         disks.append((cx, cy, r))
-        cx_arr = np.append(cx_arr, cx)
-        cy_arr = np.append(cy_arr, cy)
-        r_arr = np.append(r_arr, r)
+        grid.setdefault((gx, gy), []).append((cx, cy, r))
         xs = np.arange(int(math.floor(cx - r)), int(math.ceil(cx + r)) + 1)
         ys = np.arange(int(math.floor(cy - r)), int(math.ceil(cy + r)) + 1)
         dy = ys[:, None] - cy
@@ -258,3 +270,24 @@ def config1(**kw) -> dict:
     """2D D2Q9 porous bed 1024x512, catalytic disks r ~ U[6, 12], porosity 0.6, seed
     1000, plug inlet 0.01 (run length 20000 steps)."""
     return porous_disks(**kw)
+
+
+def batch_instances(n: int = 64, seed: int = 3000, nx_range=(256, 1024), ny_range=(128, 256),
+                    porosity=(0.6, 0.7), u_inlet=(0.005, 0.03), T_inlet_K=(450.0, 600.0)) -> list:
+    """Independent 2D porous beds of uneven size for batched stepping: per instance, nx
+    and ny uniform over multiples of 8 in the given ranges, porosity, plug inlet velocity
+    and inlet temperature uniform in their ranges (the inlet temperature is also the
+    reference T0, the initial gas and solid temperature), disks seeded by seed + 1 + i.
+    Porosity stays >= 0.6: random sequential addition with a 2-node gap jams near a
+    solid fraction of 0.45."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx = int(rng.integers(nx_range[0] // 8, nx_range[1] // 8 + 1)) * 8
+        ny = int(rng.integers(ny_range[0] // 8, ny_range[1] // 8 + 1)) * 8
+        por = float(rng.uniform(*porosity))
+        u = float(rng.uniform(*u_inlet))
+        T = float(rng.uniform(*T_inlet_K))
+        out.append(porous_disks(nx=nx, ny=ny, porosity=por, seed=seed + 1 + i, u_inlet=u, T0_K=T, T_init_K=T,
+                                T_inlet_K=T, T_solid_init_K=T, T_outer_K=T))
+    return out
