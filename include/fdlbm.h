@@ -136,6 +136,8 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, size_t bytes, void* ctx);
   void* alloc_ctx;
+  int band_rows;           /* rows per band of the step kernel's block order (gas blocks of a
+                              band, then its wall blocks); 0: 8 */
 } fdlbm_options;
 
 /* Counts and derived constants of a handle. */

@@ -388,7 +388,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     auto chunks = [&](int role, int first, int last) {
       for (int s0 = first; s0 < last; s0 += STEP_BLOCK) blocks.push_back(make_int4(role, s0, std::min(STEP_BLOCK, last - s0), 0));
     };
-    const int band = 8;
+    const int band = (opts && opts->band_rows > 0) ? opts->band_rows : 8;
     for (int y0 = 0; y0 < ny; y0 += band) {
       const int y1 = std::min(ny, y0 + band);
       chunks(0, gas_row[y0], gas_row[y1]);

@@ -67,7 +67,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 class Options(C.Structure):
     _fields_ = [("storage", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("band_rows", C.c_int)]
 
 
 class Info(C.Structure):
@@ -163,11 +163,12 @@ def _fields(init, keep):
 class Solver:
     """One coupled FD-LBM problem on one GPU, built from a problem dict (see
     ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
-    storage (FP32 arithmetic in every case)."""
+    storage (FP32 arithmetic in every case). band_rows: rows per band of the step
+    kernel's block order (0: 8; "auto": the autotuner's table)."""
 
     STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
 
-    def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32"):
+    def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32", band_rows: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
@@ -228,8 +229,12 @@ class Solver:
         if storage not in self.STORAGE:
             raise FdlbmError(-1, f"storage must be one of {sorted(self.STORAGE)}")
         self.storage = storage
+        if band_rows == "auto":
+            from . import autotune
+            band_rows = autotune.lookup(p, storage)
+        self.band_rows = int(band_rows)
         opts = Options(self.STORAGE[storage], device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
-                       self._free_cb, None)
+                       self._free_cb, None, self.band_rows)
         h = C.c_void_p()
         _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
                               C.byref(opts), C.byref(h)))
