@@ -461,20 +461,28 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   const float iden = 1.f / den;
   const float Ucx = ncx * iden, Ucy = ncy * iden;
 
-  // Per-species inputs of the collision parked in this thread's shared-memory column so
-  // that the species loop below is not unrolled (keeps the live register set small).
-  float* s_m = s_h + NS * Q * GB;  // [4 NS][GB]
+  // The species loop below is not unrolled (keeps the live register set small). Its
+  // inputs: the lagged divergence, parked in this thread's shared-memory column, and the
+  // species' density and momentum, formed again from the pulled values in the pull's
+  // order (the same FP32 sums).
+  float* s_m = s_h + NS * Q * GB;  // [NS][GB]
 #pragma unroll
-  for (int j = 0; j < NS; ++j) {
-    s_m[(4 * j + 0) * GB + tid] = m.drho[j];
-    s_m[(4 * j + 1) * GB + tid] = m.Jx[j];
-    s_m[(4 * j + 2) * GB + tid] = m.Jy[j];
-    s_m[(4 * j + 3) * GB + tid] = divq[j];
-  }
+  for (int j = 0; j < NS; ++j) s_m[j * GB + tid] = divq[j];
 #pragma unroll 1
   for (int j = 0; j < NS; ++j) {
-    const float drj = s_m[(4 * j + 0) * GB + tid], Jxj = s_m[(4 * j + 1) * GB + tid];
-    const float Jyj = s_m[(4 * j + 2) * GB + tid], dqj = s_m[(4 * j + 3) * GB + tid];
+    float h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = s_h[(j * Q + i) * GB + tid];
+    float drj = 0.f, axj = 0.f, ayj = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      drj += h[i];
+      if (EX(i) > 0) axj += h[i];
+      if (EX(i) < 0) axj -= h[i];
+      if (EY(i) > 0) ayj += h[i];
+      if (EY(i) < 0) ayj -= h[i];
+    }
+    const float Jxj = P.c[j] * axj, Jyj = P.c[j] * ayj, dqj = s_m[j * GB + tid];
     const float rho = P.rref[j] + drj;
     // f-momentum of the species (Eq. moments_of_g) and its velocity, limited for trace
     // species (reading R15).
@@ -520,10 +528,9 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
       float force = PSX(i) * gfx + PSY(i) * gfy;
       if (i == 0) force -= gphi;
       else if (i <= 4) force += 0.25f * gphi;
-      const float h = s_h[(j * Q + i) * GB + tid];
       // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi); the two
       // small differences are formed first so that FP32 keeps their precision.
-      hn[i] = fmaf(-om, h - fst, fmaf(-omt, fst - feq, h + force));
+      hn[i] = fmaf(-om, h[i] - fst, fmaf(-omt, fst - feq, h[i] + force));
     }
     // 32-bit element offsets: the host keeps ns Q plane below 2^31.
     const int pl = (int)P.plane;
@@ -579,7 +586,7 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, co
 
 template <int NS, int MODE>
 size_t gas_smem_bytes() {
-  return sizeof(float) * (MODE == 0 ? (NS * Q + 4 * NS) * GB : 1);
+  return sizeof(float) * (MODE == 0 ? (NS * Q + NS) * GB : 1);
 }
 
 // ---------------------------------------------------------------------------------------
