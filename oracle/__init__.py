@@ -13,7 +13,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "fdlbm_oracle.c")
+_SRCS = [os.path.join(_HERE, "fdlbm_oracle.c"), os.path.join(_HERE, "fdlbm_oracle3d.c")]
+_HDRS = [os.path.join(_HERE, "fdlbm_oracle.h"), os.path.join(_HERE, "fdlbm_oracle3d.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MAX_NS = 8
@@ -29,9 +30,9 @@ def build(force: bool = False, openmp: bool = False) -> str:
     """Compile the oracle into a shared library (plain C99, -O2, FP-contract off so the
     FP64 arithmetic follows the source order)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "fdlbm_oracle.h"))):
+            os.path.getmtime(f) for f in _SRCS + _HDRS):
         cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-o", _LIB + ".tmp", *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -50,6 +51,33 @@ class _Problem(C.Structure):
         ("T0_K", C.c_double), ("T_init_K", C.c_double), ("T_inlet_K", C.c_double),
         ("T_solid_init_K", C.c_double), ("T_outer_K", C.c_double),
         ("u_inlet", C.c_double), ("inlet_profile", C.c_int),
+        ("alpha_s", C.c_double), ("rhocp_s", C.c_double), ("kappa_f", C.c_double),
+        ("coupling", C.c_int),
+        ("nr", C.c_int),
+        ("nu", (C.c_int * MAX_NS) * MAX_NR),
+        ("k0", C.c_double * MAX_NR), ("Ea_Jmol", C.c_double * MAX_NR),
+        ("Keq", C.c_double * MAX_NR), ("dH_Jmol", C.c_double * MAX_NR),
+        ("rate_form", C.c_int * MAX_NR),
+        ("rho_w_tol", C.c_double), ("rho_w_maxit", C.c_int),
+        ("init_X", C.POINTER(C.c_double)), ("init_u", C.POINTER(C.c_double)),
+        ("init_T", C.POINTER(C.c_double)), ("init_Ts", C.POINTER(C.c_double)),
+        ("init_C", C.POINTER(C.c_double)),
+    ]
+
+
+class _Problem3(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("mask", C.POINTER(C.c_ubyte)),
+        ("face_bc", C.c_int * 6),
+        ("ns", C.c_int),
+        ("M_gmol", C.c_double * MAX_NS), ("tau1", C.c_double * MAX_NS),
+        ("tau2", C.c_double * MAX_NS), ("X_init", C.c_double * MAX_NS),
+        ("X_inlet", C.c_double * MAX_NS),
+        ("Pr", C.c_double), ("energy_correction", C.c_int),
+        ("T0_K", C.c_double), ("T_init_K", C.c_double), ("T_inlet_K", C.c_double),
+        ("T_solid_init_K", C.c_double), ("T_outer_K", C.c_double),
+        ("u_inlet", C.c_double),
         ("alpha_s", C.c_double), ("rhocp_s", C.c_double), ("kappa_f", C.c_double),
         ("coupling", C.c_int),
         ("nr", C.c_int),
@@ -93,6 +121,23 @@ def lib():
         L.ora_uc.restype = C.c_double
         L.ora_collide.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.ora_units.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.ora3_create.restype = C.c_void_p
+        L.ora3_create.argtypes = [C.POINTER(_Problem3), C.c_char_p, C.c_int]
+        L.ora3_destroy.argtypes = [C.c_void_p]
+        L.ora3_step.argtypes = [C.c_void_p, C.c_int]
+        L.ora3_nfields.argtypes = [C.c_void_p]
+        L.ora3_moments.argtypes = [C.c_void_p, dp]
+        L.ora3_populations.argtypes = [C.c_void_p, dp]
+        L.ora3_balance.argtypes = [C.c_void_p, dp]
+        L.ora3_residual.argtypes = [C.c_void_p, C.c_int]
+        L.ora3_residual.restype = C.c_double
+        L.ora3_counts.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
+        L.ora3_classes.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+        L.ora3_velocity.argtypes = [C.c_int, C.POINTER(C.c_int)]
+        L.ora3_equilibrium.argtypes = [C.c_double] * 6 + [dp]
+        L.ora3_psi.argtypes = [C.c_double, dp, dp, dp]
+        L.ora3_phi.argtypes = [C.c_double, dp]
+        L.ora3_collide.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -245,4 +290,159 @@ def collide(M, tau1, tau2, g, divq):
     go = np.zeros((ns, Q))
     mom = np.zeros(ns + 4)
     lib().ora_collide(ns, _dptr(M), _dptr(t1), _dptr(t2), _dptr(g), _dptr(dq), _dptr(go), _dptr(mom))
+    return go, mom
+
+
+# ---- D3Q19 oracle ------------------------------------------------------------------
+
+Q3 = 19
+
+
+def _fill_common(s, p, keep):
+    sp = p["species"]
+    s.ns = len(sp)
+    for j, d in enumerate(sp):
+        s.M_gmol[j] = d["M_gmol"]
+        s.tau1[j] = d["tau1"]
+        s.tau2[j] = d["tau2"]
+        s.X_init[j] = d["X_init"]
+        s.X_inlet[j] = d["X_inlet"]
+    for k in ("Pr", "T0_K", "T_init_K", "T_inlet_K", "T_solid_init_K", "T_outer_K",
+              "u_inlet", "alpha_s", "rhocp_s", "kappa_f", "rho_w_tol"):
+        setattr(s, k, float(p[k]))
+    for k in ("energy_correction", "coupling", "rho_w_maxit"):
+        setattr(s, k, int(p[k]))
+    rx = p["reactions"]
+    s.nr = len(rx)
+    for r, d in enumerate(rx):
+        for j, v in enumerate(d["nu"]):
+            s.nu[r][j] = int(v)
+        s.k0[r], s.Ea_Jmol[r], s.Keq[r], s.dH_Jmol[r] = d["k0"], d["Ea_Jmol"], d["Keq"], d["dH_Jmol"]
+        s.rate_form[r] = d["rate_form"]
+    init = p.get("init") or {}
+    for key, field in (("X", "init_X"), ("u", "init_u"), ("T_K", "init_T"), ("Ts_K", "init_Ts"),
+                       ("C", "init_C")):
+        if init.get(key) is not None:
+            a = np.ascontiguousarray(init[key], dtype=np.float64)
+            keep.append(a)
+            setattr(s, field, _dptr(a))
+
+
+class Oracle3:
+    """FP64 CPU solver of the D3Q19 form of the scheme for one 3D problem dict."""
+
+    def __init__(self, p: dict):
+        if p["dim"] != 3 or p["lattice"] != 19:
+            raise NotImplementedError("Oracle3 covers D3Q19")
+        if p.get("inlet_profile", 0) != 0:
+            raise NotImplementedError("Oracle3: plug inlet only")
+        L = lib()
+        s = _Problem3()
+        s.nx, s.ny, s.nz = p["nx"], p["ny"], p["nz"]
+        self._mask = np.ascontiguousarray(p["mask"], dtype=np.uint8)
+        s.mask = self._mask.ctypes.data_as(C.POINTER(C.c_ubyte))
+        for f in range(6):
+            s.face_bc[f] = p["face_bc"][f]
+        self._keep = []
+        _fill_common(s, p, self._keep)
+        err = C.create_string_buffer(256)
+        h = L.ora3_create(C.byref(s), err, 256)
+        if not h:
+            raise ValueError("oracle3: " + err.value.decode())
+        self._h = C.c_void_p(h)
+        self.ns = s.ns
+        self.nx, self.ny, self.nz = s.nx, s.ny, s.nz
+        self.n = s.nx * s.ny * s.nz
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.ora3_destroy(h)
+            self._h = None
+
+    def step(self, n: int = 1):
+        lib().ora3_step(self._h, int(n))
+
+    def moments(self) -> np.ndarray:
+        """[2*ns + 5, n]: rho_j, X_j, ux, uy, uz, T (K) on gas nodes, T_s (K) on solid nodes."""
+        nf = lib().ora3_nfields(self._h)
+        out = np.zeros((nf, self.n))
+        lib().ora3_moments(self._h, _dptr(out))
+        return out
+
+    def populations(self) -> np.ndarray:
+        out = np.zeros((self.ns, Q3, self.n))
+        lib().ora3_populations(self._h, _dptr(out))
+        return out
+
+    def balance(self) -> dict:
+        out = np.zeros(B_MASS + 4 * self.ns)
+        lib().ora3_balance(self._h, _dptr(out))
+        ns = self.ns
+        return {
+            "steps": out[B_STEPS], "E_gas": out[B_E_GAS], "E_gas0": out[B_E_GAS0],
+            "H_solid": out[B_H_SOLID], "H_solid0": out[B_H_SOLID0], "Q_reaction": out[B_Q_RXN],
+            "Q_wall": out[B_Q_WALL], "Q_couple": out[B_Q_COUPLE], "Q_fixedT": out[B_Q_FIXEDT],
+            "residual": out[B_RESIDUAL], "solid_residual": out[B_SOLID_RESIDUAL],
+            "eps_paper": out[B_EPS_PAPER], "noconv": out[B_NOCONV],
+            "mass": out[B_MASS:B_MASS + ns].copy(), "mass0": out[B_MASS + ns:B_MASS + 2 * ns].copy(),
+            "moles": out[B_MASS + 2 * ns:B_MASS + 3 * ns].copy(),
+            "moles0": out[B_MASS + 3 * ns:B_MASS + 4 * ns].copy(),
+        }
+
+    def residual(self, K: int) -> float:
+        return lib().ora3_residual(self._h, int(K))
+
+    def counts(self) -> dict:
+        out = (C.c_long * 11)()
+        lib().ora3_counts(self._h, out)
+        v = list(out)
+        return {"gas": v[0], "inlet": v[1], "outlet": v[2], "wall": v[3], "solid": v[4],
+                "stencil": v[5:11]}
+
+    def classes(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        lib().ora3_classes(self._h, out.ctypes.data_as(C.POINTER(C.c_int)))
+        return out
+
+
+def velocities3() -> np.ndarray:
+    """[19, 3] lattice velocities of the D3Q19 oracle, in its direction order."""
+    out = np.zeros((Q3, 3), np.int64)
+    v = (C.c_int * 3)()
+    for i in range(Q3):
+        lib().ora3_velocity(i, v)
+        out[i] = list(v)
+    return out
+
+
+def equilibrium3(rho, ux, uy, uz, M, T) -> np.ndarray:
+    out = np.zeros(Q3)
+    lib().ora3_equilibrium(rho, ux, uy, uz, M, T, _dptr(out))
+    return out
+
+
+def psi3(c):
+    px, py, pz = np.zeros(Q3), np.zeros(Q3), np.zeros(Q3)
+    lib().ora3_psi(c, _dptr(px), _dptr(py), _dptr(pz))
+    return px, py, pz
+
+
+def phi3(c):
+    out = np.zeros(Q3)
+    lib().ora3_phi(c, _dptr(out))
+    return out
+
+
+def collide3(M, tau1, tau2, g, divq):
+    """One-node D3Q19 collision: (g_out [ns, 19], moments rho_j.., ux, uy, uz, T, Tg)."""
+    M = np.ascontiguousarray(M, np.float64)
+    ns = len(M)
+    t1 = np.ascontiguousarray(tau1, np.float64)
+    t2 = np.ascontiguousarray(tau2, np.float64)
+    g = np.ascontiguousarray(g, np.float64).reshape(ns, Q3)
+    dq = np.ascontiguousarray(divq, np.float64)
+    go = np.zeros((ns, Q3))
+    mom = np.zeros(ns + 5)
+    lib().ora3_collide(ns, _dptr(M), _dptr(t1), _dptr(t2), _dptr(g), _dptr(dq), _dptr(go), _dptr(mom))
     return go, mom

@@ -221,16 +221,115 @@ def periodic_box(nx: int = 16, ny: int = 12, solid_rows: int = 0, solid_cols: in
     return _base(2, nx, ny, 1, mask, [PERIODIC] * 4, **kw)
 
 
+def sphere_mask(nx: int, ny: int, nz: int, porosity: float, rmin: float, rmax: float, seed: int,
+                free_cols: int = 12, max_spheres: int = 1_000_000):
+    """Seeded Boolean model of overlapping spheres, periodic in y and z.
+
+    Radii are uniform in [rmin, rmax]; centres are uniform in the box but keep
+    ``free_cols`` columns free of solid at the inlet and outlet ends. Spheres are added
+    until the digitised solid fraction of the lattice reaches ``1 - porosity`` (random
+    sequential addition of non-overlapping spheres jams near a solid fraction of 0.38,
+    below the 0.4-0.6 the 3D packings need, so spheres may overlap). The gas phase must
+    connect the inlet columns to the outlet columns (6-connected, periodic in y and z),
+    else a ValueError is raised. Returns (mask [nz, ny, nx], list of (cx, cy, cz, r)).
+    """
+    rng = np.random.default_rng(seed)
+    solid = np.zeros((nz, ny, nx), bool)
+    target = (1.0 - porosity) * nx * ny * nz
+    spheres = []
+    n_solid = 0
+    while n_solid < target:
+        if len(spheres) >= max_spheres:
+            raise RuntimeError("sphere packing did not reach the target porosity")
+        r = rng.uniform(rmin, rmax)
+        cx = rng.uniform(free_cols + r, nx - free_cols - r)
+        cy = rng.uniform(0, ny)
+        cz = rng.uniform(0, nz)
+        spheres.append((cx, cy, cz, r))
+        xs = np.arange(max(int(math.floor(cx - r)), 0), min(int(math.ceil(cx + r)), nx - 1) + 1)
+        ys = np.arange(int(math.floor(cy - r)), int(math.ceil(cy + r)) + 1)
+        zs = np.arange(int(math.floor(cz - r)), int(math.ceil(cz + r)) + 1)
+        inside = ((xs[None, None, :] - cx) ** 2 + (ys[None, :, None] - cy) ** 2
+                  + (zs[:, None, None] - cz) ** 2) <= r * r
+        zi, yi, xi = np.nonzero(inside)
+        zw, yw, xw = zs[zi] % nz, ys[yi] % ny, xs[xi]
+        n_solid += int((~solid[zw, yw, xw]).sum())
+        solid[zw, yw, xw] = True
+    if not _percolates(~solid):
+        raise ValueError("sphere packing: the gas phase does not connect inlet and outlet")
+    mask = np.where(solid, CATALYTIC, GAS).astype(np.uint8)
+    return mask, spheres
+
+
+def _percolates(gas: np.ndarray) -> bool:
+    """Breadth-first search over 6-connected gas cells (periodic in y and z) from the
+    x = 0 layer; True when it reaches the x = nx - 1 layer."""
+    nz, ny, nx = gas.shape
+    seen = np.zeros_like(gas)
+    front = np.argwhere(gas[:, :, 0])
+    front = np.concatenate([front, np.zeros((len(front), 1), np.int64)], axis=1)  # z, y, x
+    seen[front[:, 0], front[:, 1], front[:, 2]] = True
+    steps = ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))
+    while len(front):
+        nxt = []
+        for dz, dy, dx in steps:
+            z = (front[:, 0] + dz) % nz
+            y = (front[:, 1] + dy) % ny
+            x = front[:, 2] + dx
+            ok = (x >= 0) & (x < nx)
+            z, y, x = z[ok], y[ok], x[ok]
+            new = gas[z, y, x] & ~seen[z, y, x]
+            z, y, x = z[new], y[new], x[new]
+            seen[z, y, x] = True
+            nxt.append(np.stack([z, y, x], axis=1))
+        front = np.unique(np.concatenate(nxt), axis=0) if nxt else np.zeros((0, 3), np.int64)
+        if seen[:, :, nx - 1].any():
+            return True
+    return bool(seen[:, :, nx - 1].any())
+
+
+def porous_spheres(nx: int = 256, ny: int = 128, nz: int = 128, porosity: float = 0.5,
+                   rmin: float = 5.0, rmax: float = 10.0, seed: int = 2000, u_inlet: float = 0.01,
+                   **kw) -> dict:
+    """3D D3Q19 porous bed of catalytic FD-solid spheres (overlapping, Boolean model),
+    inlet x-, outlet x+, periodic in y and z. Defaults: the 256x128x128 packing with
+    radii U[5, 10], porosity 0.5, plug inlet 0.01."""
+    mask, _ = sphere_mask(nx, ny, nz, porosity, rmin, rmax, seed)
+    return _base(3, nx, ny, nz, mask, [INLET, OUTLET, PERIODIC, PERIODIC, PERIODIC, PERIODIC],
+                 u_inlet=u_inlet, inlet_profile=PLUG, **kw)
+
+
+def crop3(p: dict, nx: int, ny: int, nz: int, open_outlet: int = 2) -> dict:
+    """Corner crop [0, nz) x [0, ny) x [0, nx) of a 3D problem's geometry, with the same
+    faces (periodic in y and z) and the last ``open_outlet`` columns cleared of solid so
+    that the outlet has upstream gas."""
+    mask = np.asarray(p["mask"]).reshape(p["nz"], p["ny"], p["nx"])[:nz, :ny, :nx].copy()
+    if open_outlet:
+        mask[:, :, nx - open_outlet:] = GAS
+    q = {k: v for k, v in p.items() if k not in ("mask", "nx", "ny", "nz", "init")}
+    return _base(3, nx, ny, nz, mask, p["face_bc"], **{k: v for k, v in q.items()
+                                                        if k not in ("dim", "lattice", "face_bc")})
+
+
+def periodic_box3(nx: int = 12, ny: int = 10, nz: int = 8, solid_layers: int = 0, **kw) -> dict:
+    """Fully periodic 3D box; ``solid_layers`` > 0 puts a catalytic slab of that many
+    z-layers at the bottom."""
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    if solid_layers:
+        mask[:solid_layers] = CATALYTIC
+    return _base(3, nx, ny, nz, mask, [PERIODIC] * 6, **kw)
+
+
 def smooth_noise(shape, rng, modes: int = 4) -> np.ndarray:
-    """Sum of a few random low-order Fourier modes, scaled to max |value| = 1."""
-    ny, nx = shape
-    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    """Sum of a few random low-order Fourier modes, scaled to max |value| = 1 (2D shape
+    (ny, nx) or 3D shape (nz, ny, nx))."""
+    grids = np.meshgrid(*[np.arange(m, dtype=np.float64) for m in shape], indexing="ij")
     out = np.zeros(shape)
     for _ in range(modes):
-        kx = rng.integers(0, 4)
-        ky = rng.integers(0, 4)
+        ks = [rng.integers(0, 4) for _ in shape]  # drawn x first, then y (then z)
         ph = rng.uniform(0, 2 * np.pi)
-        out += rng.normal() * np.cos(2 * np.pi * (kx * x / nx + ky * y / ny) + ph)
+        arg = sum(k * g / m for k, g, m in zip(ks, grids[::-1], shape[::-1]))
+        out += rng.normal() * np.cos(2 * np.pi * arg + ph)
     m = np.abs(out).max()
     return out / m if m > 0 else out
 
@@ -242,21 +341,20 @@ def random_fields(p: dict, seed: int, dX: float = 0.2, du: float = 0.01,
     Mole fractions are scaled by (1 + dX * noise) and renormalised, velocities are
     +-``du``, gas and solid temperatures deviate by up to ``dT_K`` / ``dTs_K``.
     """
-    if p["dim"] != 2:
-        raise NotImplementedError("random_fields: 2D only")
     rng = np.random.default_rng(seed)
-    ny, nx = p["ny"], p["nx"]
+    shape = (p["ny"], p["nx"]) if p["dim"] == 2 else (p["nz"], p["ny"], p["nx"])
+    dim = p["dim"]
     ns = len(p["species"])
     X0 = np.array([s["X_init"] for s in p["species"]])
-    X = np.empty((ns, ny, nx))
+    X = np.empty((ns,) + shape)
     for j in range(ns):
-        X[j] = X0[j] * (1.0 + dX * smooth_noise((ny, nx), rng))
+        X[j] = X0[j] * (1.0 + dX * smooth_noise(shape, rng))
     X /= X.sum(axis=0, keepdims=True)
-    u = np.stack([du * smooth_noise((ny, nx), rng), du * smooth_noise((ny, nx), rng)])
-    T = p["T_init_K"] + dT_K * smooth_noise((ny, nx), rng)
-    Ts = p["T_solid_init_K"] + dTs_K * smooth_noise((ny, nx), rng)
-    n = nx * ny
-    return {"X": X.reshape(ns, n).copy(), "u": u.reshape(2, n).copy(),
+    u = np.stack([du * smooth_noise(shape, rng) for _ in range(dim)])
+    T = p["T_init_K"] + dT_K * smooth_noise(shape, rng)
+    Ts = p["T_solid_init_K"] + dTs_K * smooth_noise(shape, rng)
+    n = int(np.prod(shape))
+    return {"X": X.reshape(ns, n).copy(), "u": u.reshape(dim, n).copy(),
             "T_K": T.reshape(n).copy(), "Ts_K": Ts.reshape(n).copy()}
 
 
@@ -270,6 +368,18 @@ def config1(**kw) -> dict:
     """2D D2Q9 porous bed 1024x512, catalytic disks r ~ U[6, 12], porosity 0.6, seed
     1000, plug inlet 0.01 (run length 20000 steps)."""
     return porous_disks(**kw)
+
+
+def config2(**kw) -> dict:
+    """3D D3Q19 porous bed 256x128x128 of catalytic spheres r ~ U[5, 10] (overlapping),
+    porosity 0.5, seed 2000, plug inlet 0.01."""
+    return porous_spheres(**kw)
+
+
+def config2_crop(nx: int = 64, ny: int = 32, nz: int = 32, **kw) -> dict:
+    """The 64x32x32 corner crop of the config-2 packing (same seed), periodic in y and
+    z, outlet opened: the oracle-sized case of the 3D bed."""
+    return crop3(config2(**kw), nx, ny, nz)
 
 
 def batch_instances(n: int = 64, seed: int = 3000, nx_range=(256, 1024), ny_range=(128, 256),

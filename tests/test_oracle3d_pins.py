@@ -1,0 +1,375 @@
+"""Pins of the D3Q19 FP64 oracle against what the mathematics and the paper fix.
+
+The 3D lattice is the paper's announced extension (reading R1b). Each test checks the
+oracle against something other than itself: the textbook D3Q19 rest weights, moment
+identities of the folded product-form equilibrium and of the correction coefficients,
+conservation laws, fixed points, and decay rates of diffusion, entropy and shear modes
+against their transport coefficients (including the Prandtl number 5/2 of the
+uncorrected 3D model, which pins the 3D reading of the lattice heat-flux correction).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_07588_gb300 import workloads as W
+
+E = None
+
+
+def _vel():
+    global E
+    if E is None:
+        E = oracle.velocities3()
+    return E
+
+
+def test_velocity_set_d3q19():
+    """Rest, the 6 axis links and the 12 face diagonals, each with its opposite."""
+    e = _vel()
+    assert e.shape == (19, 3)
+    n2 = (e * e).sum(1)
+    assert (n2 == 0).sum() == 1 and (n2 == 1).sum() == 6 and (n2 == 2).sum() == 12
+    rows = {tuple(v) for v in e}
+    assert len(rows) == 19 and all(tuple(-v) in rows for v in e)
+
+
+def test_equilibrium3_rest_weights():
+    """At u = 0 and T = 1/3 the folded equilibrium is the standard D3Q19 lattice
+    (weights 1/3, 1/18, 1/36)."""
+    e = _vel()
+    f = oracle.equilibrium3(1.0, 0.0, 0.0, 0.0, 1.0, 1.0 / 3.0)
+    n2 = (e * e).sum(1)
+    ref = np.where(n2 == 0, 1 / 3, np.where(n2 == 1, 1 / 18, 1 / 36))
+    np.testing.assert_allclose(f, ref, rtol=1e-14)
+
+
+@pytest.mark.parametrize("M", [1.0, 8.936, 13.894, 21.83])
+def test_equilibrium3_moments(M):
+    """The folded equilibrium carries the species density, momentum rho u and pressure
+    tensor rho (u u + T/M I) (Eq. eq_state_pop moments, reading R1b)."""
+    rng = np.random.default_rng(21)
+    c = 1.0 / math.sqrt(M)
+    cv = c * _vel().astype(float)
+    for _ in range(20):
+        rho = rng.uniform(0.01, 5.0)
+        u = rng.uniform(-0.05, 0.05, 3)
+        T = rng.uniform(0.25, 0.4)
+        f = oracle.equilibrium3(rho, *u, M, T)
+        assert np.isclose(f.sum(), rho, rtol=1e-14)
+        np.testing.assert_allclose(cv.T @ f, rho * u, atol=1e-15, rtol=1e-12)
+        P = (cv[:, :, None] * cv[:, None, :] * f[:, None, None]).sum(0)
+        np.testing.assert_allclose(P, rho * (np.outer(u, u) + np.eye(3) * T / M), atol=1e-15, rtol=1e-12)
+        assert (f > 0).all()
+
+
+def test_equilibrium3_closed_form():
+    """Summing the fold by hand: a face diagonal (a, b) keeps rho w(a) w(b) (its two
+    corners add rho w(a) w(b) (w(+) + w(-)) and w(0) + w(+) + w(-) = 1); an axis link a
+    gets rho w(a) (w0_b w0_c - S_b S_c), the rest rho (w0_x w0_y w0_z + S_x S_y S_z), with
+    w0 = 1 - M u^2 - T and S = w(+) + w(-) = M u^2 + T per axis."""
+    rng = np.random.default_rng(22)
+    e = _vel()
+    for _ in range(10):
+        M = rng.uniform(1, 22)
+        rho = rng.uniform(0.1, 3)
+        u = rng.uniform(-0.04, 0.04, 3)
+        T = rng.uniform(0.28, 0.38)
+
+        def w(a, v):
+            return 1 - M * v * v - T if a == 0 else 0.5 * (a * math.sqrt(M) * v + M * v * v + T)
+
+        S = [M * v * v + T for v in u]
+        w0 = [w(0, v) for v in u]
+        f = oracle.equilibrium3(rho, *u, M, T)
+        for i, v in enumerate(e):
+            nz = [ax for ax in range(3) if v[ax] != 0]
+            if not nz:
+                ref = rho * (w0[0] * w0[1] * w0[2] + S[0] * S[1] * S[2])
+            elif len(nz) == 1:
+                a = nz[0]
+                b, cc = [ax for ax in range(3) if ax != a]
+                ref = rho * w(v[a], u[a]) * (w0[b] * w0[cc] - S[b] * S[cc])
+            else:
+                ref = rho * w(v[nz[0]], u[nz[0]]) * w(v[nz[1]], u[nz[1]])
+            assert np.isclose(f[i], ref, rtol=1e-12, atol=1e-16)
+
+
+@pytest.mark.parametrize("M", [1.0, 13.894, 21.83])
+def test_psi3_phi3_moments(M):
+    """psi (reading R4 on D3Q19) has zero mass, unit momentum along its axis, zero
+    energy and zero energy flux c_alpha c^2; phi has zero mass and momentum, unit energy
+    and an isotropic second moment."""
+    c = 1.0 / math.sqrt(M)
+    cv = c * _vel().astype(float)
+    c2 = (cv * cv).sum(1)
+    ps = oracle.psi3(c)
+    ph = oracle.phi3(c)
+    for al, p in enumerate(ps):
+        assert abs(p.sum()) < 1e-14
+        for be in range(3):
+            assert np.isclose((cv[:, be] * p).sum(), 1.0 if be == al else 0.0, atol=1e-14)
+        assert abs((c2 * p).sum()) < 1e-13
+        assert abs((cv[:, al] * c2 * p).sum()) < 1e-13
+    assert abs(ph.sum()) < 1e-13
+    assert np.abs(cv.T @ ph).max() < 1e-14
+    assert np.isclose((c2 * ph).sum(), 1.0, rtol=1e-13)
+    P = (cv[:, :, None] * cv[:, None, :] * ph[:, None, None]).sum(0)
+    np.testing.assert_allclose(P, np.eye(3) / 3.0, atol=1e-13)
+
+
+def _random_node3(ns, rng):
+    M = np.array([W.MOLAR_MASS[s] for s in W.SPECIES_ORDER])[:ns]
+    M = M / M.min()
+    g = np.zeros((ns, 19))
+    for j in range(ns):
+        g[j] = oracle.equilibrium3(rng.uniform(0.1, 3.0), *rng.uniform(-0.04, 0.04, 3), M[j],
+                                   rng.uniform(0.3, 0.36))
+        g[j] *= 1.0 + 0.05 * rng.normal(size=19)
+    return M, g
+
+
+TAU1 = np.array([0.8, 0.7, 1.0, 0.6, 0.9])
+TAU2 = np.array([0.7, 0.9, 0.65, 1.0, 0.75])
+
+
+def test_collision3_conserves_species_mass_and_mixture_momentum():
+    """Eq. final_kinetic_equation with U^c (reading R3) keeps every species mass and
+    the mixture momentum exactly on D3Q19."""
+    rng = np.random.default_rng(23)
+    e = _vel().astype(float)
+    for _ in range(20):
+        M, g = _random_node3(5, rng)
+        c = 1.0 / np.sqrt(M)
+        go, mom = oracle.collide3(M, TAU1, TAU2, g, rng.normal(size=5) * 1e-3)
+        np.testing.assert_allclose(go.sum(1), g.sum(1), rtol=1e-13)
+        J0 = ((c[:, None, None] * e[None]) * g[:, :, None]).sum((0, 1))
+        J1 = ((c[:, None, None] * e[None]) * go[:, :, None]).sum((0, 1))
+        assert np.abs(J1 - J0).max() < 1e-13
+
+
+def test_collision3_energy_equal_relaxation():
+    """Equal relaxation times: the collision changes the energy sum c^2 g by exactly
+    the Phi divergence sum_j divq_j (T(f) of Eq. moments_of_g with D = 3)."""
+    rng = np.random.default_rng(24)
+    tau = np.full(5, 0.8)
+    e2 = (_vel() ** 2).sum(1)
+    for _ in range(10):
+        M, g = _random_node3(5, rng)
+        c2 = (1.0 / M)[:, None] * e2[None]
+        dq = rng.normal(size=5) * 1e-3
+        go, _ = oracle.collide3(M, tau, tau, g, dq)
+        assert np.isclose((c2 * go).sum() - (c2 * g).sum(), dq.sum(), rtol=1e-9, atol=1e-14)
+
+
+def test_rest_state3_fixed_point_periodic():
+    p = W.periodic_box3(8, 6, 5, reactions=[])
+    o = oracle.Oracle3(p)
+    g0 = o.populations()
+    o.step(10)
+    np.testing.assert_allclose(o.populations(), g0, rtol=1e-13, atol=1e-15)
+
+
+def test_rest_state3_fixed_point_with_walls():
+    """Gas at rest at the wall temperature above an FD-solid slab stays at rest: the
+    diffusive wall re-emits the gas equilibrium, near-wall stencils reproduce uniform
+    fields, the solid is at equilibrium."""
+    p = W.periodic_box3(8, 6, 9, solid_layers=3, reactions=[])
+    o = oracle.Oracle3(p)
+    m0 = o.moments()
+    o.step(15)
+    np.testing.assert_allclose(o.moments(), m0, rtol=1e-12, atol=1e-14)
+
+
+def test_uniform_flow3_inlet_outlet_fixed_point():
+    nx, ny, nz = 16, 3, 3
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    p = W._base(3, nx, ny, nz, mask, [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC],
+                u_inlet=0.02, inlet_profile=W.PLUG, reactions=[])
+    n = nx * ny * nz
+    X = np.array([s["X_inlet"] for s in p["species"]])
+    p["init"] = {"X": np.repeat(X[:, None], n, 1), "u": np.vstack([np.full(n, 0.02), np.zeros(n), np.zeros(n)]),
+                 "T_K": np.full(n, p["T_inlet_K"]), "Ts_K": np.full(n, p["T_inlet_K"])}
+    o = oracle.Oracle3(p)
+    m0 = o.moments()
+    o.step(15)
+    np.testing.assert_allclose(o.moments(), m0, rtol=1e-12, atol=1e-14)
+
+
+def test_periodic3_conservation():
+    """Periodic 3D box from random smooth fields: species masses and the mixture
+    momentum are conserved to rounding."""
+    p = W.periodic_box3(10, 8, 6, reactions=[], Pr=0.7)
+    p["init"] = W.random_fields(p, seed=31)
+    o = oracle.Oracle3(p)
+    b0 = o.balance()
+    gas = o.classes() == 0
+
+    def momentum():
+        m = o.moments()
+        rho = m[:5].sum(0)
+        return np.array([(rho * m[10 + a])[gas].sum() for a in range(3)])
+
+    P0 = momentum()
+    o.step(20)
+    b = o.balance()
+    np.testing.assert_allclose(b["mass"], b0["mass"], rtol=1e-13)
+    assert np.abs(momentum() - P0).max() < 1e-12 * b0["mass"].sum() * 0.01
+
+
+def test_periodic3_energy_equal_relaxation():
+    p = W.periodic_box3(10, 8, 6, reactions=[], Pr=0.7)
+    for s in p["species"]:
+        s["tau1"] = s["tau2"] = 0.8
+    p["init"] = W.random_fields(p, seed=32)
+    o = oracle.Oracle3(p)
+    o.step(20)
+    b = o.balance()
+    assert abs(b["E_gas"] - b["E_gas0"]) < 1e-12 * b["E_gas0"]
+
+
+def _unit_mass(p, tau=0.25):
+    for s in p["species"]:
+        s["M_gmol"] = 2.016
+        s["tau1"] = s["tau2"] = tau
+    return p
+
+
+def test_reactive_closed_box3_exact_balance_unit_mass():
+    """Equal species masses (every species on-lattice): the reactive diffusive wall on
+    D3Q19 keeps exact mole bookkeeping and, with the conservative coupling, the gas
+    energy gain plus the solid enthalpy gain equal the reaction heat to rounding."""
+    p = _unit_mass(W.periodic_box3(10, 6, 8, solid_layers=3, reactions=[W.wgs_reaction(k0=2000.0)]))
+    o = oracle.Oracle3(p)
+    o.step(60)
+    b = o.balance()
+    dH = p["reactions"][0]["dH_Jmol"] / (3 * 8.314462618 * p["T0_K"])
+    extent = b["Q_reaction"] / (-dH)
+    assert extent > 1e-3
+    nu = np.array(p["reactions"][0]["nu"], float)
+    np.testing.assert_allclose(b["moles"] - b["moles0"], nu * extent, atol=1e-11 * b["moles0"].sum())
+    assert abs(b["solid_residual"]) < 1e-12 * b["H_solid0"]
+    assert abs(b["residual"]) < 1e-10 * b["Q_reaction"]
+
+
+def test_fixed_t_solid_eigenmode3():
+    """Eq. heat_equation_fd with the 7-point difference in a solid column between two
+    fixed-T faces (z): the discrete eigenmode sin(pi (z + 1) / (N + 1)) decays by
+    1 - 4 alpha sin^2(pi / (2 (N + 1))) per step."""
+    nx, ny, nz = 2, 2, 13
+    mask = np.full((nz, ny, nx), W.INERT, np.uint8)
+    p = W._base(3, nx, ny, nz, mask, [W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.FIXED_T, W.FIXED_T],
+                reactions=[])
+    z = np.arange(nz)
+    A = 6.0
+    Ts = p["T_outer_K"] + A * np.sin(np.pi * (z + 1) / (nz + 1))
+    p["init"] = {"Ts_K": np.repeat(Ts, nx * ny).astype(np.float64)}
+    o = oracle.Oracle3(p)
+    o.step(30)
+    lam = 1.0 - 4.0 * p["alpha_s"] * math.sin(math.pi / (2 * (nz + 1))) ** 2
+    got = o.moments()[-1].reshape(nz, ny, nx)[:, 0, 0] - p["T_outer_K"]
+    np.testing.assert_allclose(got, A * lam ** 30 * np.sin(np.pi * (z + 1) / (nz + 1)), rtol=1e-11)
+
+
+# ---------------------------------------------------------------------------------------
+# Transport against analytic decay rates
+# ---------------------------------------------------------------------------------------
+
+def _amp(f, nx):
+    x = np.arange(nx)
+    return 2.0 * (f * np.cos(2 * np.pi * x / nx)).mean()
+
+
+def _trace_rate3(species, nx, t0, t1):
+    p = W.periodic_box3(nx, 1, 1, reactions=[], energy_correction=0)
+    j = W.SPECIES_ORDER.index(species)
+    X0 = np.array([s["X_init"] for s in p["species"]])
+    X0[j] = 1e-3
+    x = np.arange(nx)
+    X = np.repeat(X0[:, None], nx, 1)
+    X[j] *= 1.0 + 0.01 * np.cos(2 * np.pi * x / nx)
+    X[4] = 1.0 - X[:4].sum(0)
+    p["init"] = {"X": X}
+    o = oracle.Oracle3(p)
+    o.step(t0)
+    a0 = _amp(o.moments()[5 + j], nx)
+    o.step(t1 - t0)
+    a1 = _amp(o.moments()[5 + j], nx)
+    k = 2 * np.pi / nx
+    return -math.log(a1 / a0) / (k * k * (t1 - t0)), p, j
+
+
+@pytest.mark.parametrize("species", ["CO2", "H2O"])
+def test_trace_species_diffusion3(species):
+    """Heavy trace species on D3Q19: D = tau2 T / M_j (extrapolated to k -> 0 from two
+    wavelengths; 1% tolerance)."""
+    D1, p, j = _trace_rate3(species, 48, 100, 900)
+    D2, _, _ = _trace_rate3(species, 96, 400, 3600)
+    D0 = (4.0 * D2 - D1) / 3.0
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    D_th = p["species"][j]["tau2"] * (1.0 / 3.0) / M[j]
+    assert abs(D0 / D_th - 1.0) < 0.01, (D1, D2, D0, D_th)
+
+
+@pytest.mark.parametrize("ec,pr,pr_eff", [(1, 1.0, 1.0), (1, 0.7, 0.7), (0, 1.0, 2.5)])
+def test_entropy_mode3_thermal_diffusivity(ec, pr, pr_eff):
+    """Isobaric temperature mode of an equal-mass gas on D3Q19 decays with
+    alpha = tau1 T / Pr. Without the energy correction the folded product form carries
+    (D - 1) / (D + 2) = 2/5 of the kinetic heat flux, i.e. Pr = 5/2 (the 3D counterpart
+    of the paper's Pr = 4 for D2Q9). 2% tolerance."""
+    nx, tau = 48, 0.25
+    p = _unit_mass(W.periodic_box3(nx, 1, 1, reactions=[], Pr=pr, energy_correction=ec), tau=tau)
+    x = np.arange(nx)
+    T = p["T_init_K"] * (1.0 + 0.002 * np.cos(2 * np.pi * x / nx))
+    X0 = np.array([s["X_init"] for s in p["species"]])
+    p["init"] = {"X": np.repeat(X0[:, None], nx, 1), "T_K": T, "C": p["T_init_K"] / T}
+    o = oracle.Oracle3(p)
+    k = 2 * np.pi / nx
+    ts, amps = [], []
+    dt = 10
+    nsamp = int(1.2 / (tau / 3.0 / pr_eff * k * k) / dt)
+    o.step(100)
+    for i in range(nsamp):
+        ts.append(100 + i * dt)
+        amps.append(_amp(o.moments()[13] - p["T_init_K"], nx))
+        o.step(dt)
+    rate = -np.polyfit(np.array(ts, float), np.log(np.array(amps)), 1)[0]
+    alpha = rate / (k * k)
+    alpha_th = tau * (1.0 / 3.0) / pr_eff
+    assert abs(alpha / alpha_th - 1.0) < 0.02, (alpha, alpha_th)
+
+
+def _shear_rate3(nz, tsteps):
+    p = W.periodic_box3(1, 1, nz, reactions=[], Pr=0.7)
+    z = np.arange(nz)
+    u = np.zeros((3, nz))
+    u[0] = 0.002 * np.cos(2 * np.pi * z / nz)
+    p["init"] = {"u": u}
+    o = oracle.Oracle3(p)
+    k = 2 * np.pi / nz
+    ts, amps = [], []
+    dt = 10
+    o.step(20)
+    for i in range(tsteps // dt):
+        ts.append(20 + i * dt)
+        amps.append(2.0 * (o.moments()[10] * np.cos(2 * np.pi * z / nz)).mean())
+        o.step(dt)
+    rate = -np.polyfit(np.array(ts, float), np.log(np.array(amps)), 1)[0]
+    return rate / (k * k), p
+
+
+def test_shear_wave3_mixture_viscosity():
+    """A shear wave u_x(z) in the 5-species mixture on D3Q19 decays with nu = mu / rho,
+    mu = sum_j tau1_j C_j T (Eq. multicomponent_mu); two wavelengths, 1% tolerance."""
+    nu1, p = _shear_rate3(32, 400)
+    nu2, _ = _shear_rate3(64, 1600)
+    nu0 = (4.0 * nu2 - nu1) / 3.0
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    X = np.array([s["X_init"] for s in p["species"]])
+    t1 = np.array([s["tau1"] for s in p["species"]])
+    mu = (t1 * X / 3.0).sum()
+    rho = (X * M).sum()
+    assert abs(nu0 / (mu / rho) - 1.0) < 0.01, (nu1, nu2, nu0, mu / rho)
