@@ -36,8 +36,12 @@ BYTES_PER_VALUE = {"fp32": 4, "bf16": 2, "fp16": 2}
 WORKLOAD = "porous-bed-d2q9-1024x512-5species-fp32"
 
 
-def workload_name(storage):
-    return WORKLOAD if storage == "fp32" else WORKLOAD.replace("-fp32", f"-{storage}-storage")
+WORKLOAD3 = "porous-bed-d3q19-256x128x128-5species-fp32"
+
+
+def workload_name(storage, three_d=False):
+    w = WORKLOAD3 if three_d else WORKLOAD
+    return w if storage == "fp32" else w.replace("-fp32", f"-{storage}-storage")
 
 
 def parse():
@@ -49,9 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-steady", action="store_true", help="skip the time-to-steady runs")
-    ap.add_argument("--workload", default="bed", choices=["bed", "batch"],
+    ap.add_argument("--workload", default="bed", choices=["bed", "batch", "bed3d"],
                     help="bed: the 1024x512 porous bed; batch: 64 independent porous beds of uneven "
-                         "size stepped together (one launch per step)")
+                         "size stepped together (one launch per step); bed3d: the D3Q19 256x128x128 "
+                         "sphere packing")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="population storage (FP32 arithmetic in every case)")
     return ap.parse_args()
@@ -71,24 +76,28 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(three_d=False):
+    """Hash of the sources of the step kernel of the D2Q9 (or D3Q19) path."""
     h = hashlib.sha256()
-    for f in ("fdlbm_device.cuh", "fdlbm_kernels.cu", "fdlbm_internal.h"):
+    files = ("fdlbm_device.cuh", "fdlbm3d_kernels.cu", "fdlbm_internal.h") if three_d else \
+        ("fdlbm_device.cuh", "fdlbm_kernels.cu", "fdlbm_internal.h")
+    for f in files:
         with open(os.path.join(ROOT, "paper_1804_07588_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
+def ncu_traffic(three_d=False):
     """DRAM bytes per step-kernel launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    name = "step_kernel3_traffic.json" if three_d else "step_kernel_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_source_sha") != kernel_source_hash():
+    if d.get("kernel_source_sha") != kernel_source_hash(three_d):
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -161,10 +170,16 @@ def crop_problem(n_target: int):
     return p, f"top-left {w}x{h} crop of the 1024x512 bed (same disk packing), outlet opened"
 
 
-def oracle_throughput(seconds: float = 10.0, n_target: int = 16384, max_steps=None):
+def oracle_throughput(seconds: float = 10.0, n_target: int = 16384, max_steps=None, three_d=False):
     import oracle
-    p, desc = crop_problem(n_target)
-    o = oracle.Oracle(p)
+    if three_d:
+        from paper_1804_07588_gb300 import workloads as W
+        p = W.config2_crop()
+        desc = "64x32x32 corner crop of the 256x128x128 sphere packing (same seed), outlet opened"
+        o = oracle.Oracle3(p)
+    else:
+        p, desc = crop_problem(n_target)
+        o = oracle.Oracle(p)
     n_gas = o.counts()["gas"]
     ns = len(p["species"])
     t0 = time.perf_counter()
@@ -335,7 +350,9 @@ def run_fdlbm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local_rank}"))
     dev = local_rank
     torch.cuda.set_device(dev)
-    p = workloads.config1()
+    three_d = args.workload == "bed3d"
+    p = workloads.config2() if three_d else workloads.config1()
+    Q = 19 if three_d else 9
     s = fdlbm.Solver(p, device=dev, storage=args.storage)
     info = s.info()
     ns = info["ns"]
@@ -370,7 +387,7 @@ def run_fdlbm(args, rank, world, local_rank):
     total_ms = max_over_ranks(total_ms, dist, device=f"cuda:{dev}")
     value = whole_job_value(ns, n_gas, args.steps, world, total_ms)
     step_kernel_ms = ms_step / max(timed, 1)
-    alg_bytes = 18 * BYTES_PER_VALUE[args.storage] * ns * n_gas
+    alg_bytes = 2 * Q * BYTES_PER_VALUE[args.storage] * ns * n_gas
     achieved = alg_bytes / (step_kernel_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
 
@@ -384,8 +401,17 @@ def run_fdlbm(args, rank, world, local_rank):
         m = s2.moments_host()
         s2.sync()
         el = time.perf_counter() - t0
-        n = p["nx"] * p["ny"]
-        h2d = 4 * n + 4 * (info["n_wall"] + info["n_solid"]) + 8 * (ns + 5) * n + 8 * (p["ny"] + ns + 1) + n
+        n = info["n_nodes"]
+        if three_d:
+            # mask, FP64 initial fields (X, u, T, Ts, C), inlet state, 64-bit code words of the
+            # padded lattice, gas list, solid list, block table
+            blocks = (n_gas + 127) // 128 + (info["n_wall"] + info["n_solid"]) // 128 + p["nz"] + 1
+            pitch = (p["nx"] + 8 + 31) // 32 * 32
+            plane = pitch * (p["ny"] + 6) * (p["nz"] + 6)
+            h2d = n + 8 * (ns + 6) * n + 8 * (ns + 2) + 8 * plane + 8 * n_gas + \
+                4 * (info["n_wall"] + info["n_solid"]) + 16 * blocks
+        else:
+            h2d = 4 * n + 4 * (info["n_wall"] + info["n_solid"]) + 8 * (ns + 5) * n + 8 * (p["ny"] + ns + 1) + n
         d2h = m.nbytes
         e2e = {"value": ns * n_gas * args.steps / el / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
@@ -395,12 +421,12 @@ def run_fdlbm(args, rank, world, local_rank):
         del np
 
     tts = None
-    if rank == 0 and not args.no_steady:
+    if rank == 0 and not args.no_steady and not three_d:
         tts = time_to_steady(fdlbm, workloads, device=dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, desc, el = oracle_throughput(seconds=10.0)
+        v, desc, el = oracle_throughput(seconds=10.0, three_d=three_d)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
 
@@ -409,7 +435,9 @@ def run_fdlbm(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args.storage), "nx": p["nx"], "ny": p["ny"], "porosity": 0.6,
+            "config": {"workload": workload_name(args.storage, three_d), "nx": p["nx"], "ny": p["ny"],
+                       **({"nz": p["nz"], "lattice": "D3Q19"} if three_d else {"lattice": "D2Q9"}),
+                       "porosity": 0.5 if three_d else 0.6,
                        "storage": {"fp32": "FP32 deviations", "bf16": "BF16 deviations, stochastic rounding",
                                    "fp16": "FP16 deviations (power-of-two scale per species), stochastic "
                                            "rounding"}[args.storage],
@@ -418,7 +446,7 @@ def run_fdlbm(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": ncu_traffic() if args.storage == "fp32" else None,
+                         "traffic": ncu_traffic(three_d) if args.storage == "fp32" else None,
                          "peak_kind": peak_kind + " copy bandwidth",
                          "alg_bytes_per_launch": alg_bytes, "kernel_ms_per_launch": step_kernel_ms},
             "cpu_baseline": cpu,

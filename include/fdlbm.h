@@ -22,8 +22,12 @@
  *     the handle's device; transfers and kernels run on the handle's stream.
  *   - Device memory is taken from the caller's allocator (fdlbm_options.alloc) or
  *     cudaMalloc and released by fdlbm_destroy.
- *   - Lattice nodes are indexed n = x + nx * y (x fastest); field arrays are
- *     [field][n] in that order.
+ *   - Lattice nodes are indexed n = x + nx * y (2D) or n = x + nx * (y + ny * z) (3D),
+ *     x fastest; field arrays are [field][n] in that order.
+ *   - D3Q19 handles (fdlbm_geometry.lattice = FDLBM_D3Q19) support create, step, sync,
+ *     moments, populations, enthalpy balance, residual, set_fields, info, profiling and
+ *     destroy with any population storage and a plug inlet; checkpoints, batches and
+ *     the allocation-free totals are D2Q9 only and return EINVAL for a 3D handle.
  *   - Error messages of the last failing call on this thread: fdlbm_last_error().
  */
 #ifndef FDLBM_H
@@ -53,7 +57,10 @@ typedef enum {
   FDLBM_EIO = -8        /* checkpoint file missing, unreadable, truncated or not written */
 } fdlbm_status;
 
-enum { FDLBM_D2Q9 = 9 };
+/* Lattices: the paper's D2Q9 and the D3Q19 extension it announces (Sec. 2), built from
+ * the D3Q27 product-form equilibrium by folding each corner population onto its three
+ * face diagonals (+), its three axis links (-) and the rest population (+). */
+enum { FDLBM_D2Q9 = 9, FDLBM_D3Q19 = 19 };
 /* Face boundary kinds for faces x-, x+, y-, y+ (indices 0..3). Periodic faces come in
  * pairs; inlet only on x-, outlet only on x+. */
 enum { FDLBM_FACE_PERIODIC = 0, FDLBM_FACE_INLET = 1, FDLBM_FACE_OUTLET = 2,
@@ -77,9 +84,10 @@ enum { FDLBM_STORAGE_FP32 = 0, FDLBM_STORAGE_BF16 = 1, FDLBM_STORAGE_FP16 = 2 };
 /* Lattice and geometry (Sec. 4.3: walls sit on the solid nodes next to the gas). */
 typedef struct {
   int nx, ny;              /* lattice size, each >= 4 */
-  int lattice;             /* FDLBM_D2Q9 */
-  const uint8_t* mask;     /* host, nx*ny, FDLBM_MASK_* */
-  int face_bc[4];          /* FDLBM_FACE_* for x-, x+, y-, y+ */
+  int lattice;             /* FDLBM_D2Q9 or FDLBM_D3Q19 */
+  const uint8_t* mask;     /* host, nx*ny (2D) or nx*ny*nz (3D), x fastest then y, FDLBM_MASK_* */
+  int face_bc[6];          /* FDLBM_FACE_* for x-, x+, y-, y+, z-, z+ (z faces: 3D only) */
+  int nz;                  /* D3Q19: z size >= 4; ignored for D2Q9 */
 } fdlbm_geometry;
 
 /* One gas species (Sec. 2; relaxation times in lattice units). */
@@ -117,8 +125,8 @@ typedef struct {
 } fdlbm_kinetics;
 
 /* Optional initial fields (host, may be NULL individually): mole fractions [ns][n],
- * velocity [2][n] (lattice), gas and solid temperatures [n] (K), molar concentration
- * [n] (lattice, default 1). */
+ * velocity [D][n] (lattice, D = 2 or 3), gas and solid temperatures [n] (K), molar
+ * concentration [n] (lattice, default 1). */
 typedef struct {
   const double* X;
   const double* u;
@@ -188,13 +196,13 @@ fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n);
 /* Wait for the handle's stream and report sticky device errors (EUNSTABLE). */
 fdlbm_status fdlbm_sync(fdlbm_handle* h);
 
-/* Moment fields at the current time into dst, [2 ns + 4][n] float32: rho_j, X_j, ux, uy,
- * T (K) on gas nodes, T_s (K) on solid nodes, 0 elsewhere. dst_on_device selects a
- * device or host destination; a host copy is synchronous. */
+/* Moment fields at the current time into dst, [2 ns + 2 + D][n] float32: rho_j, X_j, ux,
+ * uy (, uz), T (K) on gas nodes, T_s (K) on solid nodes, 0 elsewhere. dst_on_device
+ * selects a device or host destination; a host copy is synchronous. */
 fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device);
 
 /* Stored populations g* (post-collision on gas, inlet and outlet nodes, emissions on
- * wall nodes), [ns][9][n] float32 (absolute values, not deviations). */
+ * wall nodes), [ns][Q][n] float32 (Q = 9 or 19; absolute values, not deviations). */
 fdlbm_status fdlbm_populations(fdlbm_handle* h, float* dst, int dst_on_device);
 
 /* FP64 ledger (synchronous). */

@@ -63,6 +63,7 @@ struct fdlbm_handle {
   float* out_buf = nullptr;   // staging for host copies of outputs
   // host-side description kept for re-initialisation and outputs
   int nx = 0, ny = 0, ns = 0;
+  int dim = 2, nz = 1;        // D2Q9 (2) or D3Q19 (3)
   std::vector<uint32_t> code;
   std::vector<double> X_init, X_inlet, inlet_u;
   double T0 = 0, T_init_lat = 0, T_inlet_lat = 0, Ts_init_lat = 0;
@@ -169,6 +170,9 @@ struct Geo {
 };
 
 fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f);
+fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, int ns, const fdlbm_transport* tr,
+                     const fdlbm_kinetics* kin, const fdlbm_fields* init, const fdlbm_options* opts,
+                     fdlbm_handle** out);
 
 }  // namespace
 
@@ -183,7 +187,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   *out = nullptr;
   if (!geom || !species || !tr || !kin || !geom->mask)
     return fail(FDLBM_EINVAL, "geometry, species, transport, kinetics and mask are required");
-  if (geom->lattice != FDLBM_D2Q9) return fail(FDLBM_EINVAL, "only the D2Q9 lattice is supported");
+  if (geom->lattice != FDLBM_D2Q9 && geom->lattice != FDLBM_D3Q19)
+    return fail(FDLBM_EINVAL, "lattice must be FDLBM_D2Q9 or FDLBM_D3Q19 (got %d)", geom->lattice);
   if (geom->nx < 4 || geom->ny < 4) return fail(FDLBM_EINVAL, "lattice must be at least 4x4 (got %dx%d)", geom->nx, geom->ny);
   if ((long long)geom->nx * geom->ny > (1LL << 29)) return fail(FDLBM_EINVAL, "lattice too large (at most 2^29 nodes)");
   if (n_species < 1 || n_species > MAX_NS) return fail(FDLBM_EINVAL, "n_species must be 1..%d", MAX_NS);
@@ -223,6 +228,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     for (int j = 0; j < n_species; ++j)
       if (kin->nu[r][j] < -4 || kin->nu[r][j] > 4) return fail(FDLBM_EINVAL, "reaction %d: |nu| <= 4", r);
   }
+
+  if (geom->lattice == FDLBM_D3Q19) return create3(geom, species, n_species, tr, kin, init, opts, out);
 
   fdlbm_handle* h = new fdlbm_handle();
   h->device = opts ? opts->device : 0;
@@ -534,7 +541,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.ledger, double, (size_t)LG_COUNT * ledger_slots(P));
   ALLOC(S.rw, float, (size_t)ns * std::max<size_t>(walls.size(), 1));
   ALLOC(S.flags, int, 4);
-  ALLOC(S.red, double, totals_count(ns) + residual_count(ns) + LG_COUNT + 8);
+  ALLOC(S.red, double, totals_count(ns) + residual_count3(ns) + LG_COUNT + 8);
   ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
 #undef ALLOC
   cudaError_t e = cudaMemcpyAsync(S.code, pcode.data(), sizeof(uint32_t) * pcode.size(), cudaMemcpyHostToDevice,
@@ -569,9 +576,12 @@ fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n) {
     if (h->profiling && h->events_used + 2 <= h->events.size()) {
       cudaEvent_t* ev = h->events.data() + h->events_used;
       CK(cudaEventRecord(ev[0], h->stream), "event record");
-      CK(launch_step(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
+      if (h->dim == 3) CK(launch_step3(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
+      else CK(launch_step(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
       CK(cudaEventRecord(ev[1], h->stream), "event record");
       h->events_used += 2;
+    } else if (h->dim == 3) {
+      CK(launch_step3(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
     } else {
       CK(launch_step(h->P, h->S, h->cur, false, h->stream, uint32_t(h->steps + k)), "step launch");
     }
@@ -600,7 +610,8 @@ fdlbm_status ensure_moments(fdlbm_handle* h) {
   if (h->mom_fresh) return FDLBM_OK;
   // The buffer read by the last step still holds its input: recompute that step's
   // pre-collision moments (time t) from it.
-  CK(launch_step(h->P, h->S, h->cur ^ 1, true, h->stream), "moments launch");
+  if (h->dim == 3) CK(launch_step3(h->P, h->S, h->cur ^ 1, true, h->stream), "moments launch");
+  else CK(launch_step(h->P, h->S, h->cur ^ 1, true, h->stream), "moments launch");
   h->mom_fresh = true;
   return FDLBM_OK;
 }
@@ -608,14 +619,18 @@ fdlbm_status ensure_moments(fdlbm_handle* h) {
 fdlbm_status read_totals(fdlbm_handle* h, double* tot) {
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
-  CK(launch_totals(h->P, h->S, h->cur, h->stream), "totals launch");
+  if (h->dim == 3) CK(launch_totals3(h->P, h->S, h->cur, h->stream), "totals launch");
+  else CK(launch_totals(h->P, h->S, h->cur, h->stream), "totals launch");
   CK(cudaMemcpyAsync(tot, h->S.red, sizeof(double) * totals_count(h->ns), cudaMemcpyDeviceToHost, h->stream),
      "read totals");
   CK(cudaStreamSynchronize(h->stream), "stream sync");
   return FDLBM_OK;
 }
 
+fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f);
+
 fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
+  if (h->dim == 3) return upload_and_init3(h, f);
   const int n = h->nx * h->ny, ns = h->ns;
   const double tl = 1.0 / (3.0 * h->T0);
   std::vector<double> X((size_t)ns * n), u(2 * (size_t)n, 0.0), T(n), Ts(n), C(n, 1.0);
@@ -679,6 +694,452 @@ fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
   return FDLBM_OK;
 }
 
+
+// ---- D3Q19 handles ------------------------------------------------------------------
+// D3Q19 velocities in the order of the 3D kernels (rest, +-x, +-y, +-z, face diagonals).
+constexpr int H3X[Q19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int H3Y[Q19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int H3Z[Q19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+struct Geo3 {
+  int nx, ny, nz;
+  bool px, py, pz;
+  std::vector<uint32_t> cls;
+  static int wrap(int v, int len, bool per) {
+    if (v >= 0 && v < len) return v;
+    return per ? ((v % len) + len) % len : -1;
+  }
+  long at(int x, int y, int z) const {
+    x = wrap(x, nx, px);
+    y = wrap(y, ny, py);
+    z = wrap(z, nz, pz);
+    if (x < 0 || y < 0 || z < 0) return -1;
+    return x + (long)nx * (y + (long)ny * z);
+  }
+  uint32_t cls_at(int x, int y, int z) const {
+    const long k = at(x, y, z);
+    return k < 0 ? uint32_t(OUTSIDE) : cls[k];
+  }
+  // Node (x, y, z) holds a population moving along i (reading R6).
+  bool emits(int x, int y, int z, int i) const {
+    const uint32_t c = cls_at(x, y, z);
+    if (c == GAS || c == INLET || c == OUTLET) return true;
+    return c == WALL && cls_at(x + H3X[i], y + H3Y[i], z + H3Z[i]) == GAS;
+  }
+  uint32_t stencil(int x, int y, int z, int i) const {
+    const int ex = H3X[i], ey = H3Y[i], ez = H3Z[i];
+    const bool up2 = emits(x - 2 * ex, y - 2 * ey, z - 2 * ez, i);
+    const bool self = emits(x, y, z, i);
+    const bool down = emits(x + ex, y + ey, z + ez, i);
+    const bool up3 = emits(x - 3 * ex, y - 3 * ey, z - 3 * ez, i);
+    if (up2 && self) return ST_CENTRAL;
+    if (self && down) return ST_FORWARD;
+    if (up2 && up3) return ST_BACKWARD;
+    if (self) return ST_LIN_S0;
+    if (up2) return ST_LIN_S2;
+    return ST_NONE;
+  }
+};
+
+// D3Q19 rest-equilibrium weight of direction i at lattice temperature T.
+double wrest3_h(int i, double T) {
+  const int nz = (H3X[i] != 0) + (H3Y[i] != 0) + (H3Z[i] != 0);
+  if (nz == 0) return (1.0 - T) * (1.0 - T) * (1.0 - T) + T * T * T;
+  if (nz == 1) return 0.5 * T * (1.0 - 2.0 * T);
+  return 0.25 * T * T;
+}
+
+fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, int ns, const fdlbm_transport* tr,
+                     const fdlbm_kinetics* kin, const fdlbm_fields* init, const fdlbm_options* opts,
+                     fdlbm_handle** out) {
+  const int nx = geom->nx, ny = geom->ny, nz = geom->nz;
+  if (nz < 4) return fail(FDLBM_EINVAL, "D3Q19: nz must be at least 4 (got %d)", nz);
+  if ((long long)nx * ny * nz > (1LL << 29)) return fail(FDLBM_EINVAL, "lattice too large (at most 2^29 nodes)");
+  const int* fb = geom->face_bc;
+  for (int f = 4; f < 6; ++f)
+    if (fb[f] < 0 || fb[f] > 4) return fail(FDLBM_EINVAL, "face_bc[%d] invalid", f);
+  if ((fb[4] == FDLBM_FACE_PERIODIC) != (fb[5] == FDLBM_FACE_PERIODIC))
+    return fail(FDLBM_EINVAL, "periodic faces must come in pairs");
+  if (fb[4] == FDLBM_FACE_INLET || fb[4] == FDLBM_FACE_OUTLET || fb[5] == FDLBM_FACE_INLET ||
+      fb[5] == FDLBM_FACE_OUTLET)
+    return fail(FDLBM_EINVAL, "inlet only on x-, outlet only on x+");
+  if (tr->alpha_s > 1.0 / 6.0) return fail(FDLBM_EINVAL, "alpha_s must be <= 1/6 (explicit FD stability in 3D)");
+  if (tr->inlet_profile != FDLBM_PROFILE_PLUG) return fail(FDLBM_EINVAL, "D3Q19: plug inlet only");
+  const int storage = opts ? opts->storage : FDLBM_STORAGE_FP32;
+  double Mmin = 1e300;
+  for (int j = 0; j < ns; ++j) Mmin = std::min(Mmin, species[j].M_gmol);
+
+  fdlbm_handle* h = new fdlbm_handle();
+  h->device = opts ? opts->device : 0;
+  DeviceGuard guard(h->device);
+  h->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+  if (opts) {
+    h->ualloc = opts->alloc;
+    h->ufree = opts->free;
+    h->uctx = opts->alloc_ctx;
+  }
+  const long n = (long)nx * ny * nz;
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->ns = ns;
+  h->dim = 3;
+  auto bail = [&](fdlbm_status st) {
+    release(h);
+    delete h;
+    return st;
+  };
+
+  // Node classes (gas, inlet, outlet; solid nodes with a gas neighbour along any of the
+  // 18 links are interface wall nodes).
+  Geo3 G;
+  G.nx = nx;
+  G.ny = ny;
+  G.nz = nz;
+  G.px = fb[0] == FDLBM_FACE_PERIODIC;
+  G.py = fb[2] == FDLBM_FACE_PERIODIC;
+  G.pz = fb[4] == FDLBM_FACE_PERIODIC;
+  G.cls.assign(n, GAS);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = x + (long)nx * (y + (long)ny * z);
+        const uint8_t m = geom->mask[k];
+        if (m > 2) return bail(fail(FDLBM_EINVAL, "mask value %d at (%d,%d,%d)", m, x, y, z));
+        if (m == FDLBM_MASK_GAS) {
+          if (x == 0 && fb[0] == FDLBM_FACE_INLET) G.cls[k] = INLET;
+          else if (x == nx - 1 && fb[1] == FDLBM_FACE_OUTLET) G.cls[k] = OUTLET;
+          else G.cls[k] = GAS;
+        } else {
+          G.cls[k] = SOLID;
+        }
+      }
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = x + (long)nx * (y + (long)ny * z);
+        if (G.cls[k] != SOLID) continue;
+        for (int i = 1; i < Q19; ++i)
+          if (G.cls_at(x + H3X[i], y + H3Y[i], z + H3Z[i]) == GAS) G.cls[k] = WALL;
+      }
+  // Code words; geometry checks.
+  std::vector<uint64_t> code(n, 0);
+  std::vector<int32_t> walls, solids;
+  std::vector<int> gas_z(nz + 1, 0), wall_z(nz + 1, 0);
+  long gcount = 0;
+  for (int z = 0; z < nz; ++z) {
+    gas_z[z] = (int)gcount;
+    wall_z[z] = (int)walls.size();
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = x + (long)nx * (y + (long)ny * z);
+        const uint32_t c = G.cls[k];
+        uint64_t w = c;
+        if (geom->mask[k] == FDLBM_MASK_CATALYTIC) w |= CATALYTIC_BIT;
+        if (c == GAS) {
+          ++gcount;
+          for (int i = 1; i < Q19; ++i) {
+            if (G.at(x + H3X[i], y + H3Y[i], z + H3Z[i]) < 0)
+              return bail(fail(FDLBM_EGEOM, "gas node (%d,%d,%d) touches a closed lattice face", x, y, z));
+            const uint32_t st = G.stencil(x, y, z, i);
+            w |= uint64_t(st) << (STENCIL_SHIFT3 + 3 * (i - 1));
+            h->stencil_counts[st]++;
+          }
+          for (int d = 1; d <= 6; ++d)
+            if (G.cls_at(x + H3X[d], y + H3Y[d], z + H3Z[d]) == GAS) w |= 1ull << (NBR_SHIFT3 + d - 1);
+        } else if (c == WALL || c == SOLID) {
+          if (c == WALL) {
+            for (int i = 1; i < Q19; ++i) {
+              uint32_t st = ST_NOT_ARRIVAL;
+              if (G.cls_at(x - H3X[i], y - H3Y[i], z - H3Z[i]) == GAS) {
+                st = G.stencil(x, y, z, i);
+                h->stencil_counts[st]++;
+              }
+              w |= uint64_t(st) << (STENCIL_SHIFT3 + 3 * (i - 1));
+            }
+            walls.push_back((int32_t)k);
+          } else {
+            solids.push_back((int32_t)k);
+          }
+          for (int d = 1; d <= 6; ++d) {
+            const uint32_t cn = G.cls_at(x + H3X[d], y + H3Y[d], z + H3Z[d]);
+            if (cn == WALL || cn == SOLID) w |= 1ull << (NBR_SHIFT3 + d - 1);
+          }
+        } else if (c == OUTLET && G.cls[k - 1] != GAS) {
+          return bail(fail(FDLBM_EGEOM, "outlet node (%d,%d,%d) has no upstream gas node", x, y, z));
+        }
+        code[k] = w;
+        h->counts[c]++;
+      }
+  }
+  gas_z[nz] = (int)gcount;
+  wall_z[nz] = (int)walls.size();
+  std::vector<int32_t> solid_list(walls);
+  solid_list.insert(solid_list.end(), solids.begin(), solids.end());
+
+  DevParams& P = h->P;
+  P.dim = 3;
+  P.nx = nx;
+  P.ny = ny;
+  P.nz = nz;
+  P.n = (int)n;
+  P.xoff = XOFF3;
+  P.yoff = GHOST3;
+  P.zoff = GHOST3;
+  P.pitch = (nx + 2 * XOFF3 + 31) / 32 * 32;
+  P.slab = (long long)P.pitch * (ny + 2 * GHOST3);
+  P.plane = (P.slab * (nz + 2 * GHOST3) + 63) / 64 * 64;
+  if ((long long)ns * Q19 * P.plane >= (1LL << 31))
+    return bail(fail(FDLBM_EINVAL, "lattice too large: %d species x 19 x %lld padded cells exceed 2^31 elements", ns,
+                     (long long)P.plane));
+  // Padded code words: ghost cells within GHOST3 of a periodic face carry the wrapped
+  // node's word, everything else outside the lattice is OUTSIDE.
+  std::vector<uint64_t> pcode((size_t)P.plane, uint64_t(OUTSIDE));
+  for (int pz = 0; pz < nz + 2 * GHOST3; ++pz)
+    for (int py = 0; py < ny + 2 * GHOST3; ++py)
+      for (int px = 0; px < P.pitch; ++px) {
+        int x = px - XOFF3, y = py - GHOST3, z = pz - GHOST3;
+        if (x < 0 || x >= nx) {
+          if (!G.px || x < -GHOST3 || x >= nx + GHOST3) continue;
+          x = x < 0 ? x + nx : x - nx;
+        }
+        if (y < 0 || y >= ny) {
+          if (!G.py) continue;
+          y = y < 0 ? y + ny : y - ny;
+        }
+        if (z < 0 || z >= nz) {
+          if (!G.pz) continue;
+          z = z < 0 ? z + nz : z - nz;
+        }
+        pcode[(size_t)px + (size_t)py * P.pitch + (size_t)pz * P.slab] = code[x + (long)nx * (y + (long)ny * z)];
+      }
+  // Gas list in z, y, x order.
+  std::vector<int2> gas_list;
+  gas_list.reserve((size_t)gcount);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const long k = x + (long)nx * (y + (long)ny * z);
+        if (G.cls[k] != GAS) continue;
+        const bool near = (G.px && (x < GHOST3 || x >= nx - GHOST3)) || (G.py && (y < GHOST3 || y >= ny - GHOST3)) ||
+                          (G.pz && (z < GHOST3 || z >= nz - GHOST3));
+        const bool outlet = x + 1 == nx - 1 && G.cls[k + 1] == OUTLET;
+        const int aux = int(k) | (outlet ? GAS_AUX_OUTLET : 0) | (near ? GAS_AUX_GHOST : 0);
+        const long pk = (x + XOFF3) + (long)(y + GHOST3) * P.pitch + (long)(z + GHOST3) * P.slab;
+        gas_list.push_back(make_int2((int)pk, aux));
+      }
+  P.n_gas = (int)gas_list.size();
+  // Step-kernel blocks: per z layer the gas blocks, then the wall blocks of that layer;
+  // interior solid blocks last.
+  std::vector<int4> blocks;
+  auto chunks = [&](int role, int first, int last) {
+    for (int s0 = first; s0 < last; s0 += STEP_BLOCK3)
+      blocks.push_back(make_int4(role, s0, std::min(STEP_BLOCK3, last - s0), 0));
+  };
+  for (int z = 0; z < nz; ++z) {
+    chunks(0, gas_z[z], gas_z[z + 1]);
+    chunks(1, wall_z[z], wall_z[z + 1]);
+  }
+  chunks(1, (int)walls.size(), (int)solid_list.size());
+  P.n_blocks = (int)blocks.size();
+  h->blocks_host = blocks;
+  P.ns = ns;
+  P.periodic_x = G.px;
+  P.periodic_y = G.py;
+  P.periodic_z = G.pz;
+  P.n_solid_list = (int)solid_list.size();
+  P.n_wall_list = (int)walls.size();
+  P.energy_correction = tr->energy_correction ? 1 : 0;
+  P.coupling = tr->coupling;
+  for (int f = 0; f < 6; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
+  h->T0 = tr->T0_K;
+  const double tl = 1.0 / (3.0 * tr->T0_K);
+  const double Tref = tr->T_inlet_K * tl;
+  h->T_inlet_lat = Tref;
+  h->T_init_lat = tr->T_init_K * tl;
+  h->Ts_init_lat = tr->T_solid_init_K * tl;
+  P.Tref = (float)Tref;
+  P.p_out = (float)Tref;
+  P.u_inlet = (float)tr->u_inlet;
+  P.Tin_lat = (float)Tref;
+  h->X_init.resize(ns);
+  h->X_inlet.resize(ns);
+  for (int j = 0; j < ns; ++j) {
+    const double M = species[j].M_gmol / Mmin;
+    const double c = 1.0 / std::sqrt(M);
+    const double t1 = species[j].tau1, t2 = species[j].tau2;
+    P.M[j] = (float)M;
+    P.invM[j] = (float)(1.0 / M);
+    P.sqrtM[j] = (float)std::sqrt(M);
+    P.c[j] = (float)c;
+    P.c2[j] = (float)(1.0 / M);
+    const double a = 1.0 - c;
+    P.a[j] = (float)a;
+    P.ha[j] = (float)(0.5 * a);
+    P.ha2[j] = (float)(0.5 * a * a);
+    P.onlattice[j] = (M == 1.0);
+    P.rref[j] = (float)(species[j].X_inlet * M);
+    P.Xin[j] = (float)species[j].X_inlet;
+    P.omega[j] = (float)(2.0 / (1.0 + 2.0 * t1));
+    P.t1t2[j] = (float)(t1 / t2);
+    P.wt1[j] = (float)(2.0 * t1 / (1.0 + 2.0 * t1));
+    P.a2[j] = (float)(1.0 / (2.0 * t2));
+    P.inv1a2[j] = (float)(1.0 / (1.0 + 1.0 / (2.0 * t2)));
+    P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
+    P.invtau2[j] = (float)(1.0 / t2);
+    // Energy-correction flux K_j = (2 c_pj / Pr - 2 / M_j) tau1_j C_j T, c_pj = 5 / (2 M_j) (3D).
+    P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.5 / M) / tr->Pr - 2.0 / M) * t1) : 0.f;
+    // FP16 storage: the same power-of-two scale as for D2Q9 (deviations below 2 M_j + rref_j).
+    P.hs[j] = P.hsi[j] = 1.f;
+    if (storage == FDLBM_STORAGE_FP16) {
+      const double bound = 2.0 * M + species[j].X_inlet * M;
+      const int e = (int)std::floor(std::log2(32768.0 / bound));
+      P.hs[j] = (float)std::ldexp(1.0, e);
+      P.hsi[j] = (float)std::ldexp(1.0, -e);
+    }
+    h->X_init[j] = species[j].X_init;
+    h->X_inlet[j] = species[j].X_inlet;
+  }
+  P.storage = storage;
+  for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, Tref);
+  P.alpha_s = (float)tr->alpha_s;
+  P.rhocp_s = (float)tr->rhocp_s;
+  P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
+  P.kappa_f = (float)tr->kappa_f;
+  P.dTout = (float)(tr->T_outer_K * tl - Tref);
+  P.nr = kin->n_react;
+  for (int r = 0; r < kin->n_react; ++r) {
+    for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
+    P.rate_form[r] = kin->rate_form[r];
+    P.k0[r] = (float)kin->k0[r];
+    P.EaR[r] = (float)(kin->Ea_Jmol[r] / R_GAS);
+    P.inv_Keq[r] = kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE ? (float)(1.0 / kin->Keq[r]) : 0.f;
+    P.heat[r] = (float)(-kin->dH_Jmol[r] / (3.0 * R_GAS * tr->T0_K));
+  }
+  P.T3T0 = (float)(3.0 * tr->T0_K);
+  P.rho_w_tol = (float)kin->rho_w_tol;
+  P.rho_w_maxit = kin->rho_w_maxit;
+  if (kin->n_react > 0) {
+    h->heat0 = -kin->dH_Jmol[0] / (3.0 * R_GAS * tr->T0_K);
+    for (int j = 0; j < ns && h->eps_species < 0; ++j)
+      if (kin->nu[0][j] < 0) {
+        h->eps_species = j;
+        h->eps_nu = kin->nu[0][j];
+      }
+  }
+
+  // Device state.
+  fdlbm_status st;
+  DevState& S = h->S;
+  const size_t pop_bytes = pop_bytes_per_value(storage) * (size_t)ns * Q19 * (size_t)P.plane;
+  void* p;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = dalloc(h, pop_bytes, &p)) != FDLBM_OK) return bail(st);
+    S.h[b] = p;
+    if ((st = dalloc(h, sizeof(float) * n, &p)) != FDLBM_OK) return bail(st);
+    S.Ts[b] = (float*)p;
+  }
+#define ALLOC3(field, type, count)                                               \
+  if ((st = dalloc(h, sizeof(type) * (size_t)(count), &p)) != FDLBM_OK) return bail(st); \
+  field = (type*)p;
+  ALLOC3(S.code64, uint64_t, P.plane);
+  ALLOC3(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
+  ALLOC3(S.gas_list, int2, std::max<size_t>(gas_list.size(), 1));
+  ALLOC3(S.blocks, int4, std::max<size_t>(blocks.size(), 1));
+  ALLOC3(S.F[0], float, (size_t)(ns + 1) * P.plane);
+  ALLOC3(S.F[1], float, (size_t)(ns + 1) * P.plane);
+  ALLOC3(S.mom, float, (size_t)(ns + 4) * n);
+  ALLOC3(S.Tgas, float, 2 * (size_t)n);
+  ALLOC3(S.snap, float, (size_t)(ns + 5) * n);
+  ALLOC3(S.ledger, double, (size_t)LG_COUNT * ledger_slots(P));
+  ALLOC3(S.rw, float, (size_t)ns * std::max<size_t>(walls.size(), 1));
+  ALLOC3(S.flags, int, 4);
+  ALLOC3(S.red, double, totals_count(ns) + residual_count3(ns) + LG_COUNT + 8);
+  ALLOC3(h->out_buf, float, (size_t)(2 * ns + 5) * n);
+#undef ALLOC3
+  cudaError_t e = cudaMemcpyAsync(S.code64, pcode.data(), sizeof(uint64_t) * pcode.size(), cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess && !solid_list.empty())
+    e = cudaMemcpyAsync(S.solid_list, solid_list.data(), sizeof(int32_t) * solid_list.size(), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess && !blocks.empty())
+    e = cudaMemcpyAsync(S.blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess && !gas_list.empty())
+    e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int2) * gas_list.size(), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "upload geometry"));
+  if ((st = upload_and_init3(h, init)) != FDLBM_OK) return bail(st);
+  *out = h;
+  return FDLBM_OK;
+}
+
+// Initial state of a D3Q19 handle from FP64 host fields (as upload_and_init).
+fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f) {
+  const long n = (long)h->nx * h->ny * h->nz;
+  const int ns = h->ns;
+  const double tl = 1.0 / (3.0 * h->T0);
+  std::vector<double> X((size_t)ns * n), u(3 * (size_t)n, 0.0), T(n), Ts(n), C(n, 1.0);
+  for (int j = 0; j < ns; ++j)
+    for (long k = 0; k < n; ++k) X[(size_t)j * n + k] = (f && f->X) ? f->X[(size_t)j * n + k] : h->X_init[j];
+  if (f && f->u) std::memcpy(u.data(), f->u, sizeof(double) * 3 * n);
+  for (long k = 0; k < n; ++k) {
+    T[k] = (f && f->T_K) ? f->T_K[k] * tl : h->T_init_lat;
+    Ts[k] = (f && f->Ts_K) ? f->Ts_K[k] * tl : h->Ts_init_lat;
+    if (f && f->C) C[k] = f->C[k];
+    if (!(T[k] > 0) || !(C[k] > 0)) return fail(FDLBM_EINVAL, "initial T and C must be positive (node %ld)", k);
+  }
+  // inlet: X_inlet[ns], T_inlet (lattice), u_inlet (plug)
+  std::vector<double> inlet(h->X_inlet);
+  inlet.push_back(h->T_inlet_lat);
+  inlet.push_back(double(h->P.u_inlet));
+  const size_t total = X.size() + u.size() + T.size() + Ts.size() + C.size() + inlet.size();
+  double* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(double) * total), "init staging alloc");
+  size_t off = 0;
+  double* dX = d + off; off += X.size();
+  double* du = d + off; off += u.size();
+  double* dT = d + off; off += T.size();
+  double* dTs = d + off; off += Ts.size();
+  double* dC = d + off; off += C.size();
+  double* dIn = d + off;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](double* dst, const std::vector<double>& v) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, h->stream);
+  };
+  up(dX, X);
+  up(du, u);
+  up(dT, T);
+  up(dTs, Ts);
+  up(dC, C);
+  up(dIn, inlet);
+  if (e == cudaSuccess) e = launch_init3(h->P, h->S, dX, du, dT, dTs, dC, dIn, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->S.ledger, 0, sizeof(double) * LG_COUNT * ledger_slots(h->P), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->S.flags, 0, sizeof(int) * 4, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->S.rw, 0xFF, sizeof(float) * (size_t)ns * std::max(h->P.n_wall_list, 1), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "initialise state");
+  h->cur = 0;
+  h->steps = 0;
+  h->steps_at_residual = 0;
+  h->have_snap = false;
+  h->mom_fresh = true;
+  std::vector<double> tot(totals_count(ns));
+  fdlbm_status st = read_totals(h, tot.data());
+  if (st != FDLBM_OK) return st;
+  h->E0 = tot[0];
+  h->H0 = tot[1];
+  for (int j = 0; j < ns; ++j) {
+    h->mass0[j] = tot[2 + j];
+    h->moles0[j] = tot[2 + ns + j];
+  }
+  return FDLBM_OK;
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -694,12 +1155,16 @@ fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device) {
   DeviceGuard guard(h->device);
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
-  const size_t count = (size_t)(2 * h->ns + 4) * h->nx * h->ny;
+  const size_t count = (size_t)(2 * h->ns + 2 + h->dim) * h->nx * h->ny * h->nz;
+  auto out = [&](float* d) {
+    return h->dim == 3 ? launch_moments_out3(h->P, h->S, h->cur, d, h->stream)
+                       : launch_moments_out(h->P, h->S, h->cur, d, h->stream);
+  };
   if (dst_on_device) {
-    CK(launch_moments_out(h->P, h->S, h->cur, dst, h->stream), "moments output");
+    CK(out(dst), "moments output");
     return FDLBM_OK;
   }
-  CK(launch_moments_out(h->P, h->S, h->cur, h->out_buf, h->stream), "moments output");
+  CK(out(h->out_buf), "moments output");
   CK(cudaMemcpyAsync(dst, h->out_buf, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream), "copy moments");
   CK(cudaStreamSynchronize(h->stream), "stream sync");
   return FDLBM_OK;
@@ -708,14 +1173,18 @@ fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device) {
 fdlbm_status fdlbm_populations(fdlbm_handle* h, float* dst, int dst_on_device) {
   if (!h || !dst) return fail(FDLBM_EINVAL, "bad handle or destination");
   DeviceGuard guard(h->device);
-  const size_t count = (size_t)h->ns * Q * h->nx * h->ny;
+  const size_t count = (size_t)h->ns * (h->dim == 3 ? Q19 : Q) * h->nx * h->ny * h->nz;
+  auto out = [&](float* d) {
+    return h->dim == 3 ? launch_populations_out3(h->P, h->S, h->cur, d, h->stream)
+                       : launch_populations_out(h->P, h->S, h->cur, d, h->stream);
+  };
   if (dst_on_device) {
-    CK(launch_populations_out(h->P, h->S, h->cur, dst, h->stream), "populations output");
+    CK(out(dst), "populations output");
     return FDLBM_OK;
   }
   float* tmp = nullptr;
   CK(cudaMalloc(&tmp, sizeof(float) * count), "staging alloc");
-  cudaError_t e = launch_populations_out(h->P, h->S, h->cur, tmp, h->stream);
+  cudaError_t e = out(tmp);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, sizeof(float) * count, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(tmp);
@@ -731,7 +1200,7 @@ fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out) {
   fdlbm_status st = read_totals(h, tot.data());
   if (st != FDLBM_OK) return st;
   double lg[LG_COUNT];
-  double* lsum = h->S.red + totals_count(ns) + residual_count(ns);
+  double* lsum = h->S.red + totals_count(ns) + residual_count3(ns);
   CK(launch_ledger_sum(h->P, h->S, lsum, h->stream), "ledger sum");
   CK(cudaMemcpyAsync(lg, lsum, sizeof(lg), cudaMemcpyDeviceToHost, h->stream), "read ledger");
   CK(cudaStreamSynchronize(h->stream), "stream sync");
@@ -768,9 +1237,10 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out) {
   DeviceGuard guard(h->device);
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
-  const int ns = h->ns, nf = ns + 4;
-  CK(launch_residual(h->P, h->S, h->cur, h->stream), "residual launch");
-  std::vector<double> sums(residual_count(ns));
+  const int ns = h->ns, nf = ns + 2 + h->dim;
+  if (h->dim == 3) CK(launch_residual3(h->P, h->S, h->cur, h->stream), "residual launch");
+  else CK(launch_residual(h->P, h->S, h->cur, h->stream), "residual launch");
+  std::vector<double> sums(h->dim == 3 ? residual_count3(ns) : residual_count(ns));
   CK(cudaMemcpyAsync(sums.data(), h->S.red + totals_count(ns), sizeof(double) * sums.size(),
                      cudaMemcpyDeviceToHost, h->stream),
      "read residual");
@@ -800,6 +1270,7 @@ double* g_static_scratch[STATIC_MAX_DEVICES] = {};
 
 fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
   if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
+  if (h->dim != 2) return fail(FDLBM_EINVAL, "the allocation-free totals are implemented for D2Q9 handles only");
   const int ns = h->ns, cnt = totals_count(ns);
   if (out_len < cnt) return fail(FDLBM_EINVAL, "out_len %d < %d (2 + 2 n_species)", out_len, cnt);
   const long long need = totals_static_doubles((long long)h->nx * h->ny, ns) * (long long)sizeof(double);
@@ -882,6 +1353,7 @@ std::vector<std::pair<void*, size_t>> ck_buffers(fdlbm_handle* h) {
 
 fdlbm_status fdlbm_save(fdlbm_handle* h, const char* path) {
   if (!h || !path) return fail(FDLBM_EINVAL, "bad handle or path");
+  if (h->dim != 2) return fail(FDLBM_EINVAL, "checkpoints are implemented for D2Q9 handles only");
   DeviceGuard guard(h->device);
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
@@ -923,6 +1395,7 @@ fdlbm_status fdlbm_save(fdlbm_handle* h, const char* path) {
 
 fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path) {
   if (!h || !path) return fail(FDLBM_EINVAL, "bad handle or path");
+  if (h->dim != 2) return fail(FDLBM_EINVAL, "checkpoints are implemented for D2Q9 handles only");
   DeviceGuard guard(h->device);
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(FDLBM_EIO, "cannot open %s", path);
@@ -974,7 +1447,7 @@ fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path) {
 fdlbm_status fdlbm_info(const fdlbm_handle* h, fdlbm_info_t* out) {
   if (!h || !out) return fail(FDLBM_EINVAL, "bad handle or output");
   std::memset(out, 0, sizeof(*out));
-  out->n_nodes = (int64_t)h->nx * h->ny;
+  out->n_nodes = (int64_t)h->nx * h->ny * h->nz;
   out->n_gas = h->counts[GAS];
   out->n_inlet = h->counts[INLET];
   out->n_outlet = h->counts[OUTLET];
@@ -1128,6 +1601,7 @@ fdlbm_status fdlbm_batch_create(fdlbm_handle* const* handles, int n, fdlbm_batch
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!handles[i]) return fail(FDLBM_EINVAL, "handle %d is NULL", i);
+    if (handles[i]->dim != 2) return fail(FDLBM_EINVAL, "batches are implemented for D2Q9 handles only");
     for (int q = 0; q < i; ++q)
       if (handles[q] == handles[i]) return fail(FDLBM_EINVAL, "handle %d appears twice", i);
     const fdlbm_handle* h = handles[i];

@@ -45,7 +45,7 @@ struct DevParams {
   int n_gas;            // gas-node list length
   int n_blocks;         // blocks of the fused step kernel
   int energy_correction, coupling;
-  int fixedT_face[4];   // x-, x+, y-, y+
+  int fixedT_face[6];   // x-, x+, y-, y+, z-, z+
   // species
   float M[MAX_NS], invM[MAX_NS], sqrtM[MAX_NS], c[MAX_NS], c2[MAX_NS];
   float a[MAX_NS];      // 1 - c_j
@@ -73,6 +73,11 @@ struct DevParams {
   // steady-state residual references
   float Xin[MAX_NS];
   float Tin_lat;
+  // D3Q19 lattice (dim 3): node (x, y, z) at (x + xoff) + (y + yoff) pitch + (z + zoff) slab
+  int dim;              // 2 (D2Q9) or 3 (D3Q19)
+  int nz, zoff, periodic_z;
+  long long slab;       // padded cells of one z layer
+  float W0_19[19];      // D3Q19 rest-equilibrium weights at T_ref
 };
 
 // Device state of one handle.
@@ -92,6 +97,7 @@ struct DevState {
   int* flags;           // sticky error flags
   float* rw;            // converged wall densities of the last step, [ns][n_wall_list] (NaN: none)
   double* red;          // reduction scratch (doubles)
+  uint64_t* code64;     // D3Q19: node code words on the padded lattice, [plane]
 };
 
 enum Ledger { LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV, LG_COUNT };
@@ -139,6 +145,38 @@ struct BatchLaunch {
 };
 // One batched step (the step kernel, then the counter advance) on stream st.
 cudaError_t launch_batch_step(const BatchLaunch& B, cudaStream_t st);
+
+// ---- D3Q19 lattice (fdlbm3d_kernels.cu) ----------------------------------------------
+constexpr int Q19 = 19;
+// Ghost layers of the padded 3D lattice (the deepest pull reaches 3 nodes upstream).
+constexpr int GHOST3 = 3;
+constexpr int XOFF3 = 4;
+// 64-bit code word of a 3D node: class (bits 0..2), catalytic (3), 3-bit streaming
+// stencil per direction i = 1..18 at bit 4 + 3 (i - 1), and at bit 58 + (d - 1) for the
+// axis directions d = 1..6 a gas neighbour (gas nodes) or a solid neighbour (solid
+// nodes).
+constexpr int STENCIL_SHIFT3 = 4;
+constexpr int NBR_SHIFT3 = 58;
+__host__ __device__ inline uint32_t node_class3(uint64_t code) { return uint32_t(code & 7u); }
+__host__ __device__ inline uint32_t stencil_of3(uint64_t code, int i) {
+  return uint32_t(code >> (STENCIL_SHIFT3 + 3 * (i - 1))) & 7u;
+}
+// Step-kernel block size of the 3D path.
+constexpr int STEP_BLOCK3 = 128;
+// Doubles written by the 3D totals / residual reductions.
+inline int residual_count3(int ns) { return 2 * (ns + 5); }
+cudaError_t launch_init3(const DevParams& P, const DevState& S, const double* X, const double* u,
+                         const double* T_lat, const double* Ts_lat, const double* C, const double* inlet,
+                         cudaStream_t st);
+// One 3D time step reading buffer src (step: the step's index, which seeds the stochastic
+// rounding of 16-bit storage); with moments_only the pre-collision moments into S.mom.
+cudaError_t launch_step3(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
+                         uint32_t step = 0);
+cudaError_t launch_moments_out3(const DevParams& P, const DevState& S, int cur, float* dst, cudaStream_t st);
+cudaError_t launch_populations_out3(const DevParams& P, const DevState& S, int cur, float* dst,
+                                    cudaStream_t st);
+cudaError_t launch_totals3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
+cudaError_t launch_residual3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 
 // Bytes of one stored population.
 inline size_t pop_bytes_per_value(int storage) { return storage == FDLBM_STORAGE_FP32 ? 4 : 2; }

@@ -30,7 +30,7 @@ class FdlbmError(RuntimeError):
 
 class Geometry(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lattice", C.c_int),
-                ("mask", C.POINTER(C.c_uint8)), ("face_bc", C.c_int * 4)]
+                ("mask", C.POINTER(C.c_uint8)), ("face_bc", C.c_int * 6), ("nz", C.c_int)]
 
 
 class Species(C.Structure):
@@ -172,8 +172,8 @@ class Solver:
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
-        if p["dim"] != 2 or p["lattice"] != 9:
-            raise FdlbmError(-1, "only D2Q9 problems are supported")
+        if (p["dim"], p["lattice"]) not in ((2, 9), (3, 19)):
+            raise FdlbmError(-1, "problems are D2Q9 (dim 2) or D3Q19 (dim 3)")
         L = load()
         self._torch = torch
         self.device = device
@@ -181,12 +181,13 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         keep = []
         g = Geometry()
-        g.nx, g.ny, g.lattice = p["nx"], p["ny"], 9
+        g.nx, g.ny, g.lattice = p["nx"], p["ny"], p["lattice"]
+        g.nz = p["nz"] if p["dim"] == 3 else 1
         mask = np.ascontiguousarray(p["mask"], dtype=np.uint8)
         keep.append(mask)
         g.mask = mask.ctypes.data_as(C.POINTER(C.c_uint8))
-        for f in range(4):
-            g.face_bc[f] = p["face_bc"][f]
+        for f in range(6):
+            g.face_bc[f] = p["face_bc"][f] if f < len(p["face_bc"]) else 0
         sp = p["species"]
         ns = len(sp)
         spec = (Species * ns)()
@@ -240,8 +241,11 @@ class Solver:
                               C.byref(opts), C.byref(h)))
         self._h = h
         self.ns = ns
+        self.dim = p["dim"]
+        self.Q = 9 if self.dim == 2 else 19
         self.nx, self.ny = p["nx"], p["ny"]
-        self.n = self.nx * self.ny
+        self.nz = p["nz"] if self.dim == 3 else 1
+        self.n = self.nx * self.ny * self.nz
         m = np.array([d["M_gmol"] for d in sp], np.float64)
         self._M_lat = m / m.min()
         self._X_init = np.array([d["X_init"] for d in sp], np.float64)
@@ -267,11 +271,15 @@ class Solver:
     def sync(self):
         _check(load().fdlbm_sync(self._h))
 
+    @property
+    def nfields(self) -> int:
+        return 2 * self.ns + 2 + self.dim
+
     def moments(self, out=None):
-        """[2 ns + 4, n] float32: rho_j, X_j, ux, uy, T (K), T_s (K). Returns a CUDA tensor
-        (``out`` may be a preallocated CUDA tensor or a numpy float32 array)."""
+        """[2 ns + 2 + D, n] float32: rho_j, X_j, ux, uy (, uz), T (K), T_s (K). Returns a
+        CUDA tensor (``out`` may be a preallocated CUDA tensor or a numpy float32 array)."""
         torch = self._torch
-        nf = 2 * self.ns + 4
+        nf = self.nfields
         if out is None:
             out = torch.empty((nf, self.n), dtype=torch.float32, device=f"cuda:{self.device}")
         if isinstance(out, np.ndarray):
@@ -283,11 +291,11 @@ class Solver:
         return out
 
     def moments_host(self) -> np.ndarray:
-        out = np.empty((2 * self.ns + 4, self.n), np.float32)
+        out = np.empty((self.nfields, self.n), np.float32)
         return self.moments(out)
 
     def populations(self) -> np.ndarray:
-        out = np.empty((self.ns, Q, self.n), np.float32)
+        out = np.empty((self.ns, self.Q, self.n), np.float32)
         _check(load().fdlbm_populations(self._h, out.ctypes.data_as(C.c_void_p), 0))
         return out
 
@@ -328,14 +336,14 @@ class Solver:
         the same geometry): mole fractions, velocity, gas and solid temperature (K) and
         molar concentration, with the create-time defaults where a field is undefined
         (gas fields on solid nodes and the reverse)."""
-        ns = self.ns
+        ns, D = self.ns, self.dim
         m = self.moments_host().astype(np.float64)
         rho, X = m[:ns], m[ns:2 * ns]
-        T, Ts = m[2 * ns + 2], m[2 * ns + 3]
+        T, Ts = m[2 * ns + D], m[2 * ns + D + 1]
         gas = T > 0
         C_lat = (rho / self._M_lat[:, None]).sum(axis=0)
         X = np.where(gas[None, :], X, self._X_init[:, None])
-        return {"X": X, "u": np.where(gas[None, :], m[2 * ns:2 * ns + 2], 0.0),
+        return {"X": X, "u": np.where(gas[None, :], m[2 * ns:2 * ns + D], 0.0),
                 "T_K": np.where(gas, T, self._T_init), "Ts_K": np.where(Ts > 0, Ts, self._T_init),
                 "C": np.where(gas, C_lat, 1.0)}
 

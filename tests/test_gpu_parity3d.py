@@ -1,0 +1,181 @@
+"""GPU parity of the D3Q19 path: the CUDA solver (through the C ABI) against the FP64
+D3Q19 oracle on the same seeded inputs, field by field.
+
+Sizes: periodic boxes and sphere-packing crops that span several 128-node blocks with
+ragged tails; the 64x32x32 crop of the 256x128x128 sphere packing (the oracle-sized
+case of the 3D bed); and the full-size bed in the benchmark's launch configuration,
+sampled where a crop's oracle run is exact (a node's state after k steps depends only on
+nodes within 3k lattice spacings, the deepest pull). Tolerance: 1e-5 of max |field| on
+every moment field (field-normalised relative error; the velocity components share the
+maximum speed as their scale)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1804_07588_gb300 import workloads as W
+from parity import TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def _fdlbm():
+    from paper_1804_07588_gb300 import fdlbm
+    return fdlbm
+
+
+def names3(ns):
+    return ([f"rho_{j}" for j in range(ns)] + [f"X_{j}" for j in range(ns)] +
+            ["ux", "uy", "uz", "T", "Ts"])
+
+
+def errors3(m_gpu, m_ora, classes, ns, sel_extra=None):
+    """Per-field max |gpu - oracle| / max |oracle| over gas nodes (T_s: solid nodes). The
+    velocity is one vector field: its components are normalised by the maximum speed
+    (a component that has decayed to a small fraction of the others would otherwise be
+    measured against FP32 rounding at the others' scale)."""
+    gas = classes == 0
+    solid = classes >= 3
+    if sel_extra is not None:
+        gas = gas & sel_extra
+        solid = solid & sel_extra
+    u_scale = np.sqrt((np.asarray(m_ora[2 * ns:2 * ns + 3][:, gas], np.float64) ** 2).sum(0)).max()
+    errs = {}
+    for f, name in enumerate(names3(ns)):
+        sel = solid if name == "Ts" else gas
+        if not sel.any():
+            continue
+        a = np.asarray(m_ora[f][sel], np.float64)
+        b = np.asarray(m_gpu[f][sel], np.float64)
+        scale = u_scale if name in ("ux", "uy", "uz") else np.abs(a).max()
+        errs[name] = float(np.abs(a - b).max() / scale) if scale > 0 else float(np.abs(b).max())
+    return errs
+
+
+def run_both3(p, steps):
+    s = _fdlbm().Solver(p)
+    o = oracle.Oracle3(p)
+    s.step(steps)
+    o.step(steps)
+    s.sync()
+    return s, o
+
+
+def check(s, o, tol=TOL, what="", sel=None):
+    errs = errors3(s.moments_host(), o.moments(), o.classes(), o.ns, sel)
+    worst = max(errs.values())
+    print(what, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert worst <= tol, f"{what} worst {worst:.3e} > {tol:.1e}: " + ", ".join(f"{k}={v:.2e}" for k, v in errs.items())
+    return errs
+
+
+def test_initial_state3():
+    p = W.periodic_box3(20, 12, 10, solid_layers=3)
+    p["init"] = W.random_fields(p, seed=51)
+    s, o = run_both3(p, 0)
+    check(s, o, tol=1e-6, what="t=0")
+    s.close()
+
+
+def test_populations3_one_step_periodic():
+    """One step of a 20x12x10 periodic box from random fields: every stored population
+    (all 19 directions, 5 species) matches the oracle's."""
+    p = W.periodic_box3(20, 12, 10, reactions=[])
+    p["init"] = W.random_fields(p, seed=52)
+    s, o = run_both3(p, 1)
+    g_gpu = s.populations().astype(np.float64)
+    g_ora = o.populations()
+    gas = o.classes() == 0
+    err = np.abs(g_gpu[:, :, gas] - g_ora[:, :, gas]).max() / np.abs(g_ora[:, :, gas]).max()
+    assert err < 2e-6, err
+    s.close()
+
+
+@pytest.mark.parametrize("pr,ec", [(0.7, 1), (1.0, 0)])
+def test_parity3_periodic_random(pr, ec):
+    p = W.periodic_box3(20, 12, 10, reactions=[], Pr=pr, energy_correction=ec)
+    p["init"] = W.random_fields(p, seed=53)
+    s, o = run_both3(p, 100)
+    check(s, o, what="periodic 3D")
+    s.close()
+
+
+@pytest.mark.parametrize("coupling", [W.CONSERVATIVE, W.PAPER])
+def test_parity3_reactive_slab(coupling):
+    """Catalytic FD-solid slab under a periodic gas layer: reactive wall, wall-density
+    iteration, reaction heat and the interface coupling (both readings)."""
+    p = W.periodic_box3(18, 10, 14, solid_layers=4, coupling=coupling)
+    p["init"] = W.random_fields(p, seed=54)
+    s, o = run_both3(p, 150)
+    check(s, o, what="reactive slab 3D")
+    b_gpu, b_ora = s.balance(), o.balance()
+    assert b_ora["Q_reaction"] != 0.0
+    assert abs(b_gpu["Q_reaction"] / b_ora["Q_reaction"] - 1.0) < 1e-5
+    s.close()
+
+
+def test_parity3_sphere_crop_inlet_outlet():
+    """32x16x16 corner crop of the sphere packing (inlet, outlet, periodic y and z,
+    catalytic spheres with FD heat), 300 steps."""
+    p = W.crop3(W.config2(), 32, 16, 16)
+    s, o = run_both3(p, 300)
+    check(s, o, what="sphere crop 32x16x16")
+    s.close()
+
+
+def test_parity3_config2_crop():
+    """The 64x32x32 crop of the 256x128x128 packing (the oracle-sized 3D bed), 100 steps."""
+    p = W.config2_crop()
+    s, o = run_both3(p, 100)
+    check(s, o, what="config-2 crop 64x32x32")
+    s.close()
+
+
+def test_parity3_full_bed_sampled():
+    """The full 256x128x128 bed (the benchmark's workload and launch configuration),
+    4 steps, compared on the nodes of the 64x32x32 corner crop farther than 3 x 4 nodes
+    from the crop's cut faces, where the crop's oracle run is exact."""
+    full = W.config2()
+    s = _fdlbm().Solver(full)
+    s.step(4)
+    s.sync()
+    m_full = s.moments_host()
+    s.close()
+    cx, cy, cz = 64, 32, 32
+    crop = W.crop3(full, cx, cy, cz)
+    o = oracle.Oracle3(crop)
+    o.step(4)
+    m_ora = o.moments()
+    nx, ny, nz = full["nx"], full["ny"], full["nz"]
+    nf = m_full.shape[0]
+    m_gpu = m_full.reshape(nf, nz, ny, nx)[:, :cz, :cy, :cx].reshape(nf, -1)
+    zz, yy, xx = np.meshgrid(np.arange(cz), np.arange(cy), np.arange(cx), indexing="ij")
+    margin = 12
+    inner = ((yy >= margin) & (yy < cy - margin) & (zz >= margin) & (zz < cz - margin) & (xx < cx - 2 - margin))
+    errs = errors3(m_gpu, m_ora, o.classes(), o.ns, inner.reshape(-1))
+    assert max(errs.values()) <= TOL, errs
+
+
+def test_periodic3_mass_conservation_gpu():
+    """FP32 GPU path, periodic 3D box: species masses conserved to FP32 rounding."""
+    p = W.periodic_box3(24, 16, 12, reactions=[])
+    p["init"] = W.random_fields(p, seed=55)
+    s = _fdlbm().Solver(p)
+    b0 = s.balance()
+    s.step(300)
+    b = s.balance()
+    np.testing.assert_allclose(b["mass"], b0["mass"], rtol=2e-6)
+    s.close()
+
+
+def test_3d_rejects_unsupported():
+    fdlbm = _fdlbm()
+    p = W.periodic_box3(8, 8, 8)
+    s = fdlbm.Solver(p)
+    with pytest.raises(fdlbm.FdlbmError):
+        s.totals_static()
+    s.close()
+    q = W._base(3, 16, 8, 8, np.zeros((8, 8, 16), np.uint8),
+                [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC],
+                u_inlet=0.01, inlet_profile=W.PARABOLIC)
+    with pytest.raises(fdlbm.FdlbmError):
+        fdlbm.Solver(q)
