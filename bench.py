@@ -39,8 +39,8 @@ WORKLOAD = "porous-bed-d2q9-1024x512-5species-fp32"
 WORKLOAD3 = "porous-bed-d3q19-256x128x128-5species-fp32"
 
 
-def workload_name(storage, three_d=False):
-    w = WORKLOAD3 if three_d else WORKLOAD
+def workload_name(storage, three_d=False, size="256x128x128"):
+    w = WORKLOAD3.replace("256x128x128", size) if three_d else WORKLOAD
     return w if storage == "fp32" else w.replace("-fp32", f"-{storage}-storage")
 
 
@@ -57,6 +57,8 @@ def parse():
                     help="bed: the 1024x512 porous bed; batch: 64 independent porous beds of uneven "
                          "size stepped together (one launch per step); bed3d: the D3Q19 256x128x128 "
                          "sphere packing")
+    ap.add_argument("--size", default="256x128x128",
+                    help="bed3d lattice nx x ny x nz (the same sphere recipe; 256x128x128 by default)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="population storage (FP32 arithmetic in every case)")
     return ap.parse_args()
@@ -351,7 +353,11 @@ def run_fdlbm(args, rank, world, local_rank):
     dev = local_rank
     torch.cuda.set_device(dev)
     three_d = args.workload == "bed3d"
-    p = workloads.config2() if three_d else workloads.config1()
+    if three_d:
+        nx3, ny3, nz3 = (int(v) for v in args.size.split("x"))
+        p = workloads.config2(nx=nx3, ny=ny3, nz=nz3)
+    else:
+        p = workloads.config1()
     Q = 19 if three_d else 9
     s = fdlbm.Solver(p, device=dev, storage=args.storage)
     info = s.info()
@@ -435,7 +441,7 @@ def run_fdlbm(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_name(args.storage, three_d), "nx": p["nx"], "ny": p["ny"],
+            "config": {"workload": workload_name(args.storage, three_d, args.size), "nx": p["nx"], "ny": p["ny"],
                        **({"nz": p["nz"], "lattice": "D3Q19"} if three_d else {"lattice": "D2Q9"}),
                        "porosity": 0.5 if three_d else 0.6,
                        "storage": {"fp32": "FP32 deviations", "bf16": "BF16 deviations, stochastic rounding",

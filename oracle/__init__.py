@@ -62,6 +62,7 @@ class _Problem(C.Structure):
         ("init_X", C.POINTER(C.c_double)), ("init_u", C.POINTER(C.c_double)),
         ("init_T", C.POINTER(C.c_double)), ("init_Ts", C.POINTER(C.c_double)),
         ("init_C", C.POINTER(C.c_double)),
+        ("local_tau", C.c_int), ("mu", C.c_double * MAX_NS), ("Djk", (C.c_double * MAX_NS) * MAX_NS),
     ]
 
 
@@ -121,6 +122,9 @@ def lib():
         L.ora_uc.restype = C.c_double
         L.ora_collide.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.ora_units.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.ora_wilke_phi.argtypes = [C.c_double] * 4
+        L.ora_wilke_phi.restype = C.c_double
+        L.ora_local_tau.argtypes = [C.c_int, dp, dp, dp, dp, C.c_double, dp, dp]
         L.ora3_create.restype = C.c_void_p
         L.ora3_create.argtypes = [C.POINTER(_Problem3), C.c_char_p, C.c_int]
         L.ora3_destroy.argtypes = [C.c_void_p]
@@ -187,6 +191,12 @@ class Oracle:
                 a = np.ascontiguousarray(init[key], dtype=np.float64)
                 self._keep.append(a)
                 setattr(s, field, _dptr(a))
+        if p.get("local_tau"):
+            s.local_tau = 1
+            for j, d in enumerate(sp):
+                s.mu[j] = d["mu"]
+                for k, v in enumerate(d["D"]):
+                    s.Djk[j][k] = v
         err = C.create_string_buffer(256)
         h = L.ora_create(C.byref(s), err, 256)
         if not h:
@@ -270,6 +280,23 @@ def phi(c):
     out = np.zeros(Q)
     lib().ora_phi(c, _dptr(out))
     return out
+
+
+def wilke_phi(mu_j, mu_k, M_j, M_k) -> float:
+    return lib().ora_wilke_phi(mu_j, mu_k, M_j, M_k)
+
+
+def local_tau(M, mu, Djk, rho, T):
+    """(tau1[ns], tau2[ns]) of one node (Eqs. tau1s, tau2_approx_text, D_j_text)."""
+    M = np.ascontiguousarray(M, np.float64)
+    ns = len(M)
+    mu = np.ascontiguousarray(mu, np.float64)
+    D = np.zeros((ns, MAX_NS))
+    D[:, :ns] = np.asarray(Djk, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    t1, t2 = np.zeros(ns), np.zeros(ns)
+    lib().ora_local_tau(ns, _dptr(M), _dptr(mu), _dptr(D), _dptr(rho), T, _dptr(t1), _dptr(t2))
+    return t1, t2
 
 
 def units(T0_K, M0_gmol, dx_m):

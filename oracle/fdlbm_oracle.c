@@ -63,6 +63,7 @@ struct ora_state {
   double* Tg_prev;           /* g-temperature of the previous time level (reading R8) */
   double* Cj_prev;           /* [ns][n] concentrations of the previous time level */
   double* divq;              /* scratch [ns][n] */
+  double* tau1_prev;         /* [ns][n] local tau1 of the previous time level (local_tau) */
   double* q;                 /* [n] reaction heat of the step at wall nodes */
   double* dE;                /* [n] energy the wall put into the gas this step */
   double* snap;              /* residual snapshot */
@@ -226,6 +227,41 @@ double ora_uc(int ns, const double* rho, const double* Jx, const double* tau2, d
     den += rho[j] / (tau2[j] + 0.5);
   }
   return num / den;
+}
+
+/* Wilke's mixture rule (Eq. wilke). The printed coefficient lacks the square on the
+ * bracket; without it a pure gas (phi_jj = 2 / 4) would have twice its own viscosity, so
+ * the bracket is squared as in Wilke's rule (phi_jj = 1). */
+double ora_wilke_phi(double mu_j, double mu_k, double M_j, double M_k) {
+  double b = 1.0 + sqrt(mu_j / mu_k) * pow(M_k / M_j, 0.25);
+  return b * b / sqrt(8.0 * (1.0 + M_j / M_k));
+}
+
+/* Locally updated relaxation times of one node (Sec. 3): tau1_j = mu_j / (C T sum_k X_k
+ * phi_jk) (Eq. tau1s), tau2_j = rho_j D_j / (X_j p) with p = C T (Eq. tau2_approx_text)
+ * and the mixture-averaged D_j = (1 - Y_j) / sum_{k != j} X_k / D_jk (Eq. D_j_text).
+ * X_j mole fractions, Y_j mass fractions. For an empty species (X_j = 0) rho_j / X_j is
+ * replaced by its limit M_j C. */
+void ora_local_tau(int ns, const double* M, const double* mu, const double* Djk, const double* rho, double T,
+                   double* tau1, double* tau2) {
+  double C = 0.0, r = 0.0, X[ORA_MAX_NS];
+  for (int j = 0; j < ns; ++j) {
+    C += rho[j] / M[j];
+    r += rho[j];
+  }
+  for (int j = 0; j < ns; ++j) X[j] = rho[j] / M[j] / C;
+  double p = C * T;
+  for (int j = 0; j < ns; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < ns; ++k) s += X[k] * ora_wilke_phi(mu[j], mu[k], M[j], M[k]);
+    tau1[j] = mu[j] / (C * T * s);
+    double sd = 0.0;
+    for (int k = 0; k < ns; ++k)
+      if (k != j) sd += X[k] / Djk[j * ORA_MAX_NS + k];
+    double Dj = (1.0 - rho[j] / r) / sd;
+    double rho_over_X = X[j] > 0.0 ? rho[j] / X[j] : M[j] * C;
+    tau2[j] = rho_over_X * Dj / p;
+  }
 }
 
 /* Moments of pulled g of one node (Eq. moments_of_g, first line, and Eq. moments_of_f). */
@@ -461,6 +497,7 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
   s->Tg_prev = (double*)xcalloc((size_t)n, sizeof(double));
   s->Cj_prev = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->divq = (double*)xcalloc((size_t)ns * n, sizeof(double));
+  s->tau1_prev = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->q = (double*)xcalloc((size_t)n, sizeof(double));
   s->dE = (double*)xcalloc((size_t)n, sizeof(double));
   s->snap = (double*)xcalloc((size_t)(ns + 4) * n, sizeof(double));
@@ -542,6 +579,13 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
           }
           s->Tg_prev[k] = T;
           fill_moments_from_fields(s, k, Xc, ux, uy, T);
+          for (int j = 0; j < ns; ++j) s->tau1_prev[(size_t)j * n + k] = p->tau1[j];
+          if (p->local_tau) {
+            double rl[ORA_MAX_NS], t1[ORA_MAX_NS], t2[ORA_MAX_NS];
+            for (int j = 0; j < ns; ++j) rl[j] = Xc[j] * s->M[j];
+            ora_local_tau(ns, s->M, p->mu, &p->Djk[0][0], rl, T, t1, t2);
+            for (int j = 0; j < ns; ++j) s->tau1_prev[(size_t)j * n + k] = t1[j];
+          }
         }
       } else {
         s->Ts[k] = Ts;
@@ -580,6 +624,7 @@ void ora_destroy(ora_state* s) {
   free(s->Tg_prev);
   free(s->Cj_prev);
   free(s->divq);
+  free(s->tau1_prev);
   free(s->q);
   free(s->dE);
   free(s->snap);
@@ -707,12 +752,12 @@ static void gas_pass(ora_state* s) {
         double dq = 0.0;
         if (s->p.energy_correction) {
           double cp = 2.0 / s->M[j]; /* (D + 2) / (2 M_j), D = 2 */
-          double coef = (2.0 * cp / Pr - 1.0 / s->M[j]) * s->p.tau1[j];
-          double Kc = coef * s->Cj_prev[(size_t)j * n + k] * s->Tg_prev[k];
+          double coef = (2.0 * cp / Pr - 1.0 / s->M[j]); /* times tau1 of the node */
+          double Kc = coef * s->tau1_prev[(size_t)j * n + k] * s->Cj_prev[(size_t)j * n + k] * s->Tg_prev[k];
           for (int i = 1; i <= 4; ++i) {
             int kn = node_at(s, x + EX[i], y + EY[i]);
             if (kn < 0 || s->cls[kn] != CL_GAS) continue;
-            double Kn = coef * s->Cj_prev[(size_t)j * n + kn] * s->Tg_prev[kn];
+            double Kn = coef * s->tau1_prev[(size_t)j * n + kn] * s->Cj_prev[(size_t)j * n + kn] * s->Tg_prev[kn];
             dq += 0.5 * (Kc + Kn) * (s->Tg_prev[kn] - s->Tg_prev[k]);
           }
         }
@@ -727,7 +772,22 @@ static void gas_pass(ora_state* s) {
       dq[j] = s->divq[(size_t)j * n + k];
       for (int i = 0; i < Q; ++i) gl[j * Q + i] = s->gp[PIDX(s, j, i, k)];
     }
-    ora_collide(ns, s->M, s->p.tau1, s->p.tau2, gl, dq, go, mom);
+    double t1[ORA_MAX_NS], t2[ORA_MAX_NS];
+    for (int j = 0; j < ns; ++j) {
+      t1[j] = s->p.tau1[j];
+      t2[j] = s->p.tau2[j];
+    }
+    if (s->p.local_tau) {
+      /* reading R18: the node's pulled (g) densities and g-temperature of this step */
+      double rl[ORA_MAX_NS];
+      for (int j = 0; j < ns; ++j) {
+        rl[j] = 0.0;
+        for (int i = 0; i < Q; ++i) rl[j] += gl[j * Q + i];
+      }
+      ora_local_tau(ns, s->M, s->p.mu, &s->p.Djk[0][0], rl, s->Tg[k], t1, t2);
+    }
+    for (int j = 0; j < ns; ++j) s->tau1_prev[(size_t)j * n + k] = t1[j];
+    ora_collide(ns, s->M, t1, t2, gl, dq, go, mom);
     for (int j = 0; j < ns; ++j)
       for (int i = 0; i < Q; ++i) s->gn[PIDX(s, j, i, k)] = go[j * Q + i];
     for (int j = 0; j < ns; ++j) s->rho[(size_t)j * n + k] = mom[j];

@@ -41,6 +41,13 @@ typedef struct {
   const double* init_T;   /* optional [n] gas temperature, K */
   const double* init_Ts;  /* optional [n] solid temperature, K */
   const double* init_C;   /* optional [n] molar concentration (lattice, default 1) */
+  /* Locally updated relaxation times (local_tau = 1): per node, tau1_j from the species
+   * viscosities mu_j by Wilke's mixture rule (Eq. tau1s) and tau2_j from the binary
+   * diffusivities D_jk by the mixture-averaged rule (Eqs. tau2_approx_text, D_j_text);
+   * tau1/tau2 above are then unused. Lattice units. */
+  int local_tau;
+  double mu[ORA_MAX_NS];
+  double Djk[ORA_MAX_NS][ORA_MAX_NS];
 } ora_problem;
 
 typedef struct ora_state ora_state;
@@ -70,6 +77,12 @@ double ora_interp(int code, double c, double s3, double s2, double s1, double s0
 void ora_psi(double c, double* psix9, double* psiy9);
 void ora_phi(double c, double* phi9);
 double ora_uc(int ns, const double* rho, const double* Jx, const double* tau2, double ux);
+/* Wilke's coefficient phi_jk (Eq. wilke, read with the squared bracket). */
+double ora_wilke_phi(double mu_j, double mu_k, double M_j, double M_k);
+/* Local relaxation times of one node from its species densities rho[ns], molar masses
+ * M[ns] and temperature T (Eqs. tau1s, tau2_approx_text, D_j_text). */
+void ora_local_tau(int ns, const double* M, const double* mu, const double* Djk /* [ns][ORA_MAX_NS] */,
+                   const double* rho, double T, double* tau1, double* tau2);
 void ora_collide(int ns, const double* M, const double* tau1, const double* tau2,
                  const double* g /* [ns][9] pulled */, const double* divq /* [ns] */,
                  double* gout /* [ns][9] */, double* mom /* rho_j[ns], ux, uy, T, Tg */);

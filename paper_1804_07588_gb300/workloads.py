@@ -358,6 +358,25 @@ def random_fields(p: dict, seed: int, dX: float = 0.2, du: float = 0.01,
             "T_K": T.reshape(n).copy(), "Ts_K": Ts.reshape(n).copy()}
 
 
+def local_transport(p: dict, mu_scale: float = 1.0, D_scale: float = 1.0) -> dict:
+    """Switch a problem to locally updated relaxation times: species viscosities mu_j
+    and binary diffusivities D_jk (lattice units) chosen so that, in the problem's inlet
+    mixture at C = 1, T = 1/3, a species alone would have tau1 = its table value (mu_j =
+    tau1_j C T) and every pair diffuses with D_jk = (tau2_j / M_j + tau2_k / M_k) T / 2
+    (molar masses relative to the lightest). The Lennard-Jones collision integrals that
+    would give these from the species' properties are not printed in the paper."""
+    sp = p["species"]
+    M = np.array([d["M_gmol"] for d in sp])
+    M = M / M.min()
+    T = 1.0 / 3.0
+    for j, d in enumerate(sp):
+        d["mu"] = mu_scale * d["tau1"] * T
+        d["D"] = [0.0 if k == j else D_scale * 0.5 * (d["tau2"] / M[j] + e["tau2"] / M[k]) * T
+                  for k, e in enumerate(sp)]
+    p["local_tau"] = 1
+    return p
+
+
 def config0(**kw) -> dict:
     """2D D2Q9 catalytic channel: 128x32 gas nodes between two 8-node FD-solid walls,
     parabolic inlet peak 0.02, T_in = walls = 500 K (run length 2000 steps)."""

@@ -446,3 +446,111 @@ def test_shear_wave_mixture_viscosity():
     mu = (t1 * X * T).sum()          # C = 1
     rho = (X * M).sum()
     assert abs(nu0 / (mu / rho) - 1.0) < 0.01, (nu1, nu2, nu0, mu / rho)
+
+
+# ---------------------------------------------------------------------------------------
+# Locally updated relaxation times (Sec. 3: Eqs. tau2_approx_text, D_j_text, wilke, tau1s)
+# ---------------------------------------------------------------------------------------
+
+def test_wilke_phi_identities():
+    """Wilke's coefficient (Eq. wilke, read with the squared bracket): phi_jj = 1, so a
+    pure gas keeps its own viscosity, and the reciprocity phi_kj = phi_jk (mu_k / mu_j)
+    (M_j / M_k) of Wilke's rule holds. The bracket as printed (unsquared) satisfies
+    neither."""
+    rng = np.random.default_rng(61)
+    for _ in range(20):
+        mj, mk = rng.uniform(0.05, 0.5, 2)
+        Mj, Mk = rng.uniform(1.0, 22.0, 2)
+        assert np.isclose(oracle.wilke_phi(mj, mj, Mj, Mj), 1.0, rtol=1e-14)
+        assert np.isclose(oracle.wilke_phi(mk, mj, Mk, Mj),
+                          oracle.wilke_phi(mj, mk, Mj, Mk) * (mk / mj) * (Mj / Mk), rtol=1e-12)
+
+
+def _local_box(p):
+    return W.local_transport(p)
+
+
+@pytest.mark.parametrize("species", ["CO2", "H2O"])
+def test_local_tau_trace_diffusion_mixture_averaged(species):
+    """With locally updated relaxation times a heavy trace species diffuses with the
+    mixture-averaged coefficient D_j = (1 - Y_j) / sum_{k != j} X_k / D_jk of the
+    background mixture (Eq. D_j_text), measured from the decay of a mole-fraction mode
+    (two wavelengths, extrapolated to k -> 0; 1.5% tolerance)."""
+    def rate(nx, t0, t1):
+        p = _local_box(W.periodic_box(nx, 1, reactions=[], energy_correction=0))
+        j = W.SPECIES_ORDER.index(species)
+        X0 = np.array([s["X_init"] for s in p["species"]])
+        X0[j] = 1e-3
+        x = np.arange(nx)
+        X = np.repeat(X0[:, None], nx, 1)
+        X[j] *= 1.0 + 0.01 * np.cos(2 * np.pi * x / nx)
+        X[4] = 1.0 - X[:4].sum(0)
+        p["init"] = {"X": X}
+        o = oracle.Oracle(p)
+        o.step(t0)
+        a0 = _mode_amplitude(o.moments()[5 + j], nx)
+        o.step(t1 - t0)
+        a1 = _mode_amplitude(o.moments()[5 + j], nx)
+        k = 2 * np.pi / nx
+        return -math.log(a1 / a0) / (k * k * (t1 - t0)), p, j, X.mean(axis=1)
+    D1, p, j, X0 = rate(48, 100, 900)
+    D2, _, _, _ = rate(96, 400, 3600)
+    D0 = (4.0 * D2 - D1) / 3.0
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    Y = X0 * M / (X0 * M).sum()
+    Dj = np.array(p["species"][j]["D"])
+    D_th = (1.0 - Y[j]) / sum(X0[k] / Dj[k] for k in range(5) if k != j)
+    assert abs(D0 / D_th - 1.0) < 0.015, (D1, D2, D0, D_th)
+
+
+def test_local_tau_shear_viscosity_wilke():
+    """With locally updated relaxation times a shear wave in the inlet mixture decays with
+    the mixture viscosity of Wilke's rule, mu = sum_j X_j mu_j / sum_k X_k phi_jk (Eq.
+    mu_mixture_wilke): nu = mu / rho, two wavelengths, 1% tolerance."""
+    def rate(ny, tsteps):
+        p = _local_box(W.periodic_box(1, ny, reactions=[], Pr=0.7))
+        y = np.arange(ny)
+        u = np.zeros((2, ny))
+        u[0] = 0.002 * np.cos(2 * np.pi * y / ny)
+        p["init"] = {"u": u}
+        o = oracle.Oracle(p)
+        k = 2 * np.pi / ny
+        ts, amps = [], []
+        o.step(20)
+        for i in range(tsteps // 10):
+            ts.append(20 + 10 * i)
+            amps.append(2.0 * (o.moments()[10] * np.cos(2 * np.pi * y / ny)).mean())
+            o.step(10)
+        return -np.polyfit(np.array(ts, float), np.log(np.array(amps)), 1)[0] / (k * k), p
+    nu1, p = rate(32, 400)
+    nu2, _ = rate(64, 1600)
+    nu0 = (4.0 * nu2 - nu1) / 3.0
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    Ml = M / M.min()
+    X = np.array([s["X_init"] for s in p["species"]])
+    mu = np.array([s["mu"] for s in p["species"]])
+    phi = np.array([[oracle.wilke_phi(mu[a], mu[b], Ml[a], Ml[b]) for b in range(5)] for a in range(5)])
+    mu_mix = sum(X[a] * mu[a] / (X @ phi[a]) for a in range(5))
+    rho = (X * Ml).sum()
+    assert abs(nu0 / (mu_mix / rho) - 1.0) < 0.01, (nu1, nu2, nu0, mu_mix / rho)
+
+
+def test_local_tau_conserves_periodic():
+    """Locally updated relaxation times keep species mass and mixture momentum (U^c with
+    the node's tau2) in a periodic box from random fields."""
+    p = _local_box(W.periodic_box(20, 14, reactions=[], Pr=0.7))
+    p["init"] = W.random_fields(p, seed=62)
+    o = oracle.Oracle(p)
+    b0 = o.balance()
+    gas = o.classes() == 0
+
+    def momentum():
+        m = o.moments()
+        rho = m[:5].sum(0)
+        return (rho * m[10])[gas].sum(), (rho * m[11])[gas].sum()
+
+    P0 = momentum()
+    o.step(60)
+    np.testing.assert_allclose(o.balance()["mass"], b0["mass"], rtol=1e-13)
+    P1 = momentum()
+    assert max(abs(P1[0] - P0[0]), abs(P1[1] - P0[1])) < 1e-14 * b0["mass"].sum()
