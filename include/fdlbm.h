@@ -93,8 +93,13 @@ typedef struct {
 /* One gas species (Sec. 2; relaxation times in lattice units). */
 typedef struct {
   double M_gmol;           /* molar mass; the lightest species streams on-lattice */
-  double tau1, tau2;       /* relaxation times of Eq. bare_kinetic_eq, > 0 */
+  double tau1, tau2;       /* relaxation times of Eq. bare_kinetic_eq, > 0 (constant mode) */
   double X_init, X_inlet;  /* default initial and inlet mole fractions */
+  /* Locally updated relaxation times (fdlbm_transport.local_tau = 1, Sec. 3): the
+   * species viscosity (lattice units) and the binary diffusivities D[k] with every other
+   * species k (lattice units, > 0; D[j] of the species itself is unused). */
+  double mu;
+  double D[FDLBM_MAX_SPECIES];
 } fdlbm_species;
 
 /* Transport, thermal and solid parameters. Temperatures in kelvin; the lattice
@@ -109,6 +114,13 @@ typedef struct {
   double rhocp_s;          /* solid volumetric heat capacity, lattice energy / lattice T */
   double kappa_f;          /* gas conductivity used by FDLBM_COUPLING_PAPER */
   int coupling;            /* FDLBM_COUPLING_* */
+  /* 1: relaxation times updated at every gas node and step from the local composition
+   * and temperature (Sec. 3): tau1_j = mu_j / (C T sum_k X_k phi_jk) with Wilke's phi_jk
+   * (Eqs. wilke, tau1s; the bracket of phi_jk squared, as in Wilke's rule) and
+   * tau2_j = rho_j D_j / (X_j p), D_j = (1 - Y_j) / sum_{k != j} X_k / D_jk (Eqs.
+   * tau2_approx_text, D_j_text), from the pulled densities and the g-temperature of
+   * the step. D2Q9 with FP32 storage and at least 2 species; not in batches. */
+  int local_tau;
 } fdlbm_transport;
 
 /* Surface reactions on catalytic wall nodes (Sec. 4.3 and Sec. 6). */

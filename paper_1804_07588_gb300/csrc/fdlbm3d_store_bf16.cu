@@ -1,0 +1,7 @@
+// BF16 population storage of the D3Q19 path: instantiates the storage-dependent 3D
+// kernels and entry points for __nv_bfloat16 (values rounded once per store; FP32 arithmetic).
+#include "fdlbm3d_device.cuh"
+
+namespace fdlbm {
+FDLBM3_STORAGE_ENTRY_POINTS(, __nv_bfloat16)
+}  // namespace fdlbm

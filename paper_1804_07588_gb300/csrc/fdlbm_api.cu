@@ -229,6 +229,16 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       if (kin->nu[r][j] < -4 || kin->nu[r][j] > 4) return fail(FDLBM_EINVAL, "reaction %d: |nu| <= 4", r);
   }
 
+  if (tr->local_tau) {
+    if (geom->lattice != FDLBM_D2Q9) return fail(FDLBM_EINVAL, "local relaxation times are implemented for D2Q9");
+    if (storage != FDLBM_STORAGE_FP32) return fail(FDLBM_EINVAL, "local relaxation times need FP32 storage");
+    if (n_species < 2) return fail(FDLBM_EINVAL, "local relaxation times need at least 2 species");
+    for (int j = 0; j < n_species; ++j) {
+      if (!(species[j].mu > 0)) return fail(FDLBM_EINVAL, "species %d: mu must be positive", j);
+      for (int k = 0; k < n_species; ++k)
+        if (k != j && !(species[j].D[k] > 0)) return fail(FDLBM_EINVAL, "species %d: D[%d] must be positive", j, k);
+    }
+  }
   if (geom->lattice == FDLBM_D3Q19) return create3(geom, species, n_species, tr, kin, init, opts, out);
 
   fdlbm_handle* h = new fdlbm_handle();
@@ -449,7 +459,19 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
     P.invtau2[j] = (float)(1.0 / t2);
     // Energy-correction flux K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T, c_pj = 2 / M_j (2D).
+    P.kcoef0[j] = tr->energy_correction ? (float)(2.0 * (2.0 / M) / tr->Pr - 1.0 / M) : 0.f;
     P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.0 / M) / tr->Pr - 1.0 / M) * t1) : 0.f;
+    // Locally updated relaxation times: Wilke's phi_jk (bracket squared, so phi_jj = 1)
+    // and 1 / D_jk.
+    P.mu_l[j] = (float)species[j].mu;
+    for (int q = 0; q < ns; ++q) {
+      const double Mq = species[q].M_gmol / Mmin;
+      if (tr->local_tau) {
+        const double b = 1.0 + std::sqrt(species[j].mu / species[q].mu) * std::pow(Mq / M, 0.25);
+        P.phi_w[j][q] = (float)(b * b / std::sqrt(8.0 * (1.0 + M / Mq)));
+        P.invD[j][q] = q == j ? 0.f : (float)(1.0 / species[j].D[q]);
+      }
+    }
     // FP16 storage: deviations |g - rref W0| stay below 2 M_j + rref_j (a population never
     // exceeds its species density, bounded by the molar mass at twice the inlet molar
     // concentration); the largest power of two that maps that bound below 2^15 keeps
@@ -465,6 +487,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     h->X_inlet[j] = species[j].X_inlet;
   }
   P.storage = storage;
+  P.local_tau = tr->local_tau ? 1 : 0;
   for (int i = 0; i < Q; ++i) {
     const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
     const double wy = HEY[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
@@ -1602,6 +1625,7 @@ fdlbm_status fdlbm_batch_create(fdlbm_handle* const* handles, int n, fdlbm_batch
   for (int i = 0; i < n; ++i) {
     if (!handles[i]) return fail(FDLBM_EINVAL, "handle %d is NULL", i);
     if (handles[i]->dim != 2) return fail(FDLBM_EINVAL, "batches are implemented for D2Q9 handles only");
+    if (handles[i]->P.local_tau) return fail(FDLBM_EINVAL, "batches do not take handles with local relaxation times");
     for (int q = 0; q < i; ++q)
       if (handles[q] == handles[i]) return fail(FDLBM_EINVAL, "handle %d appears twice", i);
     const fdlbm_handle* h = handles[i];

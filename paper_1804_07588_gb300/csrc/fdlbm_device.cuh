@@ -378,7 +378,10 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // MODE 1: moments only (recomputes the pre-collision moments of the step that read
 // src / Fsrc into mom[] at compact indices; writes nothing else).
 // Moment field F: [1 + NS][plane]: dTg and K_j = kcoef_j C_j T_g of every gas node.
-template <class PT, int NS, bool PHI, int MODE>
+// LT: relaxation times updated per node from its pulled densities and g-temperature
+// (Sec. 3, Eqs. tau1s with Wilke's rule, tau2_approx_text, D_j_text); they also enter
+// K_j, so the lagged field carries each node's own tau1.
+template <class PT, int NS, bool PHI, int MODE, bool LT = false>
 __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                          const uint32_t* __restrict__ code, int k, int aux,
                                          const float* __restrict__ Fsrc, float* __restrict__ Fdst,
@@ -439,12 +442,34 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   }
   Ghost gh{0, 0};
   if (aux & GAS_AUX_GHOST) gh = ghost_of(P, n % P.nx, n / P.nx);
+  // Local relaxation times: tau1_j = mu_j / (C T sum_k X_k phi_jk), tau2_j = rho_j D_j /
+  // (X_j C T) = M_j (1 - Y_j) / (T sum_{k != j} X_k / D_jk), T the g-temperature.
+  float t1l[NS], t2l[NS];
+  if constexpr (LT) {
+    const float Tg = P.Tref + m.dTg;
+    const float iC = 1.f / m.C;
+    float X[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) X[j] = (P.rref[j] + m.drho[j]) * P.invM[j] * iC;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      float sphi = 0.f, sd = 0.f;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        sphi = fmaf(X[q], P.phi_w[j][q], sphi);
+        sd = fmaf(X[q], P.invD[j][q], sd);
+      }
+      t1l[j] = P.mu_l[j] / (m.C * Tg * sphi);
+      t2l[j] = P.M[j] * (1.f - (P.rref[j] + m.drho[j]) / m.r) / (Tg * sd);
+    }
+  }
   if (PHI) {
     store_with_ghosts(Fdst, k, gh, m.dTg);
 #pragma unroll
     for (int j = 0; j < NS; ++j)
       store_with_ghosts(Fdst + (long long)(1 + j) * P.plane, k, gh,
-                        P.kcoef[j] * ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg));
+                        (LT ? P.kcoef0[j] * t1l[j] : P.kcoef[j]) * ((P.rref[j] + m.drho[j]) * P.invM[j]) *
+                            (P.Tref + m.dTg));
   }
   if (Tgas != nullptr) Tgas[n] = T;
   flag_bad<NS>(flags, m, T);
@@ -454,9 +479,10 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     const float rho = P.rref[j] + m.drho[j];
-    ncx = fmaf(P.uc_w[j], m.Jx[j] - rho * ux, ncx);
-    ncy = fmaf(P.uc_w[j], m.Jy[j] - rho * uy, ncy);
-    den = fmaf(P.uc_w[j], rho, den);
+    const float w = LT ? 1.f / (t2l[j] + 0.5f) : P.uc_w[j];
+    ncx = fmaf(w, m.Jx[j] - rho * ux, ncx);
+    ncy = fmaf(w, m.Jy[j] - rho * uy, ncy);
+    den = fmaf(w, rho, den);
   }
   const float iden = 1.f / den;
   const float Ucx = ncx * iden, Ucy = ncy * iden;
@@ -465,9 +491,16 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   // inputs: the lagged divergence, parked in this thread's shared-memory column, and the
   // species' density and momentum, formed again from the pulled values in the pull's
   // order (the same FP32 sums).
-  float* s_m = s_h + NS * Q * GB;  // [NS][GB]
+  float* s_m = s_h + NS * Q * GB;  // [NS][GB]; with LT then tau1 [NS][GB], tau2 [NS][GB]
 #pragma unroll
   for (int j = 0; j < NS; ++j) s_m[j * GB + tid] = divq[j];
+  if constexpr (LT) {
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      s_m[(NS + j) * GB + tid] = t1l[j];
+      s_m[(2 * NS + j) * GB + tid] = t2l[j];
+    }
+  }
 #pragma unroll 1
   for (int j = 0; j < NS; ++j) {
     float h[Q];
@@ -486,8 +519,20 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
     const float rho = P.rref[j] + drj;
     // f-momentum of the species (Eq. moments_of_g) and its velocity, limited for trace
     // species (reading R15).
-    const float Jfx = (Jxj + P.a2[j] * rho * (ux + Ucx)) * P.inv1a2[j];
-    const float Jfy = (Jyj + P.a2[j] * rho * (uy + Ucy)) * P.inv1a2[j];
+    // collision coefficients: per species constants, or from the node's relaxation times
+    float a2j = P.a2[j], inv1a2j = P.inv1a2[j], omj = P.omega[j], omtj = P.omega[j] * P.t1t2[j];
+    float wt1j = P.wt1[j], invtau2j = P.invtau2[j];
+    if constexpr (LT) {
+      const float t1 = s_m[(NS + j) * GB + tid], t2 = s_m[(2 * NS + j) * GB + tid];
+      omj = 2.f / (1.f + 2.f * t1);
+      wt1j = omj * t1;
+      invtau2j = 1.f / t2;
+      omtj = wt1j * invtau2j;
+      a2j = 0.5f * invtau2j;
+      inv1a2j = 1.f / (1.f + a2j);
+    }
+    const float Jfx = (Jxj + a2j * rho * (ux + Ucx)) * inv1a2j;
+    const float Jfy = (Jyj + a2j * rho * (uy + Ucy)) * inv1a2j;
     float ujx = ux, ujy = uy;
     if (rho != 0.f) {
       const float ir = 1.f / rho;
@@ -512,12 +557,12 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
       ps[e] = fmaf(dr, sx.w[e], rr * sx.dw[e]);
     }
     const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;  // rref w0(0), rref w0(+-1)
-    const float om = P.omega[j], omt = P.omega[j] * P.t1t2[j];
+    const float om = omj, omt = omtj;
     // w1 tau1 Psi_i = PSX_i gfx + PSY_i gfy with psi = PSX / (4 c_j), 1 / c_j = sqrt(M_j)
-    const float gfs = P.wt1[j] * rho * P.invtau2[j] * 0.25f * P.sqrtM[j];
+    const float gfs = wt1j * rho * invtau2j * 0.25f * P.sqrtM[j];
     const float gfx = gfs * Ucx, gfy = gfs * Ucy;
     // w1 tau1 Phi_i with phi = M_j {-1, 1/4 on the axis links, 0 on diagonals}
-    const float gphi = P.wt1[j] * M * dqj;
+    const float gphi = wt1j * M * dqj;
     float hn[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -584,9 +629,9 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, co
   gas_node<PT, NS, PHI, MODE>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, mom, Tgas, flags, smem, threadIdx.x, 0U);
 }
 
-template <int NS, int MODE>
+template <int NS, int MODE, bool LT = false>
 size_t gas_smem_bytes() {
-  return sizeof(float) * (MODE == 0 ? (NS * Q + NS) * GB : 1);
+  return sizeof(float) * (MODE == 0 ? (NS * Q + (LT ? 3 : 1) * NS) * GB : 1);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -826,7 +871,7 @@ __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], doub
 // solid blocks the wall + FD update of consecutive solid nodes. The host interleaves
 // the descriptors by row bands so that wall blocks follow the gas blocks of the same
 // rows and find their neighbours' populations in L2.
-template <class PT, int NS, bool PHI>
+template <class PT, int NS, bool PHI, bool LT = false>
 __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     DevParams P, const PT* __restrict__ src, PT* __restrict__ dst, const uint32_t* __restrict__ code,
     const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
@@ -839,7 +884,7 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   if (d.x == 0) {
     if (tid < d.z) {
       const int2 g = __ldg(gas_list + d.y + tid);
-      gas_node<PT, NS, PHI, 0>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid, step);
+      gas_node<PT, NS, PHI, 0, LT>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid, step);
     }
     return;
   }
@@ -968,8 +1013,18 @@ __global__ void init_kernel(DevParams P, PT* __restrict__ h0, PT* __restrict__ h
     if (c == GAS) {
       // Moment field of the time level before the first step: the initial fields.
       F0[k] = F1[k] = float(T - Tref);
+      // K_j = kcoef_j C_j T; with local relaxation times kcoef0_j tau1_j of this node's
+      // initial composition and temperature (Eq. tau1s)
+      double Ct = 0.0, t1l[MAX_NS];
+      for (int j = 0; j < P.ns; ++j) Ct += C * Xn[j];
+      for (int j = 0; j < P.ns; ++j) {
+        double sphi = 0.0;
+        for (int q = 0; q < P.ns; ++q) sphi += (C * Xn[q] / Ct) * double(P.phi_w[j][q]);
+        t1l[j] = double(P.mu_l[j]) / (Ct * T * sphi);
+      }
       for (int j = 0; j < P.ns; ++j)
-        F0[(long long)(1 + j) * P.plane + k] = F1[(long long)(1 + j) * P.plane + k] = float(double(P.kcoef[j]) * C * Xn[j] * T);
+        F0[(long long)(1 + j) * P.plane + k] = F1[(long long)(1 + j) * P.plane + k] =
+            float((P.local_tau ? double(P.kcoef0[j]) * t1l[j] : double(P.kcoef[j])) * C * Xn[j] * T);
     }
     if (c == GAS && real) {
       for (int j = 0; j < P.ns; ++j) mom[(long long)j * P.n + n] = float(C * Xn[j] * P.M[j]);
@@ -1105,38 +1160,48 @@ cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, cudaStr
   }
 }
 
-template <class PT, int NS, bool PHI>
+template <class PT, int NS, bool PHI, bool LT = false>
 cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   if (P.n_blocks <= 0) return cudaSuccess;
-  const size_t smem = gas_smem_bytes<NS, 0>();
+  const size_t smem = gas_smem_bytes<NS, 0, LT>();
   static unsigned long long configured = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && !(configured & (1ull << dev))) {
-    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured |= 1ull << dev;
   }
   const int dstb = 1 - src;
   const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
-  step_kernel<PT, NS, PHI><<<P.n_blocks, GB, smem, st>>>(
+  step_kernel<PT, NS, PHI, LT><<<P.n_blocks, GB, smem, st>>>(
       P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
       paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
       S.flags, S.rw, step);
   return cudaGetLastError();
 }
 
+// Locally updated relaxation times run the FP32 kernels instantiated in
+// fdlbm_local_tau.cu (the host rejects other storage types).
+template <class PT, int NS>
+cudaError_t step_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
+  const bool phi = P.energy_correction != 0;
+  if constexpr (sizeof(PT) == 4) {
+    if (P.local_tau) return launch_step_local_tau(P, S, src, st, step);
+  }
+  return phi ? step_launch<PT, NS, true>(P, S, src, st, step) : step_launch<PT, NS, false>(P, S, src, st, step);
+}
+
 template <class PT>
 cudaError_t dispatch_step(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
-  const bool phi = P.energy_correction != 0;
   switch (P.ns) {
-    case 1: return phi ? step_launch<PT, 1, true>(P, S, src, st, step) : step_launch<PT, 1, false>(P, S, src, st, step);
-    case 2: return phi ? step_launch<PT, 2, true>(P, S, src, st, step) : step_launch<PT, 2, false>(P, S, src, st, step);
-    case 3: return phi ? step_launch<PT, 3, true>(P, S, src, st, step) : step_launch<PT, 3, false>(P, S, src, st, step);
-    case 4: return phi ? step_launch<PT, 4, true>(P, S, src, st, step) : step_launch<PT, 4, false>(P, S, src, st, step);
-    case 5: return phi ? step_launch<PT, 5, true>(P, S, src, st, step) : step_launch<PT, 5, false>(P, S, src, st, step);
-    case 6: return phi ? step_launch<PT, 6, true>(P, S, src, st, step) : step_launch<PT, 6, false>(P, S, src, st, step);
+    case 1: return step_ns<PT, 1>(P, S, src, st, step);
+    case 2: return step_ns<PT, 2>(P, S, src, st, step);
+    case 3: return step_ns<PT, 3>(P, S, src, st, step);
+    case 4: return step_ns<PT, 4>(P, S, src, st, step);
+    case 5: return step_ns<PT, 5>(P, S, src, st, step);
+    case 6: return step_ns<PT, 6>(P, S, src, st, step);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -78,6 +78,12 @@ struct DevParams {
   int nz, zoff, periodic_z;
   long long slab;       // padded cells of one z layer
   float W0_19[19];      // D3Q19 rest-equilibrium weights at T_ref
+  // locally updated relaxation times
+  int local_tau;
+  float mu_l[MAX_NS];               // species viscosities
+  float phi_w[MAX_NS][MAX_NS];      // Wilke coefficients phi_jk
+  float invD[MAX_NS][MAX_NS];       // 1 / D_jk (0 on the diagonal)
+  float kcoef0[MAX_NS];             // energy-correction flux coefficient per unit tau1
 };
 
 // Device state of one handle.
@@ -177,6 +183,9 @@ cudaError_t launch_populations_out3(const DevParams& P, const DevState& S, int c
                                     cudaStream_t st);
 cudaError_t launch_totals3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 cudaError_t launch_residual3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
+
+// One D2Q9 step with locally updated relaxation times (FP32 storage; fdlbm_local_tau.cu).
+cudaError_t launch_step_local_tau(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
 
 // Bytes of one stored population.
 inline size_t pop_bytes_per_value(int storage) { return storage == FDLBM_STORAGE_FP32 ? 4 : 2; }

@@ -35,7 +35,8 @@ class Geometry(C.Structure):
 
 class Species(C.Structure):
     _fields_ = [("M_gmol", C.c_double), ("tau1", C.c_double), ("tau2", C.c_double),
-                ("X_init", C.c_double), ("X_inlet", C.c_double)]
+                ("X_init", C.c_double), ("X_inlet", C.c_double), ("mu", C.c_double),
+                ("D", C.c_double * MAX_NS)]
 
 
 class Transport(C.Structure):
@@ -44,7 +45,7 @@ class Transport(C.Structure):
                 ("T_solid_init_K", C.c_double), ("T_outer_K", C.c_double),
                 ("u_inlet", C.c_double), ("inlet_profile", C.c_int),
                 ("alpha_s", C.c_double), ("rhocp_s", C.c_double), ("kappa_f", C.c_double),
-                ("coupling", C.c_int)]
+                ("coupling", C.c_int), ("local_tau", C.c_int)]
 
 
 class Kinetics(C.Structure):
@@ -192,11 +193,13 @@ class Solver:
         ns = len(sp)
         spec = (Species * ns)()
         for j, d in enumerate(sp):
-            spec[j] = Species(d["M_gmol"], d["tau1"], d["tau2"], d["X_init"], d["X_inlet"])
+            Drow = (C.c_double * MAX_NS)(*[float(v) for v in d.get("D", [])][:MAX_NS])
+            spec[j] = Species(d["M_gmol"], d["tau1"], d["tau2"], d["X_init"], d["X_inlet"],
+                              float(d.get("mu", 0.0)), Drow)
         tr = Transport(p["Pr"], int(p["energy_correction"]), p["T0_K"], p["T_init_K"],
                        p["T_inlet_K"], p["T_solid_init_K"], p["T_outer_K"], p["u_inlet"],
                        int(p["inlet_profile"]), p["alpha_s"], p["rhocp_s"], p["kappa_f"],
-                       int(p["coupling"]))
+                       int(p["coupling"]), int(p.get("local_tau", 0)))
         kin = Kinetics()
         kin.n_react = len(p["reactions"])
         for r, d in enumerate(p["reactions"]):

@@ -161,3 +161,38 @@ def test_unstable_state_is_reported_not_faulted():
     with pytest.raises(fdlbm.FdlbmError) as ei:
         s.sync()
     assert ei.value.status == -4
+
+
+# ---------------------------------------------------------------------------------------
+# Locally updated relaxation times (Sec. 3)
+# ---------------------------------------------------------------------------------------
+
+def test_parity_local_tau_periodic():
+    """Relaxation times updated at every node and step from the local composition and
+    temperature (Wilke viscosity, mixture-averaged diffusion): GPU against the oracle on a
+    periodic box from random fields."""
+    p = W.local_transport(W.periodic_box(40, 28, reactions=[], Pr=0.7))
+    p["init"] = W.random_fields(p, seed=71)
+    s, o = run_both(p, 150)
+    assert_parity(s, o, what="local tau periodic")
+    s.close()
+
+
+def test_parity_local_tau_channel():
+    """Catalytic channel with inlet, outlet, reactive walls and FD solid, local relaxation
+    times."""
+    p = W.local_transport(W.channel(nx=72, n_gas=20, wall=4))
+    s, o = run_both(p, 200)
+    assert_parity(s, o, what="local tau channel")
+    s.close()
+
+
+def test_local_tau_rejected_where_not_built():
+    fdlbm = _fdlbm()
+    p = W.local_transport(W.periodic_box(16, 12, reactions=[]))
+    with pytest.raises(fdlbm.FdlbmError):
+        fdlbm.Solver(p, storage="bf16")
+    a = fdlbm.Solver(p)
+    with pytest.raises(fdlbm.FdlbmError):
+        fdlbm.Batch([a])
+    a.close()

@@ -49,3 +49,37 @@ def test_solver_refuses_without_cuda():
     from paper_1804_07588_gb300 import fdlbm, workloads
     with pytest.raises(RuntimeError):
         fdlbm.Solver(workloads.periodic_box(8, 8))
+
+
+# C struct name in include/fdlbm.h -> ctypes mirror in the binding
+_STRUCTS = {"fdlbm_geometry": "Geometry", "fdlbm_species": "Species", "fdlbm_transport": "Transport",
+            "fdlbm_kinetics": "Kinetics", "fdlbm_fields": "Fields", "fdlbm_options": "Options",
+            "fdlbm_info_t": "Info", "fdlbm_balance": "Balance"}
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """Every ctypes mirror of an ABI struct has the size and field offsets the C compiler
+    gives the struct in include/fdlbm.h (a plain C program compiled with gcc prints
+    them), so argument marshalling cannot drift from the header."""
+    import shutil
+    import subprocess
+    from paper_1804_07588_gb300 import fdlbm
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fdlbm.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(fdlbm, pyname)
+        lines.append(f'  printf("{pyname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{pyname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for ln in filter(None, out):
+        pyname, what, value = ln.split()
+        cls = getattr(fdlbm, pyname)
+        got = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert got == int(value), f"{pyname}.{what}: ctypes {got}, C {value}"
