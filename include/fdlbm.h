@@ -88,6 +88,12 @@ typedef struct {
   const uint8_t* mask;     /* host, nx*ny (2D) or nx*ny*nz (3D), x fastest then y, FDLBM_MASK_* */
   int face_bc[6];          /* FDLBM_FACE_* for x-, x+, y-, y+, z-, z+ (z faces: 3D only) */
   int nz;                  /* D3Q19: z size >= 4; ignored for D2Q9 */
+  /* Optional (D2Q9, may be NULL): host [2][n] lattice velocity of solid nodes. An
+   * interface wall node with a velocity U_w is a moving diffusive wall: it emits
+   * f^eq_j(1, U_w, T_w) (Eq. BC_g_ji_1 with the wall velocity) in place of the rest
+   * weights. The solid's FD heat step is unchanged; with FDLBM_COUPLING_CONSERVATIVE the
+   * mechanical work the wall does on the gas is charged to the solid's enthalpy. */
+  const double* wall_u;
 } fdlbm_geometry;
 
 /* One gas species (Sec. 2; relaxation times in lattice units). */

@@ -63,6 +63,7 @@ class _Problem(C.Structure):
         ("init_T", C.POINTER(C.c_double)), ("init_Ts", C.POINTER(C.c_double)),
         ("init_C", C.POINTER(C.c_double)),
         ("local_tau", C.c_int), ("mu", C.c_double * MAX_NS), ("Djk", (C.c_double * MAX_NS) * MAX_NS),
+        ("wall_u", C.POINTER(C.c_double)),
     ]
 
 
@@ -191,6 +192,10 @@ class Oracle:
                 a = np.ascontiguousarray(init[key], dtype=np.float64)
                 self._keep.append(a)
                 setattr(s, field, _dptr(a))
+        if p.get("wall_u") is not None:
+            wu = np.ascontiguousarray(p["wall_u"], dtype=np.float64)
+            self._keep.append(wu)
+            s.wall_u = _dptr(wu)
         if p.get("local_tau"):
             s.local_tau = 1
             for j, d in enumerate(sp):

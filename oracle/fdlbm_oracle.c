@@ -64,6 +64,7 @@ struct ora_state {
   double* Cj_prev;           /* [ns][n] concentrations of the previous time level */
   double* divq;              /* scratch [ns][n] */
   double* tau1_prev;         /* [ns][n] local tau1 of the previous time level (local_tau) */
+  double* wall_u;            /* [2][n] wall velocity of solid nodes */
   double* q;                 /* [n] reaction heat of the step at wall nodes */
   double* dE;                /* [n] energy the wall put into the gas this step */
   double* snap;              /* residual snapshot */
@@ -481,6 +482,9 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
   memcpy(s->mask, p->mask, (size_t)n);
   s->p.mask = s->mask;
   s->p.init_X = s->p.init_u = s->p.init_T = s->p.init_Ts = s->p.init_C = NULL;
+  s->wall_u = (double*)xcalloc((size_t)2 * n, sizeof(double));
+  if (p->wall_u) memcpy(s->wall_u, p->wall_u, sizeof(double) * 2 * (size_t)n);
+  s->p.wall_u = s->wall_u;
   s->cls = (int*)xcalloc((size_t)n, sizeof(int));
   size_t np = (size_t)ns * Q * n;
   s->g = (double*)xcalloc(np, sizeof(double));
@@ -625,6 +629,7 @@ void ora_destroy(ora_state* s) {
   free(s->Cj_prev);
   free(s->divq);
   free(s->tau1_prev);
+  free(s->wall_u);
   free(s->q);
   free(s->dE);
   free(s->snap);
@@ -651,11 +656,18 @@ static void wall_pass(ora_state* s) {
       if (s->cls[k] != CL_WALL) continue;
       double Tw = s->Ts[k]; /* wall temperature = solid temperature, Sec. 5 */
       int out[Q] = {0}, arr[Q] = {0};
-      double B = 0.0;
       for (int i = 1; i < Q; ++i) {
         out[i] = cls_at(s, x + EX[i], y + EY[i]) == CL_GAS;
         arr[i] = cls_at(s, x - EX[i], y - EY[i]) == CL_GAS;
-        if (out[i]) B += wrest(i, Tw);
+      }
+      /* Emitted shape per species: f^eq_j(1, U_w, T_w) (at rest the rest weights), and
+       * its sum B_j over the emission directions. */
+      double fw[ORA_MAX_NS][Q], B[ORA_MAX_NS];
+      for (int j = 0; j < ns; ++j) {
+        ora_equilibrium(1.0, s->wall_u[k], s->wall_u[(size_t)s->n + k], s->M[j], Tw, fw[j]);
+        B[j] = 0.0;
+        for (int i = 1; i < Q; ++i)
+          if (out[i]) B[j] += fw[j][i];
       }
       double A[ORA_MAX_NS], Earr = 0.0;
       for (int j = 0; j < ns; ++j) {
@@ -669,7 +681,7 @@ static void wall_pass(ora_state* s) {
       }
       double rw[ORA_MAX_NS], rate[ORA_MAX_NR] = {0}, m[ORA_MAX_NS];
       int catalytic = s->mask[k] == 2 && s->p.nr > 0;
-      for (int j = 0; j < ns; ++j) rw[j] = A[j] / B;
+      for (int j = 0; j < ns; ++j) rw[j] = A[j] / B[j];
       if (catalytic) {
         int conv = 0;
         for (int it = 0; it < s->p.rho_w_maxit; ++it) {
@@ -678,7 +690,7 @@ static void wall_pass(ora_state* s) {
           for (int j = 0; j < ns; ++j) {
             double mj = 0.0;
             for (int r = 0; r < s->p.nr; ++r) mj += s->M[j] * s->p.nu[r][j] * rate[r];
-            double nw = (A[j] + mj) / B;
+            double nw = (A[j] + mj) / B[j];
             double dd = fabs(nw - rw[j]);
             d = dd > d ? dd : d;
             rw[j] = nw;
@@ -697,7 +709,7 @@ static void wall_pass(ora_state* s) {
         for (int r = 0; r < s->p.nr && catalytic; ++r) m[j] += s->M[j] * s->p.nu[r][j] * rate[r];
         for (int i = 1; i < Q; ++i)
           if (out[i]) {
-            double w = wrest(i, Tw) * (A[j] + m[j]) / B; /* Eq. BC_gji, count form */
+            double w = fw[j][i] * (A[j] + m[j]) / B[j]; /* Eq. BC_gji, count form */
             s->gn[PIDX(s, j, i, k)] = w;
             Eout += 0.5 * s->c[j] * s->c[j] * (EX[i] * EX[i] + EY[i] * EY[i]) * w;
           }

@@ -48,6 +48,9 @@ typedef struct {
   int local_tau;
   double mu[ORA_MAX_NS];
   double Djk[ORA_MAX_NS][ORA_MAX_NS];
+  /* Optional [2][n] velocity of solid nodes (lattice): a moving diffusive wall emits
+   * f^eq(1, U_w, T_w) (Eq. BC_g_ji_1 with the wall velocity); NULL: walls at rest. */
+  const double* wall_u;
 } ora_problem;
 
 typedef struct ora_state ora_state;

@@ -566,6 +566,14 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.flags, int, 4);
   ALLOC(S.red, double, totals_count(ns) + residual_count3(ns) + LG_COUNT + 8);
   ALLOC(h->out_buf, float, (size_t)(2 * ns + 4) * n);
+  std::vector<float2> wall_u;
+  if (geom->wall_u) {
+    // velocity of every wall-list entry (moving diffusive walls)
+    wall_u.resize(std::max<size_t>(walls.size(), 1), make_float2(0.f, 0.f));
+    for (size_t q = 0; q < walls.size(); ++q)
+      wall_u[q] = make_float2((float)geom->wall_u[walls[q]], (float)geom->wall_u[(size_t)n + walls[q]]);
+    ALLOC(S.wall_u, float2, wall_u.size());
+  }
 #undef ALLOC
   cudaError_t e = cudaMemcpyAsync(S.code, pcode.data(), sizeof(uint32_t) * pcode.size(), cudaMemcpyHostToDevice,
                                   h->stream);
@@ -577,6 +585,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (e == cudaSuccess && !gas_list.empty())
     e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int2) * gas_list.size(), cudaMemcpyHostToDevice,
                         h->stream);
+  if (e == cudaSuccess && !wall_u.empty())
+    e = cudaMemcpyAsync(S.wall_u, wall_u.data(), sizeof(float2) * wall_u.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     release(h);
@@ -788,6 +798,7 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
     return fail(FDLBM_EINVAL, "inlet only on x-, outlet only on x+");
   if (tr->alpha_s > 1.0 / 6.0) return fail(FDLBM_EINVAL, "alpha_s must be <= 1/6 (explicit FD stability in 3D)");
   if (tr->inlet_profile != FDLBM_PROFILE_PLUG) return fail(FDLBM_EINVAL, "D3Q19: plug inlet only");
+  if (geom->wall_u) return fail(FDLBM_EINVAL, "D3Q19: moving walls are not implemented");
   const int storage = opts ? opts->storage : FDLBM_STORAGE_FP32;
   double Mmin = 1e300;
   for (int j = 0; j < ns; ++j) Mmin = std::min(Mmin, species[j].M_gmol);

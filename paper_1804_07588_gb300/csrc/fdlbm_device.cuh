@@ -683,12 +683,20 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // into acc (Q_rxn, Q_wall, Q_couple, Q_fixedT, non-converged iterations). rw_prev
 // [ns][n_wall_list] holds each catalytic wall's converged density of the previous step
 // (NaN before the first step), the start of its iteration.
+// A moving wall (wall_u != nullptr: velocity per wall-list entry) emits f^eq_j(1, U_w, T_w)
+// of each species instead of the rest weights (Eq. BC_g_ji_1 with the wall velocity).
+__device__ __forceinline__ float wmove(int i, float sM, float M, float2 u, float T) {
+  const float fx = EX(i) == 0 ? 1.f - M * u.x * u.x - T : 0.5f * (float(EX(i)) * sM * u.x + M * u.x * u.x + T);
+  const float fy = EY(i) == 0 ? 1.f - M * u.y * u.y - T : 0.5f * (float(EY(i)) * sM * u.y + M * u.y * u.y + T);
+  return fx * fy;
+}
+
 template <class PT, int NS>
 __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                            const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
                                            const uint32_t* __restrict__ code, const float* __restrict__ Tgas, int n,
                                            double (&acc)[LG_COUNT], float* __restrict__ rw_prev, int idx,
-                                           uint32_t step) {
+                                           uint32_t step, const float2* __restrict__ wall_u) {
   {
     const int x = n % P.nx, y = n / P.nx;
     const int k = pad_index(P, x, y);
@@ -764,10 +772,27 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
           Earr = fmaf(e2h * P.c2[j], v, Earr);
         }
       }
-      const float iB = 1.f / B;
+      // normalisation of the emitted shape: 1 / B, per species for a moving wall
+      float iBj[NS];
+      const bool moving = wall_u != nullptr;
+      float2 uw = make_float2(0.f, 0.f);
+      if (moving) {
+        uw = wall_u[idx];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+          float Bj = 0.f;
+          for (int i = 1; i < Q; ++i)
+            if (arr & (1u << OPP(i))) Bj += wmove(i, P.sqrtM[j], P.M[j], uw, Tw);
+          iBj[j] = 1.f / Bj;
+        }
+      } else {
+        const float iB = 1.f / B;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) iBj[j] = iB;
+      }
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
-        rw[j] = A[j] * iB;
+        rw[j] = A[j] * iBj[j];
         mj[j] = 0.f;
       }
       float rate[MAX_NR] = {0.f, 0.f, 0.f, 0.f};
@@ -792,7 +817,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
           for (int j = 0; j < NS; ++j) {
             float mm = 0.f;
             for (int r = 0; r < P.nr; ++r) mm += P.M[j] * float(P.nu[r][j]) * rate[r];
-            const float nw = (A[j] + mm) * iB;
+            const float nw = (A[j] + mm) * iBj[j];
             d = fmaxf(d, fabsf(nw - rw[j]));
             rmax = fmaxf(rmax, fabsf(nw));
             rw[j] = nw;
@@ -815,7 +840,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
       float Eout = 0.f;
       float scale[NS];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iB;
+      for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iBj[j];
       // Emissions towards the gas neighbours (the directions opposite to the arrivals).
 #pragma unroll 1
       for (int i = 1; i < Q; ++i) {
@@ -824,7 +849,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
         const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          const float w = wr * scale[j];
+          const float w = (moving ? wmove(i, P.sqrtM[j], P.M[j], uw, Tw) : wr) * scale[j];
           pop_store_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, w - P.rref[j] * P.W0[i], P.hs[j], seed,
                            j * Q + i);
           Eout = fmaf(e2h * P.c2[j], w, Eout);
@@ -877,7 +902,8 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
     const float* __restrict__ Fsrc, float* __restrict__ Fdst, const float* __restrict__ Ts_src,
     float* __restrict__ Ts_dst, const float* __restrict__ Tgas_src, float* __restrict__ Tgas_dst,
-    double* __restrict__ ledger, int* __restrict__ flags, float* __restrict__ rw_prev, uint32_t step) {
+    double* __restrict__ ledger, int* __restrict__ flags, float* __restrict__ rw_prev, uint32_t step,
+    const float2* __restrict__ wall_u) {
   extern __shared__ float smem[];
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
@@ -893,7 +919,7 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
   if (tid < d.z)
     solid_node<PT, NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
-                       d.y + tid, step);
+                       d.y + tid, step, wall_u);
   ledger_block_store(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
@@ -940,7 +966,7 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel_batch(
   for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
   if (tid < d.z)
     solid_node<PT, NS>(P, hs, hd, S.Ts[src], S.Ts[dstb], S.code, paper ? S.Tgas + (long long)src * P.n : nullptr,
-                       __ldg(S.solid_list + d.y + tid), acc, S.rw, d.y + tid, step);
+                       __ldg(S.solid_list + d.y + tid), acc, S.rw, d.y + tid, step, S.wall_u);
   ledger_block_store(acc, S.ledger + (long long)d.w * LG_COUNT);
 }
 
@@ -1178,7 +1204,7 @@ cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStre
   step_kernel<PT, NS, PHI, LT><<<P.n_blocks, GB, smem, st>>>(
       P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
       paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
-      S.flags, S.rw, step);
+      S.flags, S.rw, step, S.wall_u);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ struct DevState {
   float* rw;            // converged wall densities of the last step, [ns][n_wall_list] (NaN: none)
   double* red;          // reduction scratch (doubles)
   uint64_t* code64;     // D3Q19: node code words on the padded lattice, [plane]
+  float2* wall_u;       // velocity of each wall-list entry (moving walls), or nullptr
 };
 
 enum Ledger { LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV, LG_COUNT };

@@ -30,7 +30,8 @@ class FdlbmError(RuntimeError):
 
 class Geometry(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lattice", C.c_int),
-                ("mask", C.POINTER(C.c_uint8)), ("face_bc", C.c_int * 6), ("nz", C.c_int)]
+                ("mask", C.POINTER(C.c_uint8)), ("face_bc", C.c_int * 6), ("nz", C.c_int),
+                ("wall_u", C.POINTER(C.c_double))]
 
 
 class Species(C.Structure):
@@ -189,6 +190,10 @@ class Solver:
         g.mask = mask.ctypes.data_as(C.POINTER(C.c_uint8))
         for f in range(6):
             g.face_bc[f] = p["face_bc"][f] if f < len(p["face_bc"]) else 0
+        if p.get("wall_u") is not None:
+            wu = np.ascontiguousarray(p["wall_u"], dtype=np.float64)
+            keep.append(wu)
+            g.wall_u = _dptr(wu)
         sp = p["species"]
         ns = len(sp)
         spec = (Species * ns)()

@@ -135,6 +135,38 @@ def channel(nx: int = 128, n_gas: int = 32, wall: int = 8, u_inlet: float = 0.02
                  u_inlet=u_inlet, inlet_profile=profile, **kw)
 
 
+def couette(n_gas: int = 32, U_w: float = 0.03, dT_K: float = 2.0, nx: int = 1, linear_start: bool = True,
+            **kw) -> dict:
+    """Thermal Couette flow (the paper's viscous-heating test, Sec. 4.4): ``n_gas`` gas rows
+    between a plate at rest (y = 0) and a plate moving at ``U_w`` along x (y = ny - 1), the
+    moving one ``dT_K`` warmer; periodic in x. The plates are one-node FD-solid rows with
+    a huge heat capacity and no conduction, so their temperatures stay fixed. With
+    ``linear_start`` the gas starts from the linear velocity and temperature profiles."""
+    ny = n_gas + 2
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0] = INERT
+    mask[-1] = INERT
+    kw.setdefault("reactions", [])
+    kw.setdefault("alpha_s", 0.0)
+    kw.setdefault("rhocp_s", 1e12)
+    p = _base(2, nx, ny, 1, mask, [PERIODIC, PERIODIC, CLOSED, CLOSED], **kw)
+    n = nx * ny
+    wu = np.zeros((2, ny, nx))
+    wu[0, -1, :] = U_w
+    p["wall_u"] = wu.reshape(2, n)
+    Ts = np.full((ny, nx), p["T_solid_init_K"])
+    Ts[-1] += dT_K
+    init = {"Ts_K": Ts.reshape(n)}
+    if linear_start:
+        y = np.repeat(np.arange(ny)[:, None], nx, 1) / (ny - 1)
+        u = np.zeros((2, ny, nx))
+        u[0] = U_w * y
+        init["u"] = u.reshape(2, n)
+        init["T_K"] = (p["T_init_K"] + dT_K * y).reshape(n)
+    p["init"] = init
+    return p
+
+
 def disk_mask(nx: int, ny: int, porosity: float, rmin: float, rmax: float, seed: int,
               free_cols: int = 17, gap: float = 2.0, max_tries: int = 2_000_000):
     """Seeded random sequential addition of non-overlapping disks, periodic in y.

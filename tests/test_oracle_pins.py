@@ -554,3 +554,40 @@ def test_local_tau_conserves_periodic():
     np.testing.assert_allclose(o.balance()["mass"], b0["mass"], rtol=1e-13)
     P1 = momentum()
     assert max(abs(P1[0] - P0[0]), abs(P1[1] - P0[1])) < 1e-14 * b0["mass"].sum()
+
+
+# ---------------------------------------------------------------------------------------
+# Thermal Couette flow (Sec. 4.4, Eq. thermal_couette)
+# ---------------------------------------------------------------------------------------
+
+def _couette(n_gas, Pr, ec, U=0.03, dT_K=2.0, tau=0.25, steps=20000):
+    p = _unit_mass(W.couette(n_gas, U_w=U, dT_K=dT_K, Pr=Pr, energy_correction=ec), tau=tau)
+    ny = n_gas + 2
+    L = ny - 1
+    y = np.arange(ny)
+    o = oracle.Oracle(p)
+    o.step(steps)
+    m = o.moments()
+    yi = y[1:-1] / L
+    T = m[12][1:-1] / (3 * p["T0_K"])
+    cp = 2.0   # isobaric heat capacity per unit mass of the equal-mass 2D gas, (D + 2) / (2 M)
+    lin = T - p["T_init_K"] / (3 * p["T0_K"]) - dT_K / (3 * p["T0_K"]) * yi
+    visc = np.polyfit(yi * (1 - yi), lin, 1)[0] / (Pr * U * U / (2 * cp))
+    return visc, np.abs(m[10][1:-1] - U * yi).max() / U, L
+
+
+@pytest.mark.parametrize("pr,ec", [(1.0, 1), (0.7, 1), (4.0, 0)])
+def test_thermal_couette_viscous_heating(pr, ec):
+    """Steady thermal Couette flow between a plate at rest and a hotter plate moving at
+    U_w (diffusive walls emitting f^eq(1, U_w, T_w)): the velocity profile is linear and
+    the temperature carries the viscous heating Pr U_w^2 / (2 c_p) (x/L)(1 - x/L) on top
+    of the linear conduction profile (Eq. thermal_couette, read with T - T0 in place of
+    its garbled left side), for Pr = 1 and 0.7 with the energy correction and for the
+    uncorrected model (Pr = 4, as the paper states). The diffusive walls slip to first
+    order in 1/L: the viscous-heating coefficient is extrapolated from L = 17 and 33 to
+    1/L -> 0 (3% tolerance); the velocity is within 1.5% at L = 33."""
+    v1, _, L1 = _couette(16, pr, ec)
+    v2, uerr, L2 = _couette(32, pr, ec)
+    v0 = (L2 * v2 - L1 * v1) / (L2 - L1)
+    assert abs(v0 - 1.0) < 0.03, (v1, v2, v0)
+    assert uerr < 0.015, uerr
