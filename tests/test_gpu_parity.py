@@ -218,3 +218,18 @@ def test_parity_couette_moving_wall(unit_mass):
     s_, o = run_both(p, 3000)
     assert_parity(s_, o, what="couette", vector_u=True)  # uy is zero up to rounding
     s_.close()
+
+
+def test_enthalpy_coupling_error_paper_box_gpu():
+    """The paper's 200 x 3 solid/gas enthalpy-coupling box on the GPU (FP32 state, FP64
+    ledger): eps of Eq. error_coupling below the paper's order 1e-5."""
+    p = W.periodic_box(200, 3, solid_cols=100, energy_correction=0, reactions=[W.wgs_reaction(k0=2000.0)])
+    for s in p["species"]:
+        s["M_gmol"] = 2.016
+        s["tau1"] = s["tau2"] = 0.8
+    sv = _fdlbm().Solver(p)
+    sv.step(3000)
+    b = sv.balance()
+    assert b["Q_reaction"] > 0
+    assert abs(b["eps_paper"]) < 1e-5, b["eps_paper"]
+    sv.close()

@@ -591,3 +591,19 @@ def test_thermal_couette_viscous_heating(pr, ec):
     v0 = (L2 * v2 - L1 * v1) / (L2 - L1)
     assert abs(v0 - 1.0) < 0.03, (v1, v2, v0)
     assert uerr < 0.015, uerr
+
+
+@pytest.mark.parametrize("tau,ec", [(0.6, 0), (0.8, 0), (1.0, 0), (0.25, 1)])
+def test_enthalpy_coupling_error_paper_box(tau, ec):
+    """The paper's enthalpy-coupling test (Sec. 5, Eq. error_coupling): a 200 x 3 box
+    periodic in all directions, half FD solid and half gas, water-gas shift at the two
+    interfaces. The paper finds eps of the order 1e-5 for a wide range of tau1; with the
+    conservative interface coupling (reading R12) and equal species masses (every species
+    on-lattice, so the reactive wall's mole bookkeeping is exact) eps stays below 1e-5."""
+    p = _unit_mass(W.periodic_box(200, 3, solid_cols=100, energy_correction=ec,
+                                  reactions=[W.wgs_reaction(k0=2000.0)]), tau=tau)
+    o = oracle.Oracle(p)
+    o.step(3000)
+    b = o.balance()
+    assert b["Q_reaction"] > 0
+    assert abs(b["eps_paper"]) < 1e-5, b["eps_paper"]
