@@ -86,7 +86,8 @@ typedef struct {
   int nx, ny;              /* lattice size, each >= 4 */
   int lattice;             /* FDLBM_D2Q9 or FDLBM_D3Q19 */
   const uint8_t* mask;     /* host, nx*ny (2D) or nx*ny*nz (3D), x fastest then y, FDLBM_MASK_* */
-  int face_bc[6];          /* FDLBM_FACE_* for x-, x+, y-, y+, z-, z+ (z faces: 3D only) */
+  int face_bc[6];          /* FDLBM_FACE_* for x-, x+, y-, y+, z-, z+ (z faces: 3D only); a
+                              periodic axis needs at least 8 nodes (D2Q9) or 6 (D3Q19) */
   int nz;                  /* D3Q19: z size >= 4; ignored for D2Q9 */
   /* Optional (D2Q9, may be NULL): host [2][n] lattice velocity of solid nodes. An
    * interface wall node with a velocity U_w is a moving diffusive wall: it emits

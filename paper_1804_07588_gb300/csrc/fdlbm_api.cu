@@ -202,6 +202,15 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (fb[1] == FDLBM_FACE_INLET || fb[0] == FDLBM_FACE_OUTLET || fb[2] == FDLBM_FACE_INLET ||
       fb[3] == FDLBM_FACE_INLET || fb[2] == FDLBM_FACE_OUTLET || fb[3] == FDLBM_FACE_OUTLET)
     return fail(FDLBM_EINVAL, "inlet only on x-, outlet only on x+");
+  {
+    // A node writes the periodic copy for one face only, so no node may lie within the
+    // ghost depth of both faces of a periodic axis.
+    const int minp = 2 * (geom->lattice == FDLBM_D3Q19 ? GHOST3 : GHOST);
+    const int len[3] = {geom->nx, geom->ny, geom->lattice == FDLBM_D3Q19 ? geom->nz : minp};
+    for (int a = 0; a < (geom->lattice == FDLBM_D3Q19 ? 3 : 2); ++a)
+      if (fb[2 * a] == FDLBM_FACE_PERIODIC && len[a] < minp)
+        return fail(FDLBM_EINVAL, "periodic axis %d has %d nodes; at least %d are needed", a, len[a], minp);
+  }
   if (!(tr->T0_K > 0) || !(tr->T_inlet_K > 0) || !(tr->T_init_K > 0) || !(tr->T_solid_init_K > 0))
     return fail(FDLBM_EINVAL, "temperatures must be positive");
   if (!(tr->Pr > 0)) return fail(FDLBM_EINVAL, "Pr must be positive");

@@ -221,9 +221,11 @@ def test_parity_couette_moving_wall(unit_mass):
 
 
 def test_enthalpy_coupling_error_paper_box_gpu():
-    """The paper's 200 x 3 solid/gas enthalpy-coupling box on the GPU (FP32 state, FP64
-    ledger): eps of Eq. error_coupling below the paper's order 1e-5."""
-    p = W.periodic_box(200, 3, solid_cols=100, energy_correction=0, reactions=[W.wgs_reaction(k0=2000.0)])
+    """The paper's enthalpy-coupling box on the GPU (FP32 state, FP64 ledger): eps of Eq.
+    error_coupling below the paper's order 1e-5. 200 x 8 instead of the paper's 200 x 3:
+    the library needs at least 8 nodes across a periodic direction (twice its ghost
+    depth), and the paper finds the error independent of the system size."""
+    p = W.periodic_box(200, 8, solid_cols=100, energy_correction=0, reactions=[W.wgs_reaction(k0=2000.0)])
     for s in p["species"]:
         s["M_gmol"] = 2.016
         s["tau1"] = s["tau2"] = 0.8
@@ -233,3 +235,14 @@ def test_enthalpy_coupling_error_paper_box_gpu():
     assert b["Q_reaction"] > 0
     assert abs(b["eps_paper"]) < 1e-5, b["eps_paper"]
     sv.close()
+
+
+def test_short_periodic_axis_rejected():
+    """A periodic axis shorter than twice the ghost depth is rejected (a node would have to
+    write the periodic copies of both faces)."""
+    fdlbm = _fdlbm()
+    with pytest.raises(fdlbm.FdlbmError) as ei:
+        fdlbm.Solver(W.periodic_box(20, 6, reactions=[]))
+    assert ei.value.status == -1
+    with pytest.raises(fdlbm.FdlbmError):
+        fdlbm.Solver(W.periodic_box3(12, 12, 5, reactions=[]))
