@@ -124,6 +124,11 @@ __constant__ float4 c3_p[8] = {{0.f, 0.f, 0.f, 0.f},   {-1.f, 1.f, 0.f, 1.f}, {4
 __constant__ float2 c3_q[8] = {{0.f, 0.f}, {1.f, 2.f}, {1.f, -1.f}, {1.f, -1.f},
                                {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f},  {0.f, 0.f}};
 __constant__ int2 c3_m[8] = {{0, 0}, {-2, 0}, {0, 1}, {-2, -3}, {0, 0}, {-2, -2}, {0, 0}, {0, 0}};
+// Direction table {ex, ey, ez, number of non-zero components}.
+__constant__ int4 c3_e[Q19] = {{0, 0, 0, 0},  {1, 0, 0, 1},   {-1, 0, 0, 1},  {0, 1, 0, 1},   {0, -1, 0, 1},
+                               {0, 0, 1, 1},  {0, 0, -1, 1},  {1, 1, 0, 2},   {-1, -1, 0, 2}, {1, -1, 0, 2},
+                               {-1, 1, 0, 2}, {1, 0, 1, 2},   {-1, 0, -1, 2}, {1, 0, -1, 2},  {-1, 0, 1, 2},
+                               {0, 1, 1, 2},  {0, -1, -1, 2}, {0, 1, -1, 2},  {0, -1, 1, 2}};
 
 // Per-axis equilibrium factors and their deviations from the reference factors
 // (W(0) = 1 - T_ref, W(+-1) = T_ref / 2, S_ref = T_ref).
@@ -229,10 +234,12 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     ax[j] = ay[j] = az[j] = 0.f;
     ee[j] = ec0 * v;
   }
-  // Pull every direction: the loads of all species of one direction are issued first.
-#pragma unroll
+  // Pull every direction (a rolled loop: the direction's components come from a table,
+  // which keeps the code small); the loads of all species of one direction first.
+#pragma unroll 1
   for (int i = 1; i < Q19; ++i) {
-    const int off = (int)poff(P, i);
+    const int4 e = c3_e[i];  // {ex, ey, ez, ecoef index}
+    const int off = e.x + e.y * P.pitch + e.z * (int)P.slab;
     const uint32_t st = stencil_of3(cw, i);
     const float4 cp = c3_p[st];
     const float2 cq = c3_q[st];
@@ -249,7 +256,8 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
         vB[j] = pop_ld(src + (b + dB), P.hsi[j]);
       }
     }
-    const float ec = NNZ(i) == 1 ? ec1 : ec2;
+    const float ec = e.w == 1 ? ec1 : ec2;
+    const float fx = float(e.x), fy = float(e.y), fz = float(e.z);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       float v = v1[j];
@@ -260,12 +268,9 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
       }
       s_h[(j * Q19 + i) * G3 + tid] = v;
       dr[j] += v;
-      if (DX(i) > 0) ax[j] += v;
-      if (DX(i) < 0) ax[j] -= v;
-      if (DY(i) > 0) ay[j] += v;
-      if (DY(i) < 0) ay[j] -= v;
-      if (DZ(i) > 0) az[j] += v;
-      if (DZ(i) < 0) az[j] -= v;
+      ax[j] = fmaf(fx, v, ax[j]);
+      ay[j] = fmaf(fy, v, ay[j]);
+      az[j] = fmaf(fz, v, az[j]);
       ee[j] = fmaf(ec, v, ee[j]);
     }
   }
