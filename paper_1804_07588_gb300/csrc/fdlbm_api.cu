@@ -169,6 +169,110 @@ struct Geo {
   }
 };
 
+// Unit conversion and the per-species, solid and kinetic parameters shared by the D2Q9
+// and D3Q19 handles (Sec. 4.1 units: lattice temperature T / (3 T0), molar masses relative
+// to the lightest species, c_j = 1 / sqrt(M_j)). D enters the energy-correction
+// coefficient: K_j = (2 c_pj / Pr - (D - 1) / M_j) tau1_j C_j T with c_pj = (D + 2) /
+// (2 M_j) (the product-form lattice carries (D - 1) / (D + 2) of the kinetic heat flux).
+void set_physics_params(fdlbm_handle* h, const fdlbm_species* species, int ns, const fdlbm_transport* tr,
+                        const fdlbm_kinetics* kin, int storage, int D) {
+  DevParams& P = h->P;
+  double Mmin = 1e300;
+  for (int j = 0; j < ns; ++j) Mmin = std::min(Mmin, species[j].M_gmol);
+  P.energy_correction = tr->energy_correction ? 1 : 0;
+  P.coupling = tr->coupling;
+  h->T0 = tr->T0_K;
+  const double tl = 1.0 / (3.0 * tr->T0_K);
+  const double Tref = tr->T_inlet_K * tl;
+  h->T_inlet_lat = Tref;
+  h->T_init_lat = tr->T_init_K * tl;
+  h->Ts_init_lat = tr->T_solid_init_K * tl;
+  P.Tref = (float)Tref;
+  P.p_out = (float)Tref;  // C_in T_in with C_in = 1
+  P.u_inlet = (float)tr->u_inlet;
+  P.Tin_lat = (float)Tref;
+  h->X_init.resize(ns);
+  h->X_inlet.resize(ns);
+  for (int j = 0; j < ns; ++j) {
+    const double M = species[j].M_gmol / Mmin;
+    const double c = 1.0 / std::sqrt(M);
+    const double t1 = species[j].tau1, t2 = species[j].tau2;
+    P.M[j] = (float)M;
+    P.invM[j] = (float)(1.0 / M);
+    P.sqrtM[j] = (float)std::sqrt(M);
+    P.c[j] = (float)c;
+    P.c2[j] = (float)(1.0 / M);
+    const double a = 1.0 - c;
+    P.a[j] = (float)a;
+    P.ha[j] = (float)(0.5 * a);
+    P.ha2[j] = (float)(0.5 * a * a);
+    P.onlattice[j] = (M == 1.0);
+    P.rref[j] = (float)(species[j].X_inlet * M);
+    P.Xin[j] = (float)species[j].X_inlet;
+    P.omega[j] = (float)(2.0 / (1.0 + 2.0 * t1));
+    P.t1t2[j] = (float)(t1 / t2);
+    P.wt1[j] = (float)(2.0 * t1 / (1.0 + 2.0 * t1));
+    P.a2[j] = (float)(1.0 / (2.0 * t2));
+    P.inv1a2[j] = (float)(1.0 / (1.0 + 1.0 / (2.0 * t2)));
+    P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
+    P.invtau2[j] = (float)(1.0 / t2);
+    const double cp = (D + 2.0) / (2.0 * M);
+    P.kcoef0[j] = tr->energy_correction ? (float)(2.0 * cp / tr->Pr - (D - 1.0) / M) : 0.f;
+    P.kcoef[j] = tr->energy_correction ? (float)((2.0 * cp / tr->Pr - (D - 1.0) / M) * t1) : 0.f;
+    // Locally updated relaxation times: Wilke's phi_jk (bracket squared, so phi_jj = 1)
+    // and 1 / D_jk.
+    P.mu_l[j] = (float)species[j].mu;
+    for (int q = 0; q < ns; ++q) {
+      const double Mq = species[q].M_gmol / Mmin;
+      if (tr->local_tau) {
+        const double b = 1.0 + std::sqrt(species[j].mu / species[q].mu) * std::pow(Mq / M, 0.25);
+        P.phi_w[j][q] = (float)(b * b / std::sqrt(8.0 * (1.0 + M / Mq)));
+        P.invD[j][q] = q == j ? 0.f : (float)(1.0 / species[j].D[q]);
+      }
+    }
+    // FP16 storage: deviations |g - rref W0| stay below 2 M_j + rref_j (a population never
+    // exceeds its species density, bounded by the molar mass at twice the inlet molar
+    // concentration); the largest power of two that maps that bound below 2^15 keeps
+    // them inside FP16's range (max 65504) with a factor 2 to spare.
+    P.hs[j] = P.hsi[j] = 1.f;
+    if (storage == FDLBM_STORAGE_FP16) {
+      const double bound = 2.0 * M + species[j].X_inlet * M;
+      const int e = (int)std::floor(std::log2(32768.0 / bound));
+      P.hs[j] = (float)std::ldexp(1.0, e);
+      P.hsi[j] = (float)std::ldexp(1.0, -e);
+    }
+    h->X_init[j] = species[j].X_init;
+    h->X_inlet[j] = species[j].X_inlet;
+  }
+  P.storage = storage;
+  P.local_tau = tr->local_tau ? 1 : 0;
+  P.alpha_s = (float)tr->alpha_s;
+  P.rhocp_s = (float)tr->rhocp_s;
+  P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
+  P.kappa_f = (float)tr->kappa_f;
+  P.dTout = (float)(tr->T_outer_K * tl - Tref);
+  P.nr = kin->n_react;
+  for (int r = 0; r < kin->n_react; ++r) {
+    for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
+    P.rate_form[r] = kin->rate_form[r];
+    P.k0[r] = (float)kin->k0[r];
+    P.EaR[r] = (float)(kin->Ea_Jmol[r] / R_GAS);
+    P.inv_Keq[r] = kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE ? (float)(1.0 / kin->Keq[r]) : 0.f;
+    P.heat[r] = (float)(-kin->dH_Jmol[r] / (3.0 * R_GAS * tr->T0_K));
+  }
+  P.T3T0 = (float)(3.0 * tr->T0_K);
+  P.rho_w_tol = (float)kin->rho_w_tol;
+  P.rho_w_maxit = kin->rho_w_maxit;
+  if (kin->n_react > 0) {
+    h->heat0 = -kin->dH_Jmol[0] / (3.0 * R_GAS * tr->T0_K);
+    for (int j = 0; j < ns && h->eps_species < 0; ++j)
+      if (kin->nu[0][j] < 0) {
+        h->eps_species = j;
+        h->eps_nu = kin->nu[0][j];
+      }
+  }
+}
+
 fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f);
 fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, int ns, const fdlbm_transport* tr,
                      const fdlbm_kinetics* kin, const fdlbm_fields* init, const fdlbm_options* opts,
@@ -223,12 +327,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   if (storage != FDLBM_STORAGE_FP32 && storage != FDLBM_STORAGE_BF16 && storage != FDLBM_STORAGE_FP16)
     return fail(FDLBM_EINVAL, "unsupported storage %d", storage);
 
-  double Mmin = 1e300;
-  for (int j = 0; j < n_species; ++j) {
+  for (int j = 0; j < n_species; ++j)
     if (!(species[j].M_gmol > 0) || !(species[j].tau1 > 0) || !(species[j].tau2 > 0))
       return fail(FDLBM_EINVAL, "species %d: M, tau1, tau2 must be positive", j);
-    Mmin = std::min(Mmin, species[j].M_gmol);
-  }
   for (int r = 0; r < kin->n_react; ++r) {
     if (kin->rate_form[r] != FDLBM_RATE_CONC_BILINEAR && kin->rate_form[r] != FDLBM_RATE_XFRAC_REVERSIBLE)
       return fail(FDLBM_EINVAL, "reaction %d: unknown rate form", r);
@@ -364,9 +465,10 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.plane = ((long long)P.pitch * (ny + 2 * YOFF) + 63) / 64 * 64;
   // Kernels address populations with 32-bit element offsets.
   if ((long long)ns * Q * P.plane >= (1LL << 31)) {
+    const long long plane = P.plane;  // P refers into h
     delete h;
     return fail(FDLBM_EINVAL, "lattice too large: %d species x 9 x %lld padded cells exceed 2^31 elements",
-                ns, (long long)P.plane);
+                ns, plane);
   }
   std::vector<int2> gas_list;
   gas_list.reserve((size_t)h->counts[GAS]);
@@ -429,103 +531,13 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.periodic_y = G.py;
   P.n_solid_list = (int)solid_list.size();
   P.n_wall_list = (int)walls.size();
-  P.energy_correction = tr->energy_correction ? 1 : 0;
-  P.coupling = tr->coupling;
   for (int f = 0; f < 4; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
-  h->T0 = tr->T0_K;
-  const double tl = 1.0 / (3.0 * tr->T0_K);
-  const double Tref = tr->T_inlet_K * tl;
-  h->T_inlet_lat = Tref;
-  h->T_init_lat = tr->T_init_K * tl;
-  h->Ts_init_lat = tr->T_solid_init_K * tl;
-  P.Tref = (float)Tref;
-  P.p_out = (float)Tref;  // C_in T_in with C_in = 1
-  P.u_inlet = (float)tr->u_inlet;
-  P.Tin_lat = (float)Tref;
-  h->X_init.resize(ns);
-  h->X_inlet.resize(ns);
-  for (int j = 0; j < ns; ++j) {
-    const double M = species[j].M_gmol / Mmin;
-    const double c = 1.0 / std::sqrt(M);
-    const double t1 = species[j].tau1, t2 = species[j].tau2;
-    P.M[j] = (float)M;
-    P.invM[j] = (float)(1.0 / M);
-    P.sqrtM[j] = (float)std::sqrt(M);
-    P.c[j] = (float)c;
-    P.c2[j] = (float)(1.0 / M);
-    const double a = 1.0 - c;
-    P.a[j] = (float)a;
-    P.ha[j] = (float)(0.5 * a);
-    P.ha2[j] = (float)(0.5 * a * a);
-    P.onlattice[j] = (M == 1.0);
-    P.rref[j] = (float)(species[j].X_inlet * M);
-    P.Xin[j] = (float)species[j].X_inlet;
-    P.omega[j] = (float)(2.0 / (1.0 + 2.0 * t1));
-    P.t1t2[j] = (float)(t1 / t2);
-    P.wt1[j] = (float)(2.0 * t1 / (1.0 + 2.0 * t1));
-    P.a2[j] = (float)(1.0 / (2.0 * t2));
-    P.inv1a2[j] = (float)(1.0 / (1.0 + 1.0 / (2.0 * t2)));
-    P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
-    P.invtau2[j] = (float)(1.0 / t2);
-    // Energy-correction flux K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T, c_pj = 2 / M_j (2D).
-    P.kcoef0[j] = tr->energy_correction ? (float)(2.0 * (2.0 / M) / tr->Pr - 1.0 / M) : 0.f;
-    P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.0 / M) / tr->Pr - 1.0 / M) * t1) : 0.f;
-    // Locally updated relaxation times: Wilke's phi_jk (bracket squared, so phi_jj = 1)
-    // and 1 / D_jk.
-    P.mu_l[j] = (float)species[j].mu;
-    for (int q = 0; q < ns; ++q) {
-      const double Mq = species[q].M_gmol / Mmin;
-      if (tr->local_tau) {
-        const double b = 1.0 + std::sqrt(species[j].mu / species[q].mu) * std::pow(Mq / M, 0.25);
-        P.phi_w[j][q] = (float)(b * b / std::sqrt(8.0 * (1.0 + M / Mq)));
-        P.invD[j][q] = q == j ? 0.f : (float)(1.0 / species[j].D[q]);
-      }
-    }
-    // FP16 storage: deviations |g - rref W0| stay below 2 M_j + rref_j (a population never
-    // exceeds its species density, bounded by the molar mass at twice the inlet molar
-    // concentration); the largest power of two that maps that bound below 2^15 keeps
-    // them inside FP16's range (max 65504) with a factor 2 to spare.
-    P.hs[j] = P.hsi[j] = 1.f;
-    if (storage == FDLBM_STORAGE_FP16) {
-      const double bound = 2.0 * M + species[j].X_inlet * M;
-      const int e = (int)std::floor(std::log2(32768.0 / bound));
-      P.hs[j] = (float)std::ldexp(1.0, e);
-      P.hsi[j] = (float)std::ldexp(1.0, -e);
-    }
-    h->X_init[j] = species[j].X_init;
-    h->X_inlet[j] = species[j].X_inlet;
-  }
-  P.storage = storage;
-  P.local_tau = tr->local_tau ? 1 : 0;
+  set_physics_params(h, species, ns, tr, kin, storage, 2);
+  const double Tref = h->T_inlet_lat;
   for (int i = 0; i < Q; ++i) {
     const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
     const double wy = HEY[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
     P.W0[i] = (float)(wx * wy);
-  }
-  P.alpha_s = (float)tr->alpha_s;
-  P.rhocp_s = (float)tr->rhocp_s;
-  P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
-  P.kappa_f = (float)tr->kappa_f;
-  P.dTout = (float)(tr->T_outer_K * tl - Tref);
-  P.nr = kin->n_react;
-  for (int r = 0; r < kin->n_react; ++r) {
-    for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
-    P.rate_form[r] = kin->rate_form[r];
-    P.k0[r] = (float)kin->k0[r];
-    P.EaR[r] = (float)(kin->Ea_Jmol[r] / R_GAS);
-    P.inv_Keq[r] = kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE ? (float)(1.0 / kin->Keq[r]) : 0.f;
-    P.heat[r] = (float)(-kin->dH_Jmol[r] / (3.0 * R_GAS * tr->T0_K));
-  }
-  P.T3T0 = (float)(3.0 * tr->T0_K);
-  P.rho_w_tol = (float)kin->rho_w_tol;
-  P.rho_w_maxit = kin->rho_w_maxit;
-  if (kin->n_react > 0) {
-    h->heat0 = -kin->dH_Jmol[0] / (3.0 * R_GAS * tr->T0_K);
-    for (int j = 0; j < ns && h->eps_species < 0; ++j)
-      if (kin->nu[0][j] < 0) {
-        h->eps_species = j;
-        h->eps_nu = kin->nu[0][j];
-      }
   }
   // Inlet velocity per row: plug, or a parabola vanishing on the bounding wall nodes of
   // each contiguous inlet run.
@@ -809,8 +821,6 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
   if (tr->inlet_profile != FDLBM_PROFILE_PLUG) return fail(FDLBM_EINVAL, "D3Q19: plug inlet only");
   if (geom->wall_u) return fail(FDLBM_EINVAL, "D3Q19: moving walls are not implemented");
   const int storage = opts ? opts->storage : FDLBM_STORAGE_FP32;
-  double Mmin = 1e300;
-  for (int j = 0; j < ns; ++j) Mmin = std::min(Mmin, species[j].M_gmol);
 
   fdlbm_handle* h = new fdlbm_handle();
   h->device = opts ? opts->device : 0;
@@ -992,84 +1002,9 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
   P.periodic_z = G.pz;
   P.n_solid_list = (int)solid_list.size();
   P.n_wall_list = (int)walls.size();
-  P.energy_correction = tr->energy_correction ? 1 : 0;
-  P.coupling = tr->coupling;
   for (int f = 0; f < 6; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
-  h->T0 = tr->T0_K;
-  const double tl = 1.0 / (3.0 * tr->T0_K);
-  const double Tref = tr->T_inlet_K * tl;
-  h->T_inlet_lat = Tref;
-  h->T_init_lat = tr->T_init_K * tl;
-  h->Ts_init_lat = tr->T_solid_init_K * tl;
-  P.Tref = (float)Tref;
-  P.p_out = (float)Tref;
-  P.u_inlet = (float)tr->u_inlet;
-  P.Tin_lat = (float)Tref;
-  h->X_init.resize(ns);
-  h->X_inlet.resize(ns);
-  for (int j = 0; j < ns; ++j) {
-    const double M = species[j].M_gmol / Mmin;
-    const double c = 1.0 / std::sqrt(M);
-    const double t1 = species[j].tau1, t2 = species[j].tau2;
-    P.M[j] = (float)M;
-    P.invM[j] = (float)(1.0 / M);
-    P.sqrtM[j] = (float)std::sqrt(M);
-    P.c[j] = (float)c;
-    P.c2[j] = (float)(1.0 / M);
-    const double a = 1.0 - c;
-    P.a[j] = (float)a;
-    P.ha[j] = (float)(0.5 * a);
-    P.ha2[j] = (float)(0.5 * a * a);
-    P.onlattice[j] = (M == 1.0);
-    P.rref[j] = (float)(species[j].X_inlet * M);
-    P.Xin[j] = (float)species[j].X_inlet;
-    P.omega[j] = (float)(2.0 / (1.0 + 2.0 * t1));
-    P.t1t2[j] = (float)(t1 / t2);
-    P.wt1[j] = (float)(2.0 * t1 / (1.0 + 2.0 * t1));
-    P.a2[j] = (float)(1.0 / (2.0 * t2));
-    P.inv1a2[j] = (float)(1.0 / (1.0 + 1.0 / (2.0 * t2)));
-    P.uc_w[j] = (float)(1.0 / (t2 + 0.5));
-    P.invtau2[j] = (float)(1.0 / t2);
-    // Energy-correction flux K_j = (2 c_pj / Pr - 2 / M_j) tau1_j C_j T, c_pj = 5 / (2 M_j) (3D).
-    P.kcoef[j] = tr->energy_correction ? (float)((2.0 * (2.5 / M) / tr->Pr - 2.0 / M) * t1) : 0.f;
-    // FP16 storage: the same power-of-two scale as for D2Q9 (deviations below 2 M_j + rref_j).
-    P.hs[j] = P.hsi[j] = 1.f;
-    if (storage == FDLBM_STORAGE_FP16) {
-      const double bound = 2.0 * M + species[j].X_inlet * M;
-      const int e = (int)std::floor(std::log2(32768.0 / bound));
-      P.hs[j] = (float)std::ldexp(1.0, e);
-      P.hsi[j] = (float)std::ldexp(1.0, -e);
-    }
-    h->X_init[j] = species[j].X_init;
-    h->X_inlet[j] = species[j].X_inlet;
-  }
-  P.storage = storage;
-  for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, Tref);
-  P.alpha_s = (float)tr->alpha_s;
-  P.rhocp_s = (float)tr->rhocp_s;
-  P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
-  P.kappa_f = (float)tr->kappa_f;
-  P.dTout = (float)(tr->T_outer_K * tl - Tref);
-  P.nr = kin->n_react;
-  for (int r = 0; r < kin->n_react; ++r) {
-    for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
-    P.rate_form[r] = kin->rate_form[r];
-    P.k0[r] = (float)kin->k0[r];
-    P.EaR[r] = (float)(kin->Ea_Jmol[r] / R_GAS);
-    P.inv_Keq[r] = kin->rate_form[r] == FDLBM_RATE_XFRAC_REVERSIBLE ? (float)(1.0 / kin->Keq[r]) : 0.f;
-    P.heat[r] = (float)(-kin->dH_Jmol[r] / (3.0 * R_GAS * tr->T0_K));
-  }
-  P.T3T0 = (float)(3.0 * tr->T0_K);
-  P.rho_w_tol = (float)kin->rho_w_tol;
-  P.rho_w_maxit = kin->rho_w_maxit;
-  if (kin->n_react > 0) {
-    h->heat0 = -kin->dH_Jmol[0] / (3.0 * R_GAS * tr->T0_K);
-    for (int j = 0; j < ns && h->eps_species < 0; ++j)
-      if (kin->nu[0][j] < 0) {
-        h->eps_species = j;
-        h->eps_nu = kin->nu[0][j];
-      }
-  }
+  set_physics_params(h, species, ns, tr, kin, storage, 3);
+  for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, h->T_inlet_lat);
 
   // Device state.
   fdlbm_status st;
