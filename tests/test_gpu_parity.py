@@ -246,3 +246,63 @@ def test_short_periodic_axis_rejected():
     assert ei.value.status == -1
     with pytest.raises(fdlbm.FdlbmError):
         fdlbm.Solver(W.periodic_box3(12, 12, 5, reactions=[]))
+
+
+# ---------------------------------------------------------------------------------------
+# Species counts other than 5 (each is its own kernel instantiation) and degenerate
+# lattices
+# ---------------------------------------------------------------------------------------
+
+def _species_subset(p, ns):
+    """A subset of the five-species table that keeps H2 (the lightest species, whose
+    relaxation time sets the stable range of the energy-correction flux once its molar
+    mass is the unit), or the five plus argon for ns = 6, with the mole fractions
+    renormalised; reactions only for the full table (their stoichiometry spans all of
+    CO, H2O, CO2 and H2)."""
+    pick = {1: [3], 2: [0, 3], 3: [0, 1, 3], 5: [0, 1, 2, 3, 4], 6: [0, 1, 2, 3, 4]}[ns]
+    sp = [dict(p["species"][k]) for k in pick]
+    if ns == 6:
+        sp.append({"name": "Ar", "M_gmol": 39.948, "tau1": 0.85, "tau2": 0.8, "X_init": 0.05, "X_inlet": 0.05})
+    for key in ("X_init", "X_inlet"):
+        tot = sum(s[key] for s in sp)
+        for s in sp:
+            s[key] = s[key] / tot
+    p["species"] = sp
+    if ns < 5:
+        p["reactions"] = []
+    else:
+        for r in p["reactions"]:
+            r["nu"] = (list(r["nu"]) + [0] * 6)[:ns]
+    return p
+
+
+@pytest.mark.parametrize("ns", [1, 2, 3, 6])
+def test_parity_species_counts(ns):
+    """2, 3 and 6 species: periodic box over a catalytic FD-solid slab. 1 species (pure
+    H2): a channel between FD-solid walls, driven by its inlet (in a closed periodic box
+    the single gas's random velocity decays 30-fold in 120 steps, to where the
+    field-normalised error measures FP32 rounding of a vanishing field). It takes
+    Pr = 2.5: the energy-correction coefficient K/C = ((D + 2)/Pr - (D - 1)) tau1 T of
+    unit-mass H2 is about 0.94 at Pr = 0.7 and T = 1/3, past the explicit limit of the
+    lagged flux; in the mixtures H2 is a small part of the heat capacity."""
+    if ns == 1:
+        p = _species_subset(W.channel(96, n_gas=20, wall=6, Pr=2.5), ns)
+    else:
+        p = _species_subset(W.periodic_box(36, 20, solid_rows=5), ns)
+    p["init"] = W.random_fields(p, seed=80 + ns)
+    s, o = run_both(p, 120)
+    assert_parity(s, o, what=f"{ns} species", vector_u=True)
+    s.close()
+
+
+def test_all_solid_lattice():
+    """A lattice without gas nodes: the FD heat step alone (fixed-T faces), against the
+    oracle's solid temperature."""
+    p = W._base(2, 24, 16, 1, np.full((16, 24), W.INERT, np.uint8),
+                [W.PERIODIC, W.PERIODIC, W.FIXED_T, W.FIXED_T], reactions=[], T_outer_K=480.0)
+    p["init"] = {"Ts_K": 500.0 + 5.0 * W.smooth_noise((16, 24), np.random.default_rng(9)).reshape(-1)}
+    s, o = run_both(p, 200)
+    ts_g = s.moments_host()[-1].astype(np.float64)
+    ts_o = o.moments()[-1]
+    assert np.abs(ts_g - ts_o).max() <= 1e-5 * np.abs(ts_o - 480.0).max()
+    s.close()

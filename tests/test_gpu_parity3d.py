@@ -179,3 +179,14 @@ def test_3d_rejects_unsupported():
                 u_inlet=0.01, inlet_profile=W.PARABOLIC)
     with pytest.raises(fdlbm.FdlbmError):
         fdlbm.Solver(q)
+
+
+@pytest.mark.parametrize("ns", [2, 6])
+def test_parity3_species_counts(ns):
+    """D3Q19 periodic box over a catalytic slab with 2 and 6 species."""
+    from test_gpu_parity import _species_subset
+    p = _species_subset(W.periodic_box3(14, 10, 12, solid_layers=3), ns)
+    p["init"] = W.random_fields(p, seed=90 + ns)
+    s, o = run_both3(p, 80)
+    check(s, o, what=f"3D {ns} species")
+    s.close()
