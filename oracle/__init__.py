@@ -24,6 +24,8 @@ Q = 9
 # Ledger indices (mirror the enum in fdlbm_oracle.h)
 B_STEPS, B_E_GAS, B_E_GAS0, B_H_SOLID, B_H_SOLID0, B_Q_RXN, B_Q_WALL, B_Q_COUPLE, \
     B_Q_FIXEDT, B_RESIDUAL, B_SOLID_RESIDUAL, B_EPS_PAPER, B_NOCONV, B_MASS = range(14)
+A_E_POP, A_E_POP0, A_Q_INLET, A_Q_OUTLET, A_D_INTERP, A_D_COLLISION, A_D_COUPLING, A_CLOSURE, \
+    A_MASS = range(9)
 
 
 def build(force: bool = False, openmp: bool = False) -> str:
@@ -110,6 +112,7 @@ def lib():
         L.ora_moments.argtypes = [C.c_void_p, dp]
         L.ora_populations.argtypes = [C.c_void_p, dp]
         L.ora_balance.argtypes = [C.c_void_p, dp]
+        L.ora_accounts.argtypes = [C.c_void_p, dp]
         L.ora_residual.argtypes = [C.c_void_p, C.c_int]
         L.ora_residual.restype = C.c_double
         L.ora_counts.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
@@ -246,6 +249,23 @@ class Oracle:
             "moles": out[B_MASS + 2 * ns:B_MASS + 3 * ns].copy(),
             "moles0": out[B_MASS + 3 * ns:B_MASS + 4 * ns].copy(),
         }
+
+    def accounts(self) -> dict:
+        """Exact accounts of the scheme: inventory of the stored populations, shift-sense
+        inlet/outlet fluxes, interpolation/collision/coupling defects and the energy
+        closure; per-species mass arrays of the same form (the header's ORA_A_* layout)."""
+        ns = self.ns
+        out = np.zeros(A_MASS + 8 * ns)
+        lib().ora_accounts(self._h, _dptr(out))
+        m = out[A_MASS:].reshape(8, ns)
+        d = {"E_pop": out[A_E_POP], "E_pop0": out[A_E_POP0], "Q_inlet": out[A_Q_INLET],
+             "Q_outlet": out[A_Q_OUTLET], "D_interp": out[A_D_INTERP],
+             "D_collision": out[A_D_COLLISION], "D_coupling": out[A_D_COUPLING],
+             "closure": out[A_CLOSURE]}
+        for r, name in enumerate(("M_pop", "M_pop0", "M_inlet", "M_outlet", "Dm_interp",
+                                  "Dm_collision", "M_rxn", "mass_closure")):
+            d[name] = m[r].copy()
+        return d
 
     def residual(self, K: int) -> float:
         return lib().ora_residual(self._h, int(K))

@@ -72,6 +72,12 @@ struct ora_state {
   double steps;
   double E_gas0, H_solid0, mass0[ORA_MAX_NS], moles0[ORA_MAX_NS];
   double Q_rxn, Q_wall, Q_couple, Q_fixedT, noconv;
+  /* Exact accounts (ora_accounts): inventory of the stored populations at the start,
+   * shift-sense inlet/outlet fluxes, interpolation and collision defects (energy and
+   * per-species mass) and the mass the reactions produce at the walls. */
+  double E_pop0, Q_in, Q_out, D_int, D_col;
+  double Mpop0[ORA_MAX_NS], M_in[ORA_MAX_NS], M_out[ORA_MAX_NS], Dm_int[ORA_MAX_NS], Dm_col[ORA_MAX_NS],
+      M_rxn[ORA_MAX_NS];
   long st_count[6];
 };
 
@@ -177,6 +183,17 @@ static double pull(ora_state* s, const double* gsrc, int j, int i, int x, int y,
   if (code == ST_BACKWARD) s3 = gsrc[PIDX(s, j, i, node_at(s, x - 3 * EX[i], y - 3 * EY[i]))];
   if (code == ST_FORWARD) sp = gsrc[PIDX(s, j, i, node_at(s, x + EX[i], y + EY[i]))];
   return ora_interp(code, s->c[j], s3, s2, s1, s0, sp);
+}
+
+/* The pure-shift value of a pull: population (j, i) of the node x - e_i (the node
+ * itself for the rest population). */
+static double shift_source(const ora_state* s, const double* gsrc, int j, int i, int x, int y) {
+  return gsrc[PIDX(s, j, i, node_at(s, x - EX[i], y - EY[i]))];
+}
+
+/* Energy weight of population (j, i): (1/2) c_j^2 |e_i|^2. */
+static double eps_w(const ora_state* s, int j, int i) {
+  return 0.5 * s->c[j] * s->c[j] * (double)(EX[i] * EX[i] + EY[i] * EY[i]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -451,6 +468,7 @@ static void fill_moments_from_fields(ora_state* s, int k, const double* X, doubl
 }
 
 static void ledger_totals(const ora_state* s, double* E, double* H, double* mass, double* moles);
+static void pop_totals(const ora_state* s, double* E, double* mass);
 
 ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
   if (p->nx < 1 || p->ny < 1 || p->ns < 1 || p->ns > ORA_MAX_NS || p->nr < 0 || p->nr > ORA_MAX_NR) {
@@ -607,6 +625,7 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
     s->mass0[j] = mass[j];
     s->moles0[j] = moles[j];
   }
+  pop_totals(s, &s->E_pop0, s->Mpop0);
   return s;
 }
 
@@ -675,6 +694,9 @@ static void wall_pass(ora_state* s) {
         for (int i = 1; i < Q; ++i)
           if (arr[i]) {
             double v = pull(s, s->g, j, i, x, y, 1);
+            double d = v - shift_source(s, s->g, j, i, x, y);
+            s->D_int += eps_w(s, j, i) * d;
+            s->Dm_int[j] += d;
             A[j] += v;
             Earr += 0.5 * s->c[j] * s->c[j] * (EX[i] * EX[i] + EY[i] * EY[i]) * v;
           }
@@ -707,6 +729,7 @@ static void wall_pass(ora_state* s) {
       for (int j = 0; j < ns; ++j) {
         m[j] = 0.0;
         for (int r = 0; r < s->p.nr && catalytic; ++r) m[j] += s->M[j] * s->p.nu[r][j] * rate[r];
+        s->M_rxn[j] += m[j];
         for (int i = 1; i < Q; ++i)
           if (out[i]) {
             double w = fw[j][i] * (A[j] + m[j]) / B[j]; /* Eq. BC_gji, count form */
@@ -737,6 +760,19 @@ static void gas_pass(ora_state* s) {
           double v = pull(s, s->g, j, i, x, y, 1);
           s->gp[PIDX(s, j, i, k)] = v;
           gl[j * Q + i] = v;
+          if (i == 0) continue;
+          /* accounts: the pull's departure from the pure shift, and the populations that
+           * cross the inlet and outlet faces (taken from inlet/outlet nodes as s1, or
+           * lost by this node into them) */
+          double s1 = shift_source(s, s->g, j, i, x, y), e = eps_w(s, j, i);
+          s->D_int += e * (v - s1);
+          s->Dm_int[j] += v - s1;
+          int cu = cls_at(s, x - EX[i], y - EY[i]), cd = cls_at(s, x + EX[i], y + EY[i]);
+          double own = s->g[PIDX(s, j, i, k)];
+          if (cu == CL_INLET) { s->Q_in += e * s1; s->M_in[j] += s1; }
+          if (cu == CL_OUTLET) { s->Q_out += e * s1; s->M_out[j] += s1; }
+          if (cd == CL_INLET) { s->Q_in -= e * own; s->M_in[j] -= own; }
+          if (cd == CL_OUTLET) { s->Q_out -= e * own; s->M_out[j] -= own; }
         }
       s->Tg[k] = g_temperature(ns, s->M, gl, Cj);
       for (int j = 0; j < ns; ++j) s->Cj[(size_t)j * n + k] = Cj[j];
@@ -801,7 +837,11 @@ static void gas_pass(ora_state* s) {
     for (int j = 0; j < ns; ++j) s->tau1_prev[(size_t)j * n + k] = t1[j];
     ora_collide(ns, s->M, t1, t2, gl, dq, go, mom);
     for (int j = 0; j < ns; ++j)
-      for (int i = 0; i < Q; ++i) s->gn[PIDX(s, j, i, k)] = go[j * Q + i];
+      for (int i = 0; i < Q; ++i) {
+        s->gn[PIDX(s, j, i, k)] = go[j * Q + i];
+        s->D_col += eps_w(s, j, i) * (go[j * Q + i] - gl[j * Q + i]);
+        s->Dm_col[j] += go[j * Q + i] - gl[j * Q + i];
+      }
     for (int j = 0; j < ns; ++j) s->rho[(size_t)j * n + k] = mom[j];
     s->ux[k] = mom[ns];
     s->uy[k] = mom[ns + 1];
@@ -1066,3 +1106,62 @@ void ora_counts(const ora_state* s, long* out) {
 }
 
 void ora_classes(const ora_state* s, int* out) { memcpy(out, s->cls, sizeof(int) * (size_t)s->n); }
+
+/* Inventory of the stored populations: energy sum (1/2) c_j^2 |e_i|^2 g and mass sum g
+ * over the post-collision populations of gas nodes and the wall emissions in transit
+ * (inlet and outlet nodes are outside the gas). */
+static void pop_totals(const ora_state* s, double* E, double* mass) {
+  int ns = s->ns;
+  double e = 0.0;
+  for (int j = 0; j < ns; ++j) mass[j] = 0.0;
+  for (int y = 0; y < s->ny; ++y)
+    for (int x = 0; x < s->nx; ++x) {
+      int k = x + s->nx * y;
+      if (s->cls[k] != CL_GAS && s->cls[k] != CL_WALL) continue;
+      for (int j = 0; j < ns; ++j)
+        for (int i = 0; i < Q; ++i) {
+          if (s->cls[k] == CL_WALL && (i == 0 || cls_at(s, x + EX[i], y + EY[i]) != CL_GAS)) continue;
+          double g = s->g[PIDX(s, j, i, k)];
+          e += eps_w(s, j, i) * g;
+          mass[j] += g;
+        }
+    }
+  *E = e;
+}
+
+/* Exact accounts of the scheme (layout in the header). One step moves the stored
+ * inventory by what the pulls take from inlet/outlet nodes minus what gas nodes stream
+ * into them (Q_inlet, Q_outlet), by the departure of every interpolated pull from the
+ * pure shift (D_interp: gas pulls and wall arrivals), by the collision's change
+ * (D_collision) and by what the walls emit minus what they receive (Q_wall for energy,
+ * the reaction production for mass). With the solid's identity, the energy closure
+ * dE_pop + dH_solid - Q_rxn - Q_fixedT - Q_inlet - Q_outlet - D_interp - D_collision -
+ * D_coupling vanishes to rounding, D_coupling = Q_wall + Q_couple being zero for the
+ * conservative coupling. */
+void ora_accounts(const ora_state* s, double* out) {
+  int ns = s->ns;
+  double E, H, mass[ORA_MAX_NS], moles[ORA_MAX_NS], Ep, Mp[ORA_MAX_NS];
+  ledger_totals(s, &E, &H, mass, moles);
+  pop_totals(s, &Ep, Mp);
+  double Dcpl = s->Q_wall + s->Q_couple;
+  out[ORA_A_E_POP] = Ep;
+  out[ORA_A_E_POP0] = s->E_pop0;
+  out[ORA_A_Q_INLET] = s->Q_in;
+  out[ORA_A_Q_OUTLET] = s->Q_out;
+  out[ORA_A_D_INTERP] = s->D_int;
+  out[ORA_A_D_COLLISION] = s->D_col;
+  out[ORA_A_D_COUPLING] = Dcpl;
+  out[ORA_A_CLOSURE] = (Ep - s->E_pop0) + (H - s->H_solid0) - s->Q_rxn - s->Q_fixedT - s->Q_in - s->Q_out -
+                       s->D_int - s->D_col - Dcpl;
+  for (int j = 0; j < ns; ++j) {
+    double* m = out + ORA_A_MASS;
+    m[j] = Mp[j];
+    m[ns + j] = s->Mpop0[j];
+    m[2 * ns + j] = s->M_in[j];
+    m[3 * ns + j] = s->M_out[j];
+    m[4 * ns + j] = s->Dm_int[j];
+    m[5 * ns + j] = s->Dm_col[j];
+    m[6 * ns + j] = s->M_rxn[j];
+    m[7 * ns + j] = (Mp[j] - s->Mpop0[j]) - s->M_in[j] - s->M_out[j] - s->Dm_int[j] - s->Dm_col[j] - s->M_rxn[j];
+  }
+}

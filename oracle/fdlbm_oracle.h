@@ -62,6 +62,17 @@ enum {
   ORA_B_EPS_PAPER, ORA_B_NOCONV, ORA_B_MASS /* then mass[ns], mass0[ns], moles[ns], moles0[ns] */
 };
 
+/* Exact accounts returned by ora_accounts: the inventory of the stored populations (gas
+ * post-collision populations and wall emissions in transit) now and at the start, the
+ * shift-sense inlet and outlet fluxes, the interpolation, collision and coupling
+ * defects and the energy closure; then per species (ns each) the mass inventory now
+ * and at the start, inlet and outlet mass fluxes, interpolation and collision mass
+ * defects, reaction production at the walls and the mass closure. */
+enum {
+  ORA_A_E_POP = 0, ORA_A_E_POP0, ORA_A_Q_INLET, ORA_A_Q_OUTLET, ORA_A_D_INTERP, ORA_A_D_COLLISION,
+  ORA_A_D_COUPLING, ORA_A_CLOSURE, ORA_A_MASS /* then 8 blocks of ns */
+};
+
 ora_state* ora_create(const ora_problem* p, char* err, int errlen);
 void ora_destroy(ora_state* s);
 int ora_step(ora_state* s, int nsteps);
@@ -69,6 +80,8 @@ int ora_nfields(const ora_state* s);                 /* 2*ns + 4 */
 void ora_moments(const ora_state* s, double* out);   /* [field][n]: rho_j, X_j, ux, uy, T_K, Ts_K */
 void ora_populations(const ora_state* s, double* out); /* [ns][9][n] stored post-collision / wall-emitted */
 void ora_balance(const ora_state* s, double* out);
+/* Exact accounts (energy, then per-species mass; layout ORA_A_*). */
+void ora_accounts(const ora_state* s, double* out);
 double ora_residual(ora_state* s, int K);
 void ora_counts(const ora_state* s, long* out);      /* class counts [5] + stencil counts [6] */
 void ora_classes(const ora_state* s, int* out);      /* per-node class */

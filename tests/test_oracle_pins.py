@@ -607,3 +607,95 @@ def test_enthalpy_coupling_error_paper_box(tau, ec):
     b = o.balance()
     assert b["Q_reaction"] > 0
     assert abs(b["eps_paper"]) < 1e-5, b["eps_paper"]
+
+
+# ---------------------------------------------------------------------------------------
+# Exact accounts: inventory of the stored populations, face fluxes and scheme defects
+# ---------------------------------------------------------------------------------------
+
+def test_accounts_uniform_inlet_flux_closed_form():
+    """Uniform inlet state in an open periodic-y channel, one step. Every face flux is a
+    moment of the product-form equilibrium (Eq. eq_state_pop): per inlet row the pulls
+    take sum_{e_x = 1} f from the inlet and the first gas column loses sum_{e_x = -1} f
+    into it, net sum e_x f = rho_j sqrt(M_j) u; the energy flux sum (1/2) c_j^2 |e|^2 e_x f
+    = (1/2) rho_j u (1 + T) / sqrt(M_j) (c_j^2 = 1/M_j). The outlet carries the
+    negatives. Uniform data make every interpolation exact (no defect) and the collision
+    an identity."""
+    nx, ny, u = 24, 8, 0.02
+    p = W._base(2, nx, ny, 1, np.zeros((ny, nx), np.uint8), [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC],
+                u_inlet=u, inlet_profile=W.PLUG, reactions=[])
+    n = nx * ny
+    X = np.array([s["X_inlet"] for s in p["species"]])
+    p["init"] = {"X": np.repeat(X[:, None], n, axis=1), "u": np.vstack([np.full(n, u), np.zeros(n)]),
+                 "T_K": np.full(n, p["T_inlet_K"]), "Ts_K": np.full(n, p["T_inlet_K"])}
+    o = oracle.Oracle(p)
+    o.step(1)
+    a = o.accounts()
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    rho = X * M  # C = 1 at the inlet state
+    T = p["T_inlet_K"] / (3.0 * p["T0_K"])
+    m_in = ny * rho * np.sqrt(M) * u
+    q_in = ny * np.sum(0.5 * rho * u * (1.0 + T) / np.sqrt(M))
+    np.testing.assert_allclose(a["M_inlet"], m_in, rtol=1e-12)
+    np.testing.assert_allclose(a["M_outlet"], -m_in, rtol=1e-12)
+    assert abs(a["Q_inlet"] - q_in) <= 1e-12 * q_in
+    assert abs(a["Q_outlet"] + q_in) <= 1e-12 * q_in
+    scale = abs(a["E_pop"])
+    assert abs(a["D_interp"]) <= 1e-14 * scale and abs(a["D_collision"]) <= 1e-14 * scale
+    np.testing.assert_allclose(a["M_pop"] - a["M_pop0"], 0.0, atol=1e-13 * a["M_pop"].sum())
+
+
+def _accounts_case(name):
+    if name == "closed_reactive_box":
+        p = W.periodic_box(36, 20, solid_rows=5)
+        p["init"] = W.random_fields(p, seed=3)
+        return p, 60
+    if name == "open_channel":
+        return W.channel(nx=64, n_gas=16, wall=4), 200
+    if name == "open_channel_paper_coupling":
+        return W.channel(nx=64, n_gas=16, wall=4, coupling=W.PAPER), 200
+    if name == "local_tau_channel":
+        return W.local_transport(W.channel(nx=48, n_gas=12, wall=4)), 120
+    if name == "couette_moving_wall":
+        return W.couette(n_gas=16, U_w=0.03, dT_K=2.0, nx=8), 150
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["closed_reactive_box", "open_channel", "open_channel_paper_coupling",
+                                  "local_tau_channel", "couette_moving_wall"])
+def test_accounts_close_exactly(name):
+    """Every step moves the inventory of stored populations by the face fluxes, the
+    interpolation and collision defects and what the walls emit minus what they receive;
+    the solid changes by the reaction heat, the coupling and the fixed-T faces (Sec. 5).
+    Summed, energy closes to rounding in every mode (D_coupling = Q_wall + Q_couple is
+    zero for the conservative coupling, and carries the paper law's imbalance), and each
+    species' mass closes with the walls' reaction production as its source. A term
+    dropped or streamed from the wrong node breaks the sums."""
+    p, steps = _accounts_case(name)
+    o = oracle.Oracle(p)
+    o.step(steps)
+    a, b = o.accounts(), o.balance()
+    scale = abs(a["E_pop"]) + abs(b["H_solid"])
+    assert abs(a["closure"]) <= 1e-12 * scale, a
+    assert np.abs(a["mass_closure"]).max() <= 1e-12 * a["M_pop"].sum(), a["mass_closure"]
+    if name == "open_channel_paper_coupling":
+        assert abs(a["D_coupling"]) > 1e-6 * abs(a["Q_inlet"])
+    else:
+        assert abs(a["D_coupling"]) <= 1e-12 * scale
+    if name.startswith("open") or name == "local_tau_channel":
+        assert a["Q_inlet"] > 0.0 and a["Q_outlet"] < 0.0
+    # the walls' reaction production conserves mass over the species
+    assert abs(a["M_rxn"].sum()) <= 1e-12 * max(np.abs(a["M_rxn"]).max(), 1e-300)
+
+
+def test_accounts_on_lattice_species_have_no_interpolation_defect():
+    """With equal molar masses every species streams on-lattice (c_j = 1, Sec. 4.2): each
+    pull is the pure shift, at gas nodes and at wall arrivals alike."""
+    p = _unit_mass(W.channel(nx=48, n_gas=12, wall=4))
+    o = oracle.Oracle(p)
+    o.step(100)
+    a = o.accounts()
+    assert a["D_interp"] == 0.0
+    assert np.all(a["Dm_interp"] == 0.0)
+    assert abs(a["closure"]) <= 1e-12 * abs(a["E_pop"])
