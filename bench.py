@@ -81,7 +81,7 @@ def measured_peaks():
 def kernel_source_hash(three_d=False):
     """Hash of the sources of the step kernel of the D2Q9 (or D3Q19) path."""
     h = hashlib.sha256()
-    files = ("fdlbm_device.cuh", "fdlbm3d_kernels.cu", "fdlbm_internal.h") if three_d else \
+    files = ("fdlbm_device.cuh", "fdlbm3d_device.cuh", "fdlbm3d_kernels.cu", "fdlbm_internal.h") if three_d else \
         ("fdlbm_device.cuh", "fdlbm_kernels.cu", "fdlbm_internal.h")
     for f in files:
         with open(os.path.join(ROOT, "paper_1804_07588_gb300", "csrc", f), "rb") as fh:

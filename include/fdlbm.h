@@ -165,6 +165,9 @@ typedef struct {
   void* alloc_ctx;
   int band_rows;           /* rows per band of the step kernel's block order (gas blocks of a
                               band, then its wall blocks); 0: 8 */
+  int ledger_detail;       /* 1: every step also keeps the exact accounts of fdlbm_balance
+                              (E_pop ... closure); D2Q9, FP32 storage, constant relaxation
+                              times only (else EINVAL); slower steps, same results */
 } fdlbm_options;
 
 /* Counts and derived constants of a handle. */
@@ -195,6 +198,27 @@ typedef struct {
   double noconv;           /* wall-density iterations that hit the cap */
   double mass[FDLBM_MAX_SPECIES], mass0[FDLBM_MAX_SPECIES];
   double moles[FDLBM_MAX_SPECIES], moles0[FDLBM_MAX_SPECIES];
+  /* Exact accounts (handles created with ledger_detail; otherwise zero, closure NaN).
+   * Inventory: energy (1/2) c_j^2 |e_i|^2 g of the stored populations of gas nodes and
+   * of the wall emissions in transit. Per step, FP64 sums of exact differences of the
+   * FP32 values stored and pulled:
+   *   Q_inlet, Q_outlet: energy gas nodes pull from inlet / outlet nodes as their shift
+   *     source (s1) minus the energy of their populations that stream into them;
+   *   D_interp: departure of each interpolated pull from the pure shift (Sec. 4.2), at
+   *     gas nodes and wall arrivals (zero for species with c_j = 1);
+   *   D_collision: energy change of the collision (Eq. final_kinetic_equation);
+   *   D_coupling: energy the walls put into the gas (stored emissions minus pulled
+   *     arrivals) plus Q_couple: zero up to the FP32 rounding of the exchange the solid
+   *     receives in the conservative coupling, the imbalance of Eq. wall_temperature in
+   *     the paper's;
+   *   D_solid: change of H_solid from the stored temperatures minus Q_reaction +
+   *     Q_couple + Q_fixedT (the FP32 rounding of the FD step).
+   * closure = (E_pop - E_pop0) + (H_solid - H_solid0) - Q_reaction - Q_fixedT - Q_inlet -
+   *   Q_outlet - D_interp - D_collision - D_coupling - D_solid: FP64 rounding. */
+  double E_pop, E_pop0;
+  double Q_inlet, Q_outlet, D_interp, D_collision, D_coupling, D_solid;
+  double closure;
+  int ledger_detail;
 } fdlbm_balance;
 
 /* Build a solver: validate, convert units, classify nodes (gas / inlet / outlet /

@@ -623,17 +623,17 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
 }
 
 __device__ __forceinline__ void ledger_store3(double (&acc)[LG_COUNT], double* __restrict__ slot) {
-  __shared__ double sh[LG_COUNT][G3 / 32];
+  __shared__ double sh[LG_BASIC][G3 / 32];
 #pragma unroll
-  for (int q = 0; q < LG_COUNT; ++q)
+  for (int q = 0; q < LG_BASIC; ++q)
     if (__any_sync(0xffffffffu, acc[q] != 0.0))
       for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < LG_COUNT; ++q) sh[q][warp] = acc[q];
+    for (int q = 0; q < LG_BASIC; ++q) sh[q][warp] = acc[q];
   __syncthreads();
-  if (threadIdx.x < LG_COUNT) {
+  if (threadIdx.x < LG_BASIC) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
     if (v != 0.0) slot[threadIdx.x] += v;

@@ -70,6 +70,7 @@ struct fdlbm_handle {
   double heat0 = 0;           // -dH / (3 R T0) of reaction 0
   int eps_species = -1, eps_nu = 0;
   double E0 = 0, H0 = 0, mass0[MAX_NS] = {}, moles0[MAX_NS] = {};
+  double E_pop0 = 0;          // energy of the stored populations at the start (exact accounts)
   int64_t counts[5] = {};
   std::vector<int4> blocks_host;  // step-kernel block descriptors (for batches)
   int64_t stencil_counts[6] = {};
@@ -349,6 +350,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
         if (k != j && !(species[j].D[k] > 0)) return fail(FDLBM_EINVAL, "species %d: D[%d] must be positive", j, k);
     }
   }
+  if (opts && opts->ledger_detail &&
+      (geom->lattice != FDLBM_D2Q9 || storage != FDLBM_STORAGE_FP32 || tr->local_tau))
+    return fail(FDLBM_EINVAL, "exact accounts need D2Q9, FP32 storage and constant relaxation times");
   if (geom->lattice == FDLBM_D3Q19) return create3(geom, species, n_species, tr, kin, init, opts, out);
 
   fdlbm_handle* h = new fdlbm_handle();
@@ -533,6 +537,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   P.n_wall_list = (int)walls.size();
   for (int f = 0; f < 4; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
   set_physics_params(h, species, ns, tr, kin, storage, 2);
+  P.ledger_detail = (opts && opts->ledger_detail) ? 1 : 0;
   const double Tref = h->T_inlet_lat;
   for (int i = 0; i < Q; ++i) {
     const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
@@ -681,6 +686,15 @@ fdlbm_status read_totals(fdlbm_handle* h, double* tot) {
   return FDLBM_OK;
 }
 
+// Energy of the stored populations (exact accounts), into *out.
+fdlbm_status read_pop_energy(fdlbm_handle* h, double* out) {
+  double* slot = h->S.red + totals_count(h->ns) + residual_count3(h->ns) + LG_COUNT;
+  CK(launch_pop_energy(h->P, h->S, h->cur, slot, h->stream), "population energy");
+  CK(cudaMemcpyAsync(out, slot, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read population energy");
+  CK(cudaStreamSynchronize(h->stream), "stream sync");
+  return FDLBM_OK;
+}
+
 fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f);
 
 fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
@@ -744,6 +758,11 @@ fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
   for (int j = 0; j < ns; ++j) {
     h->mass0[j] = tot[2 + j];
     h->moles0[j] = tot[2 + ns + j];
+  }
+  h->E_pop0 = 0.0;
+  if (h->P.ledger_detail) {
+    st = read_pop_energy(h, &h->E_pop0);
+    if (st != FDLBM_OK) return st;
   }
   return FDLBM_OK;
 }
@@ -1207,6 +1226,23 @@ fdlbm_status fdlbm_enthalpy_balance(fdlbm_handle* h, fdlbm_balance* out) {
     const double Qco = h->heat0 * (tot[2 + ns + jr] - h->moles0[jr]) / h->eps_nu;
     if (Qco != 0.0) out->eps_paper = ((tot[0] - h->E0) + (tot[1] - h->H0) - Qco) / Qco;
   }
+  out->closure = std::nan("");
+  if (h->P.ledger_detail) {
+    double Ep = 0.0;
+    st = read_pop_energy(h, &Ep);
+    if (st != FDLBM_OK) return st;
+    out->ledger_detail = 1;
+    out->E_pop = Ep;
+    out->E_pop0 = h->E_pop0;
+    out->Q_inlet = lg[LG_QIN];
+    out->Q_outlet = lg[LG_QOUT];
+    out->D_interp = lg[LG_DINT];
+    out->D_collision = lg[LG_DCOL];
+    out->D_coupling = lg[LG_QWALLX] + lg[LG_QCOUPLE];
+    out->D_solid = lg[LG_DH] - (lg[LG_QRXN] + lg[LG_QCOUPLE] + lg[LG_QFIXEDT]);
+    out->closure = (Ep - h->E_pop0) + (tot[1] - h->H0) - lg[LG_QRXN] - lg[LG_QFIXEDT] - out->Q_inlet -
+                   out->Q_outlet - out->D_interp - out->D_collision - out->D_coupling - out->D_solid;
+  }
   return FDLBM_OK;
 }
 
@@ -1282,14 +1318,14 @@ fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
 }
 
 // Checkpoint file: a fixed header, then the state the next step reads. Layout (native
-// little-endian): char magic[8] "FDLBMCK1"; u64 fingerprint; i32 nx, ny, ns, n_blocks;
+// little-endian): char magic[8] "FDLBMCK2"; u64 fingerprint; i32 nx, ny, ns, n_blocks;
 // i64 plane, steps, steps_at_residual; i32 have_snap, flags; f64 E0, H0, mass0[MAX_NS],
-// moles0[MAX_NS]; then h[cur] [ns][9][plane] in the storage type, FP32 F[cur] [1 + ns][plane], Ts[cur] [n],
+// moles0[MAX_NS], E_pop0; then h[cur] [ns][9][plane] in the storage type, FP32 F[cur] [1 + ns][plane], Ts[cur] [n],
 // Tgas[cur] [n], mom [ns + 3][n], snap [ns + 4][n], FP64 ledger [n_blocks][LG_COUNT],
 // FP32 wall densities [ns][n_wall_list].
 namespace {
 
-constexpr char CK_MAGIC[8] = {'F', 'D', 'L', 'B', 'M', 'C', 'K', '1'};
+constexpr char CK_MAGIC[8] = {'F', 'D', 'L', 'B', 'M', 'C', 'K', '2'};
 
 // FNV-1a over the node code words and the device parameters: a checkpoint loads only
 // into a handle built from the same geometry, species, transport and kinetics.
@@ -1310,7 +1346,7 @@ struct CkHeader {
   int32_t nx, ny, ns, n_blocks;
   int64_t plane, steps, steps_at_residual;
   int32_t have_snap, flags;
-  double E0, H0, mass0[MAX_NS], moles0[MAX_NS];
+  double E0, H0, mass0[MAX_NS], moles0[MAX_NS], E_pop0;
 };
 
 // The device buffers of a checkpoint, in file order: {device pointer, bytes}.
@@ -1349,6 +1385,7 @@ fdlbm_status fdlbm_save(fdlbm_handle* h, const char* path) {
   CK(cudaMemcpyAsync(&hd.flags, h->S.flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read flags");
   hd.E0 = h->E0;
   hd.H0 = h->H0;
+  hd.E_pop0 = h->E_pop0;
   std::memcpy(hd.mass0, h->mass0, sizeof(hd.mass0));
   std::memcpy(hd.moles0, h->moles0, sizeof(hd.moles0));
   FILE* f = std::fopen(path, "wb");
@@ -1417,6 +1454,7 @@ fdlbm_status fdlbm_load(fdlbm_handle* h, const char* path) {
   h->mom_fresh = true;
   h->E0 = hd.E0;
   h->H0 = hd.H0;
+  h->E_pop0 = hd.E_pop0;
   std::memcpy(h->mass0, hd.mass0, sizeof(hd.mass0));
   std::memcpy(h->moles0, hd.moles0, sizeof(hd.moles0));
   return FDLBM_OK;
@@ -1581,6 +1619,7 @@ fdlbm_status fdlbm_batch_create(fdlbm_handle* const* handles, int n, fdlbm_batch
     if (!handles[i]) return fail(FDLBM_EINVAL, "handle %d is NULL", i);
     if (handles[i]->dim != 2) return fail(FDLBM_EINVAL, "batches are implemented for D2Q9 handles only");
     if (handles[i]->P.local_tau) return fail(FDLBM_EINVAL, "batches do not take handles with local relaxation times");
+    if (handles[i]->P.ledger_detail) return fail(FDLBM_EINVAL, "batches do not take handles that keep exact accounts");
     for (int q = 0; q < i; ++q)
       if (handles[q] == handles[i]) return fail(FDLBM_EINVAL, "handle %d appears twice", i);
     const fdlbm_handle* h = handles[i];

@@ -127,6 +127,17 @@ struct Acc {
   float dr[NS], ax[NS], ay[NS], e[NS];
 };
 
+// Exact-account increments of one gas node, FP64 sums of exact differences of FP32
+// values (kept only by the exact-accounts step): energy taken from / lost into inlet and
+// outlet nodes, the pulls' departure from the pure shift, the collision's change.
+struct Acct {
+  double qin, qout, dint, dcol;
+};
+// Energy weight (1/2) c_j^2 |e_i|^2 of population (j, i), exact in FP32.
+__device__ __forceinline__ double eps_weight(const DevParams& P, int j, int e2) {
+  return double(0.5f * P.c2[j] * float(e2));
+}
+
 // Branch-free form of every streaming stencil: with s1 streamed from x - e_i and two more
 // sources sA, sB at x + mA e_i and x + mB e_i, the pulled value is
 //   s1 + (a/2) [(pA sA + pB sB) - (pA + pB) s1] + (a^2/2) [(qA sA + qB sB) - (qA + qB) s1]
@@ -255,10 +266,11 @@ __device__ __forceinline__ void issue_pulls(const DevParams& P, const PT* __rest
   cp_async_commit();
 }
 
-template <class PT, int NS, int I>
-__device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restrict__ src, int k, uint32_t cw,
+template <class PT, int NS, int I, bool DET>
+__device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restrict__ src,
+                                           const uint32_t* __restrict__ code, int k, uint32_t cw,
                                            Acc<NS>& a, float* __restrict__ s_h, int tid,
-                                           const float (&ecoef)[3]) {
+                                           const float (&ecoef)[3], Acct* ac) {
   constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
   if (I == 0) {
 #pragma unroll
@@ -270,6 +282,13 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
     return;
   }
   const int off = EX(I) + EY(I) * P.pitch;
+  // exact accounts: classes of the upstream node (source of s1) and of the node this
+  // node's own population i streams into
+  uint32_t cu = GAS, cd = GAS;
+  if constexpr (DET) {
+    cu = node_class(__ldg(code + k - off));
+    cd = node_class(__ldg(code + k + off));
+  }
   const uint32_t st = stencil_of(cw, I);
   const float4 cp = c_st_p[st];
   const float2 cq = c_st_q[st];
@@ -295,6 +314,18 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
       v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1));
       s_h[(j * Q + I) * GB + tid] = v;
     }
+    if constexpr (DET) {
+      const double e = eps_weight(P, j, e2);
+      ac->dint += e * (double(v) - double(v1));
+      const double off0 = double(P.rref[j]) * double(P.W0[I]);
+      if (cu == INLET) ac->qin += e * (double(v1) + off0);
+      if (cu == OUTLET) ac->qout += e * (double(v1) + off0);
+      if (cd == INLET || cd == OUTLET) {
+        const double own = e * (double(pop_ld(src + ((j * Q + I) * (int)P.plane + k), P.hsi[j])) + off0);
+        if (cd == INLET) ac->qin -= own;
+        else ac->qout -= own;
+      }
+    }
     a.dr[j] += v;
     if (EX(I) > 0) a.ax[j] += v;
     if (EX(I) < 0) a.ax[j] -= v;
@@ -304,21 +335,22 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
   }
 }
 
-template <class PT, int NS>
-__device__ __forceinline__ void interp_node(const DevParams& P, const PT* __restrict__ src, int k, uint32_t cw,
-                                            Acc<NS>& a, float* __restrict__ s_h, int tid) {
+template <class PT, int NS, bool DET>
+__device__ __forceinline__ void interp_node(const DevParams& P, const PT* __restrict__ src,
+                                            const uint32_t* __restrict__ code, int k, uint32_t cw,
+                                            Acc<NS>& a, float* __restrict__ s_h, int tid, Acct* ac) {
   const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
 #pragma unroll
   for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
-  interp_dir<PT, NS, 0>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 1>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 2>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 3>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 4>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 5>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 6>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 7>(P, src, k, cw, a, s_h, tid, ecoef);
-  interp_dir<PT, NS, 8>(P, src, k, cw, a, s_h, tid, ecoef);
+  interp_dir<PT, NS, 0, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 1, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 2, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 3, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 4, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 5, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 6, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 7, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  interp_dir<PT, NS, 8, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
 }
 
 // Mixture moments from the species accumulators (Eq. moments_of_g, Eq. moments_of_f):
@@ -381,12 +413,12 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 // LT: relaxation times updated per node from its pulled densities and g-temperature
 // (Sec. 3, Eqs. tau1s with Wilke's rule, tau2_approx_text, D_j_text); they also enter
 // K_j, so the lagged field carries each node's own tau1.
-template <class PT, int NS, bool PHI, int MODE, bool LT = false>
+template <class PT, int NS, bool PHI, int MODE, bool LT = false, bool DET = false>
 __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                          const uint32_t* __restrict__ code, int k, int aux,
                                          const float* __restrict__ Fsrc, float* __restrict__ Fdst,
                                          float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags,
-                                         float* __restrict__ s_h, int tid, uint32_t step) {
+                                         float* __restrict__ s_h, int tid, uint32_t step, Acct* ac = nullptr) {
   const uint32_t cw = __ldg(code + k);
   const int n = aux & GAS_AUX_N;
   const uint32_t seed = sizeof(PT) == 4 ? 0U : node_seed(k, step);
@@ -425,7 +457,7 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   }
   if (MODE == 0) {
     cp_async_wait_all();
-    interp_node<PT, NS>(P, src, k, cw, acc, s_h, tid);
+    interp_node<PT, NS, DET>(P, src, code, k, cw, acc, s_h, tid, ac);
   }
   finish_moments<NS>(P, acc, m);
 
@@ -577,6 +609,12 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
       // small differences are formed first so that FP32 keeps their precision.
       hn[i] = fmaf(-om, h[i] - fst, fmaf(-omt, fst - feq, h[i] + force));
     }
+    if constexpr (DET) {  // FP32 storage: hn is the value stored
+      double dc = 0.0;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) dc += eps_weight(P, j, EX(i) * EX(i) + EY(i) * EY(i)) * (double(hn[i]) - double(h[i]));
+      ac->dcol += dc;
+    }
     // 32-bit element offsets: the host keeps ns Q plane below 2^31.
     const int pl = (int)P.plane;
     PT* out = dst + j * Q * pl;
@@ -691,7 +729,7 @@ __device__ __forceinline__ float wmove(int i, float sM, float M, float2 u, float
   return fx * fy;
 }
 
-template <class PT, int NS>
+template <class PT, int NS, bool DET = false>
 __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                            const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
                                            const uint32_t* __restrict__ code, const float* __restrict__ Tgas, int n,
@@ -766,6 +804,11 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
             const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1[j];
             const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1[j];
             v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
+          }
+          if constexpr (DET) {  // arrival's departure from the shift; its energy, exactly
+            const double e = eps_weight(P, j, EX(i) * EX(i) + EY(i) * EY(i));
+            acc[LG_DINT] += e * (double(v) - double(v1[j]));
+            acc[LG_QWALLX] -= e * (double(v) + double(P.rref[j]) * double(P.W0[i]));
           }
           v += P.rref[j] * P.W0[i];
           A[j] += v;
@@ -850,8 +893,11 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
           const float w = (moving ? wmove(i, P.sqrtM[j], P.M[j], uw, Tw) : wr) * scale[j];
-          pop_store_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, w - P.rref[j] * P.W0[i], P.hs[j], seed,
-                           j * Q + i);
+          const float dv = w - P.rref[j] * P.W0[i];
+          pop_store_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, dv, P.hs[j], seed, j * Q + i);
+          if constexpr (DET)  // FP32 storage: dv is the value stored
+            acc[LG_QWALLX] += eps_weight(P, j, EX(i) * EX(i) + EY(i) * EY(i)) *
+                              (double(dv) + double(P.rref[j]) * double(P.W0[i]));
           Eout = fmaf(e2h * P.c2[j], w, Eout);
         }
       }
@@ -866,25 +912,29 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
       acc[LG_QCOUPLE] += couple;
     }
     Ts_dst[n] = Tn;
+    if constexpr (DET) acc[LG_DH] += double(P.rhocp_s) * (double(Tn) - double(Tx));
   }
 }
 
-// Block-level sum of the LG_COUNT ledger increments into this block's own slot (no
-// atomics; the slots are summed when the ledger is read).
+// Block-level sum of the first NQ ledger increments into this block's own slot (no
+// atomics; the slots are summed when the ledger is read). The plain step keeps the first
+// LG_BASIC; the exact-accounts step all LG_COUNT.
+constexpr int LG_BASIC = LG_NOCONV + 1;
+template <int NQ = LG_BASIC>
 __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], double* __restrict__ slot) {
-  __shared__ double sh[LG_COUNT][GB / 32];
+  __shared__ double sh[NQ][GB / 32];
   // FP64 arithmetic is slow on this part: quantities that are zero in the whole warp
   // (interior solid nodes away from fixed-T faces contribute nothing) skip the shuffles.
 #pragma unroll
-  for (int q = 0; q < LG_COUNT; ++q)
+  for (int q = 0; q < NQ; ++q)
     if (__any_sync(0xffffffffu, acc[q] != 0.0))
       for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < LG_COUNT; ++q) sh[q][warp] = acc[q];
+    for (int q = 0; q < NQ; ++q) sh[q][warp] = acc[q];
   __syncthreads();
-  if (threadIdx.x < LG_COUNT) {
+  if (threadIdx.x < NQ) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
     if (v != 0.0) slot[threadIdx.x] += v;
@@ -896,7 +946,7 @@ __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], doub
 // solid blocks the wall + FD update of consecutive solid nodes. The host interleaves
 // the descriptors by row bands so that wall blocks follow the gas blocks of the same
 // rows and find their neighbours' populations in L2.
-template <class PT, int NS, bool PHI, bool LT = false>
+template <class PT, int NS, bool PHI, bool LT = false, bool DET = false>
 __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     DevParams P, const PT* __restrict__ src, PT* __restrict__ dst, const uint32_t* __restrict__ code,
     const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
@@ -908,7 +958,22 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
   if (d.x == 0) {
-    if (tid < d.z) {
+    if constexpr (DET) {
+      Acct ac{0.0, 0.0, 0.0, 0.0};
+      if (tid < d.z) {
+        const int2 g = __ldg(gas_list + d.y + tid);
+        gas_node<PT, NS, PHI, 0, LT, true>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid,
+                                           step, &ac);
+      }
+      double acc[LG_COUNT];
+#pragma unroll
+      for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
+      acc[LG_QIN] = ac.qin;
+      acc[LG_QOUT] = ac.qout;
+      acc[LG_DINT] = ac.dint;
+      acc[LG_DCOL] = ac.dcol;
+      ledger_block_store<LG_COUNT>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+    } else if (tid < d.z) {
       const int2 g = __ldg(gas_list + d.y + tid);
       gas_node<PT, NS, PHI, 0, LT>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid, step);
     }
@@ -918,9 +983,9 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
 #pragma unroll
   for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
   if (tid < d.z)
-    solid_node<PT, NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
-                       d.y + tid, step, wall_u);
-  ledger_block_store(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+    solid_node<PT, NS, DET>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
+                            d.y + tid, step, wall_u);
+  ledger_block_store<DET ? LG_COUNT : LG_BASIC>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
 // Batched time step: several independent lattices (members of a batch) advance in one
@@ -1186,7 +1251,7 @@ cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, cudaStr
   }
 }
 
-template <class PT, int NS, bool PHI, bool LT = false>
+template <class PT, int NS, bool PHI, bool LT = false, bool DET = false>
 cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   if (P.n_blocks <= 0) return cudaSuccess;
   const size_t smem = gas_smem_bytes<NS, 0, LT>();
@@ -1195,25 +1260,27 @@ cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStre
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && !(configured & (1ull << dev))) {
-    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI, LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI, LT, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured |= 1ull << dev;
   }
   const int dstb = 1 - src;
   const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
-  step_kernel<PT, NS, PHI, LT><<<P.n_blocks, GB, smem, st>>>(
+  step_kernel<PT, NS, PHI, LT, DET><<<P.n_blocks, GB, smem, st>>>(
       P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
       paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
       S.flags, S.rw, step, S.wall_u);
   return cudaGetLastError();
 }
 
-// Locally updated relaxation times run the FP32 kernels instantiated in
-// fdlbm_local_tau.cu (the host rejects other storage types).
+// Locally updated relaxation times and the exact-accounts step run the FP32 kernels
+// instantiated in fdlbm_local_tau.cu and fdlbm_ledger_detail.cu (the host rejects other
+// storage types).
 template <class PT, int NS>
 cudaError_t step_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   const bool phi = P.energy_correction != 0;
   if constexpr (sizeof(PT) == 4) {
+    if (P.ledger_detail) return launch_step_detail(P, S, src, st, step);
     if (P.local_tau) return launch_step_local_tau(P, S, src, st, step);
   }
   return phi ? step_launch<PT, NS, true>(P, S, src, st, step) : step_launch<PT, NS, false>(P, S, src, st, step);

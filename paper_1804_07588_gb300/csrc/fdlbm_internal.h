@@ -84,6 +84,8 @@ struct DevParams {
   float phi_w[MAX_NS][MAX_NS];      // Wilke coefficients phi_jk
   float invD[MAX_NS][MAX_NS];       // 1 / D_jk (0 on the diagonal)
   float kcoef0[MAX_NS];             // energy-correction flux coefficient per unit tau1
+  // exact accounts: the step also measures face fluxes and scheme defects (FP32 D2Q9)
+  int ledger_detail;
 };
 
 // Device state of one handle.
@@ -107,7 +109,16 @@ struct DevState {
   float2* wall_u;       // velocity of each wall-list entry (moving walls), or nullptr
 };
 
-enum Ledger { LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV, LG_COUNT };
+// FP64 ledger increments per step-kernel block. The first five are always kept; the rest
+// only by the exact-accounts step (ledger_detail): shift-sense energy fluxes through the
+// inlet and outlet faces, the interpolation defect (pulled minus pure-shift values, gas
+// pulls and wall arrivals), the collision's energy change, the wall exchange measured
+// from the stored emissions and the pulled arrivals, and the solid's enthalpy change
+// measured from the stored temperatures.
+enum Ledger {
+  LG_QRXN = 0, LG_QWALL, LG_QCOUPLE, LG_QFIXEDT, LG_NOCONV,
+  LG_QIN, LG_QOUT, LG_DINT, LG_DCOL, LG_QWALLX, LG_DH, LG_COUNT
+};
 
 // Launchers (fdlbm_kernels.cu).
 // Initial state from device FP64 fields: X [ns][n], u [2][n], T_lat [n], Ts_lat [n], C [n];
@@ -187,6 +198,11 @@ cudaError_t launch_residual3(const DevParams& P, const DevState& S, int cur, cud
 
 // One D2Q9 step with locally updated relaxation times (FP32 storage; fdlbm_local_tau.cu).
 cudaError_t launch_step_local_tau(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
+// One D2Q9 step that also keeps the exact accounts (FP32 storage; fdlbm_ledger_detail.cu).
+cudaError_t launch_step_detail(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
+// Energy sum (1/2) c_j^2 |e_i|^2 g of the stored populations of gas nodes and of the wall
+// emissions in transit (FP32 storage), added into *out (zeroed here first).
+cudaError_t launch_pop_energy(const DevParams& P, const DevState& S, int cur, double* out, cudaStream_t st);
 
 // Bytes of one stored population.
 inline size_t pop_bytes_per_value(int storage) { return storage == FDLBM_STORAGE_FP32 ? 4 : 2; }

@@ -69,7 +69,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 
 class Options(C.Structure):
     _fields_ = [("storage", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("band_rows", C.c_int)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("band_rows", C.c_int),
+                ("ledger_detail", C.c_int)]
 
 
 class Info(C.Structure):
@@ -86,7 +87,11 @@ class Balance(C.Structure):
                 ("residual", C.c_double), ("solid_residual", C.c_double),
                 ("eps_paper", C.c_double), ("noconv", C.c_double),
                 ("mass", C.c_double * MAX_NS), ("mass0", C.c_double * MAX_NS),
-                ("moles", C.c_double * MAX_NS), ("moles0", C.c_double * MAX_NS)]
+                ("moles", C.c_double * MAX_NS), ("moles0", C.c_double * MAX_NS),
+                ("E_pop", C.c_double), ("E_pop0", C.c_double), ("Q_inlet", C.c_double),
+                ("Q_outlet", C.c_double), ("D_interp", C.c_double), ("D_collision", C.c_double),
+                ("D_coupling", C.c_double), ("D_solid", C.c_double), ("closure", C.c_double),
+                ("ledger_detail", C.c_int)]
 
 
 _lib = None
@@ -166,11 +171,14 @@ class Solver:
     """One coupled FD-LBM problem on one GPU, built from a problem dict (see
     ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
     storage (FP32 arithmetic in every case). band_rows: rows per band of the step
-    kernel's block order (0: 8; "auto": the autotuner's table)."""
+    kernel's block order (0: 8; "auto": the autotuner's table). ledger_detail: every step
+    also keeps the exact energy accounts of ``balance()`` (D2Q9, FP32, constant
+    relaxation times)."""
 
     STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
 
-    def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32", band_rows: int = 0):
+    def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32", band_rows: int = 0,
+                 ledger_detail: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
@@ -243,7 +251,7 @@ class Solver:
             band_rows = autotune.lookup(p, storage)
         self.band_rows = int(band_rows)
         opts = Options(self.STORAGE[storage], device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
-                       self._free_cb, None, self.band_rows)
+                       self._free_cb, None, self.band_rows, int(bool(ledger_detail)))
         h = C.c_void_p()
         _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
                               C.byref(opts), C.byref(h)))
