@@ -137,6 +137,7 @@ def lib():
         L.ora3_moments.argtypes = [C.c_void_p, dp]
         L.ora3_populations.argtypes = [C.c_void_p, dp]
         L.ora3_balance.argtypes = [C.c_void_p, dp]
+        L.ora3_accounts.argtypes = [C.c_void_p, dp]
         L.ora3_residual.argtypes = [C.c_void_p, C.c_int]
         L.ora3_residual.restype = C.c_double
         L.ora3_counts.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
@@ -148,6 +149,18 @@ def lib():
         L.ora3_collide.argtypes = [C.c_int, dp, dp, dp, dp, dp, dp, dp]
         _lib = L
     return _lib
+
+
+def _accounts_dict(out, ns):
+    m = out[A_MASS:].reshape(8, ns)
+    d = {"E_pop": out[A_E_POP], "E_pop0": out[A_E_POP0], "Q_inlet": out[A_Q_INLET],
+         "Q_outlet": out[A_Q_OUTLET], "D_interp": out[A_D_INTERP],
+         "D_collision": out[A_D_COLLISION], "D_coupling": out[A_D_COUPLING],
+         "closure": out[A_CLOSURE]}
+    for r, name in enumerate(("M_pop", "M_pop0", "M_inlet", "M_outlet", "Dm_interp",
+                              "Dm_collision", "M_rxn", "mass_closure")):
+        d[name] = m[r].copy()
+    return d
 
 
 def _dptr(a):
@@ -257,15 +270,7 @@ class Oracle:
         ns = self.ns
         out = np.zeros(A_MASS + 8 * ns)
         lib().ora_accounts(self._h, _dptr(out))
-        m = out[A_MASS:].reshape(8, ns)
-        d = {"E_pop": out[A_E_POP], "E_pop0": out[A_E_POP0], "Q_inlet": out[A_Q_INLET],
-             "Q_outlet": out[A_Q_OUTLET], "D_interp": out[A_D_INTERP],
-             "D_collision": out[A_D_COLLISION], "D_coupling": out[A_D_COUPLING],
-             "closure": out[A_CLOSURE]}
-        for r, name in enumerate(("M_pop", "M_pop0", "M_inlet", "M_outlet", "Dm_interp",
-                                  "Dm_collision", "M_rxn", "mass_closure")):
-            d[name] = m[r].copy()
-        return d
+        return _accounts_dict(out, ns)
 
     def residual(self, K: int) -> float:
         return lib().ora_residual(self._h, int(K))
@@ -426,6 +431,13 @@ class Oracle3:
         out = np.zeros((self.ns, Q3, self.n))
         lib().ora3_populations(self._h, _dptr(out))
         return out
+
+    def accounts(self) -> dict:
+        """Exact accounts of the D3Q19 scheme (the layout of Oracle.accounts)."""
+        ns = self.ns
+        out = np.zeros(A_MASS + 8 * ns)
+        lib().ora3_accounts(self._h, _dptr(out))
+        return _accounts_dict(out, ns)
 
     def balance(self) -> dict:
         out = np.zeros(B_MASS + 4 * self.ns)

@@ -75,6 +75,10 @@ struct ora3_state {
   double steps;
   double E_gas0, H_solid0, mass0[ORA3_MAX_NS], moles0[ORA3_MAX_NS];
   double Q_rxn, Q_wall, Q_couple, Q_fixedT, noconv;
+  /* Exact accounts (ora3_accounts), as in the D2Q9 oracle. */
+  double E_pop0, Q_in, Q_out, D_int, D_col;
+  double Mpop0[ORA3_MAX_NS], M_in[ORA3_MAX_NS], M_out[ORA3_MAX_NS], Dm_int[ORA3_MAX_NS], Dm_col[ORA3_MAX_NS],
+      M_rxn[ORA3_MAX_NS];
   long st_count[6];
 };
 
@@ -171,6 +175,16 @@ static double pull(ora3_state* s, const double* gsrc, int j, int i, int x, int y
   if (code == ST_BACKWARD) s3 = gsrc[PIDX(s, j, i, node_at(s, x - 3 * ex, y - 3 * ey, z - 3 * ez))];
   if (code == ST_FORWARD) sp = gsrc[PIDX(s, j, i, node_at(s, x + ex, y + ey, z + ez))];
   return interp(code, s->c[j], s3, s2, s1, s0, sp);
+}
+
+/* The pure-shift value of a pull: population (j, i) of the node x - e_i. */
+static double shift_source(const ora3_state* s, const double* gsrc, int j, int i, int x, int y, int z) {
+  return gsrc[PIDX(s, j, i, node_at(s, x - EX[i], y - EY[i], z - EZ[i]))];
+}
+
+/* Energy weight of population (j, i): (1/2) c_j^2 |e_i|^2. */
+static double eps_w(const ora3_state* s, int j, int i) {
+  return 0.5 * s->c[j] * s->c[j] * (double)(EX[i] * EX[i] + EY[i] * EY[i] + EZ[i] * EZ[i]);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -399,6 +413,7 @@ static void fail(char* err, int errlen, const char* msg, int x, int y, int z) {
 }
 
 static void ledger_totals(const ora3_state* s, double* E, double* H, double* mass, double* moles);
+static void pop_totals(const ora3_state* s, double* E, double* mass);
 
 ora3_state* ora3_create(const ora3_problem* p, char* err, int errlen) {
   if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->ns < 1 || p->ns > ORA3_MAX_NS || p->nr < 0 ||
@@ -544,6 +559,7 @@ ora3_state* ora3_create(const ora3_problem* p, char* err, int errlen) {
     s->mass0[j] = mass[j];
     s->moles0[j] = moles[j];
   }
+  pop_totals(s, &s->E_pop0, s->Mpop0);
   return s;
 }
 
@@ -600,6 +616,9 @@ static void wall_pass(ora3_state* s) {
           for (int i = 1; i < Q; ++i)
             if (arr[i]) {
               double v = pull(s, s->g, j, i, x, y, z, 1);
+              double d = v - shift_source(s, s->g, j, i, x, y, z);
+              s->D_int += eps_w(s, j, i) * d;
+              s->Dm_int[j] += d;
               A[j] += v;
               Earr += 0.5 * s->c[j] * s->c[j] * (EX[i] * EX[i] + EY[i] * EY[i] + EZ[i] * EZ[i]) * v;
             }
@@ -632,6 +651,7 @@ static void wall_pass(ora3_state* s) {
         for (int j = 0; j < ns; ++j) {
           m[j] = 0.0;
           for (int r = 0; r < s->p.nr && catalytic; ++r) m[j] += s->M[j] * s->p.nu[r][j] * rate[r];
+          s->M_rxn[j] += m[j];
           for (int i = 1; i < Q; ++i)
             if (out[i]) {
               double w = wr[i] * (A[j] + m[j]) / B; /* Eq. BC_gji, count form */
@@ -661,6 +681,17 @@ static void gas_pass(ora3_state* s) {
             double v = pull(s, s->g, j, i, x, y, z, 1);
             s->gp[PIDX(s, j, i, k)] = v;
             gl[j * Q + i] = v;
+            if (i == 0) continue;
+            /* accounts (see the D2Q9 oracle) */
+            double s1 = shift_source(s, s->g, j, i, x, y, z), e = eps_w(s, j, i);
+            s->D_int += e * (v - s1);
+            s->Dm_int[j] += v - s1;
+            int cu = cls_at(s, x - EX[i], y - EY[i], z - EZ[i]), cd = cls_at(s, x + EX[i], y + EY[i], z + EZ[i]);
+            double own = s->g[PIDX(s, j, i, k)];
+            if (cu == CL_INLET) { s->Q_in += e * s1; s->M_in[j] += s1; }
+            if (cu == CL_OUTLET) { s->Q_out += e * s1; s->M_out[j] += s1; }
+            if (cd == CL_INLET) { s->Q_in -= e * own; s->M_in[j] -= own; }
+            if (cd == CL_OUTLET) { s->Q_out -= e * own; s->M_out[j] -= own; }
           }
         s->Tg[k] = g_temperature(ns, s->M, gl, Cj);
         for (int j = 0; j < ns; ++j) s->Cj[(size_t)j * n + k] = Cj[j];
@@ -697,7 +728,11 @@ static void gas_pass(ora3_state* s) {
     }
     ora3_collide(ns, s->M, s->p.tau1, s->p.tau2, gl, dq, go, mom);
     for (int j = 0; j < ns; ++j)
-      for (int i = 0; i < Q; ++i) s->gn[PIDX(s, j, i, k)] = go[j * Q + i];
+      for (int i = 0; i < Q; ++i) {
+        s->gn[PIDX(s, j, i, k)] = go[j * Q + i];
+        s->D_col += eps_w(s, j, i) * (go[j * Q + i] - gl[j * Q + i]);
+        s->Dm_col[j] += go[j * Q + i] - gl[j * Q + i];
+      }
     for (int j = 0; j < ns; ++j) s->rho[(size_t)j * n + k] = mom[j];
     for (int al = 0; al < 3; ++al) s->u[(size_t)al * n + k] = mom[ns + al];
     s->T[k] = mom[ns + 3];
@@ -934,3 +969,53 @@ void ora3_counts(const ora3_state* s, long* out) {
 }
 
 void ora3_classes(const ora3_state* s, int* out) { memcpy(out, s->cls, sizeof(int) * (size_t)s->n); }
+
+/* Inventory of the stored populations (gas nodes and wall emissions in transit). */
+static void pop_totals(const ora3_state* s, double* E, double* mass) {
+  int ns = s->ns;
+  double e = 0.0;
+  for (int j = 0; j < ns; ++j) mass[j] = 0.0;
+  for (int z = 0; z < s->nz; ++z)
+    for (int y = 0; y < s->ny; ++y)
+      for (int x = 0; x < s->nx; ++x) {
+        int k = x + s->nx * (y + s->ny * z);
+        if (s->cls[k] != CL_GAS && s->cls[k] != CL_WALL) continue;
+        for (int j = 0; j < ns; ++j)
+          for (int i = 0; i < Q; ++i) {
+            if (s->cls[k] == CL_WALL && (i == 0 || cls_at(s, x + EX[i], y + EY[i], z + EZ[i]) != CL_GAS)) continue;
+            double g = s->g[PIDX(s, j, i, k)];
+            e += eps_w(s, j, i) * g;
+            mass[j] += g;
+          }
+      }
+  *E = e;
+}
+
+/* Exact accounts (layout ORA3_A_*, the D2Q9 oracle's). */
+void ora3_accounts(const ora3_state* s, double* out) {
+  int ns = s->ns;
+  double E, H, mass[ORA3_MAX_NS], moles[ORA3_MAX_NS], Ep, Mp[ORA3_MAX_NS];
+  ledger_totals(s, &E, &H, mass, moles);
+  pop_totals(s, &Ep, Mp);
+  double Dcpl = s->Q_wall + s->Q_couple;
+  out[ORA3_A_E_POP] = Ep;
+  out[ORA3_A_E_POP0] = s->E_pop0;
+  out[ORA3_A_Q_INLET] = s->Q_in;
+  out[ORA3_A_Q_OUTLET] = s->Q_out;
+  out[ORA3_A_D_INTERP] = s->D_int;
+  out[ORA3_A_D_COLLISION] = s->D_col;
+  out[ORA3_A_D_COUPLING] = Dcpl;
+  out[ORA3_A_CLOSURE] = (Ep - s->E_pop0) + (H - s->H_solid0) - s->Q_rxn - s->Q_fixedT - s->Q_in - s->Q_out -
+                        s->D_int - s->D_col - Dcpl;
+  double* m = out + ORA3_A_MASS;
+  for (int j = 0; j < ns; ++j) {
+    m[j] = Mp[j];
+    m[ns + j] = s->Mpop0[j];
+    m[2 * ns + j] = s->M_in[j];
+    m[3 * ns + j] = s->M_out[j];
+    m[4 * ns + j] = s->Dm_int[j];
+    m[5 * ns + j] = s->Dm_col[j];
+    m[6 * ns + j] = s->M_rxn[j];
+    m[7 * ns + j] = (Mp[j] - s->Mpop0[j]) - s->M_in[j] - s->M_out[j] - s->Dm_int[j] - s->Dm_col[j] - s->M_rxn[j];
+  }
+}

@@ -55,6 +55,12 @@ enum {
   ORA3_B_SOLID_RESIDUAL, ORA3_B_EPS_PAPER, ORA3_B_NOCONV, ORA3_B_MASS
 };
 
+/* Exact accounts of ora3_accounts: the layout of the D2Q9 oracle's ORA_A_*. */
+enum {
+  ORA3_A_E_POP = 0, ORA3_A_E_POP0, ORA3_A_Q_INLET, ORA3_A_Q_OUTLET, ORA3_A_D_INTERP, ORA3_A_D_COLLISION,
+  ORA3_A_D_COUPLING, ORA3_A_CLOSURE, ORA3_A_MASS /* then 8 blocks of ns */
+};
+
 ora3_state* ora3_create(const ora3_problem* p, char* err, int errlen);
 void ora3_destroy(ora3_state* s);
 int ora3_step(ora3_state* s, int nsteps);
@@ -62,6 +68,8 @@ int ora3_nfields(const ora3_state* s);                 /* 2*ns + 5 */
 void ora3_moments(const ora3_state* s, double* out);   /* rho_j, X_j, ux, uy, uz, T_K (gas), Ts_K (solid) */
 void ora3_populations(const ora3_state* s, double* out); /* [ns][19][n] */
 void ora3_balance(const ora3_state* s, double* out);
+/* Exact accounts (energy, then per-species mass; layout ORA3_A_*). */
+void ora3_accounts(const ora3_state* s, double* out);
 double ora3_residual(ora3_state* s, int K);
 void ora3_counts(const ora3_state* s, long* out);      /* class counts [5] + stencil counts [6] */
 void ora3_classes(const ora3_state* s, int* out);

@@ -373,3 +373,66 @@ def test_shear_wave3_mixture_viscosity():
     mu = (t1 * X / 3.0).sum()
     rho = (X * M).sum()
     assert abs(nu0 / (mu / rho) - 1.0) < 0.01, (nu1, nu2, nu0, mu / rho)
+
+
+# ---------------------------------------------------------------------------------------
+# Exact accounts of the D3Q19 scheme
+# ---------------------------------------------------------------------------------------
+
+def test_accounts3_uniform_inlet_flux_closed_form():
+    """Uniform inlet state, open channel periodic in y and z, one step: per inlet node the
+    net mass the pulls take is sum e_x f = rho_j sqrt(M_j) u and the energy
+    sum (1/2) c_j^2 |e|^2 e_x f = (1/2) rho_j u (1 + 2T) / sqrt(M_j): the folded D3Q19
+    equilibrium keeps the first moments and the third moments c_a c_b^2 of the D3Q27
+    product form (sum e_x e_y^2 f = rho sqrt(M) u T). The outlet carries the negatives;
+    uniform data leave no interpolation or collision defect."""
+    nx, ny, nz, u = 16, 6, 5, 0.02
+    p = W._base(3, nx, ny, nz, np.zeros((nz, ny, nx), np.uint8),
+                [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC],
+                u_inlet=u, inlet_profile=W.PLUG, reactions=[])
+    n = nx * ny * nz
+    X = np.array([s["X_inlet"] for s in p["species"]])
+    p["init"] = {"X": np.repeat(X[:, None], n, axis=1), "u": np.vstack([np.full(n, u), np.zeros(n), np.zeros(n)]),
+                 "T_K": np.full(n, p["T_inlet_K"]), "Ts_K": np.full(n, p["T_inlet_K"])}
+    o = oracle.Oracle3(p)
+    o.step(1)
+    a = o.accounts()
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    rho = X * M
+    T = p["T_inlet_K"] / (3.0 * p["T0_K"])
+    m_in = ny * nz * rho * np.sqrt(M) * u
+    q_in = ny * nz * np.sum(0.5 * rho * u * (1.0 + 2.0 * T) / np.sqrt(M))
+    np.testing.assert_allclose(a["M_inlet"], m_in, rtol=1e-12)
+    np.testing.assert_allclose(a["M_outlet"], -m_in, rtol=1e-12)
+    assert abs(a["Q_inlet"] - q_in) <= 1e-12 * q_in
+    assert abs(a["Q_outlet"] + q_in) <= 1e-12 * q_in
+    scale = abs(a["E_pop"])
+    assert abs(a["D_interp"]) <= 1e-14 * scale and abs(a["D_collision"]) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("name", ["closed_reactive_box", "closed_box_paper_coupling", "sphere_crop"])
+def test_accounts3_close_exactly(name):
+    """The D3Q19 inventory of stored populations moves by the face fluxes, the
+    interpolation and collision defects and the walls' emission minus arrival; with the
+    solid's identity energy closes to rounding, and so does each species' mass with the
+    walls' reaction production as its source."""
+    if name == "sphere_crop":
+        p, steps = W.crop3(W.config2(), 32, 16, 16), 60
+    else:
+        kw = {"coupling": W.PAPER} if name == "closed_box_paper_coupling" else {}
+        p = W.periodic_box3(14, 10, 12, solid_layers=3, **kw)
+        p["init"] = W.random_fields(p, seed=3)
+        steps = 30
+    o = oracle.Oracle3(p)
+    o.step(steps)
+    a, b = o.accounts(), o.balance()
+    scale = abs(a["E_pop"]) + abs(b["H_solid"])
+    assert abs(a["closure"]) <= 1e-12 * scale, a
+    assert np.abs(a["mass_closure"]).max() <= 1e-12 * a["M_pop"].sum(), a["mass_closure"]
+    if name == "closed_box_paper_coupling":
+        assert abs(a["D_coupling"]) > 0.0
+    else:
+        assert abs(a["D_coupling"]) <= 1e-12 * scale
+    if name == "sphere_crop":
+        assert a["Q_inlet"] > 0.0 and a["Q_outlet"] < 0.0
