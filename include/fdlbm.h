@@ -166,7 +166,7 @@ typedef struct {
   int band_rows;           /* rows per band of the step kernel's block order (gas blocks of a
                               band, then its wall blocks); 0: 8 */
   int ledger_detail;       /* 1: every step also keeps the exact accounts of fdlbm_balance
-                              (E_pop ... closure); D2Q9, FP32 storage, constant relaxation
+                              (E_pop ... closure); FP32 storage and constant relaxation
                               times only (else EINVAL); slower steps, same results */
 } fdlbm_options;
 

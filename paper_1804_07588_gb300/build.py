@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlbm.so")
 SOURCES = ["fdlbm_kernels.cu", "fdlbm_local_tau.cu", "fdlbm_ledger_detail.cu", "fdlbm_store_bf16.cu",
-           "fdlbm_store_fp16.cu", "fdlbm3d_kernels.cu", "fdlbm3d_store_bf16.cu", "fdlbm3d_store_fp16.cu", "fdlbm_api.cu"]
+           "fdlbm_store_fp16.cu", "fdlbm3d_kernels.cu", "fdlbm3d_ledger_detail.cu", "fdlbm3d_store_bf16.cu",
+           "fdlbm3d_store_fp16.cu", "fdlbm_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -34,6 +34,12 @@
 #include "fdlbm_device.cuh"
 
 namespace fdlbm {
+
+// The step that also keeps the exact accounts (FP32 storage; fdlbm3d_ledger_detail.cu), and
+// the energy of the stored populations of gas nodes and wall emissions (into *out).
+cudaError_t launch_step3_detail(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
+cudaError_t launch_pop_energy3(const DevParams& P, const DevState& S, int cur, double* out, cudaStream_t st);
+
 namespace {
 
 constexpr int G3 = STEP_BLOCK3;
@@ -213,12 +219,12 @@ __device__ __forceinline__ double block_sum3(double v, double* sh) {
 // Gas node: pull, moments, energy-correction divergence, collision (MODE 0), or the
 // pre-collision moments only (MODE 1).
 // ---------------------------------------------------------------------------------------
-template <class PT, int NS, bool PHI, int MODE>
+template <class PT, int NS, bool PHI, int MODE, bool DET = false>
 __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                           const uint64_t* __restrict__ code, int k, int aux,
                                           const float* __restrict__ Fsrc, float* __restrict__ Fdst,
                                           float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags,
-                                          float* __restrict__ s_h, int tid, uint32_t step) {
+                                          float* __restrict__ s_h, int tid, uint32_t step, Acct* ac = nullptr) {
   const uint64_t cw = __ldg(code + k);
   const uint32_t seed = sizeof(PT) == 4 ? 0U : node_seed(k, step);
   const int n = aux & GAS_AUX_N;
@@ -258,6 +264,13 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     }
     const float ec = e.w == 1 ? ec1 : ec2;
     const float fx = float(e.x), fy = float(e.y), fz = float(e.z);
+    // exact accounts: classes of the node s1 comes from and of the node this node's own
+    // population i streams into
+    uint32_t cu = GAS, cd = GAS;
+    if constexpr (DET) {
+      cu = node_class3(__ldg(code + k - off));
+      cd = node_class3(__ldg(code + k + off));
+    }
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       float v = v1[j];
@@ -265,6 +278,18 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
         const float d1 = fmaf(cp.x, vA[j], cp.y * vB[j]) - cp.z * v1[j];
         const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1[j];
         v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
+      }
+      if constexpr (DET) {
+        const double ew = eps_weight(P, j, e.w);
+        ac->dint += ew * (double(v) - double(v1[j]));
+        const double off0 = double(P.rref[j]) * double(P.W0_19[i]);
+        if (cu == INLET) ac->qin += ew * (double(v1[j]) + off0);
+        if (cu == OUTLET) ac->qout += ew * (double(v1[j]) + off0);
+        if (cd == INLET || cd == OUTLET) {
+          const double own = ew * (double(pop_ld(src + ((j * Q19 + i) * pl + k), P.hsi[j])) + off0);
+          if (cd == INLET) ac->qin -= own;
+          else ac->qout -= own;
+        }
       }
       s_h[(j * Q19 + i) * G3 + tid] = v;
       dr[j] += v;
@@ -417,6 +442,8 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
       const float h = s_h[(j * Q19 + i) * G3 + tid];
       const float hn = fmaf(-om, h - fst[i], fmaf(-omt, fst[i] - feq[i], h + force));
       pop_store3(out + (long long)i * pl, k, g, gh, hn, sc, seed, j * Q19 + i);
+      if constexpr (DET)  // FP32 storage: hn is the value stored
+        if (i > 0) ac->dcol += eps_weight(P, j, NNZ(i)) * (double(hn) - double(h));
     }
   }
 
@@ -469,7 +496,7 @@ __device__ __forceinline__ void rates3(const DevParams& P, const float (&rw)[NS]
   }
 }
 
-template <class PT, int NS>
+template <class PT, int NS, bool DET = false>
 __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                             const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
                                             const uint64_t* __restrict__ code, const float* __restrict__ Tgas, int n,
@@ -538,6 +565,11 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
           const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1[j];
           v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
         }
+        if constexpr (DET) {  // arrival's departure from the shift; its energy, exactly
+          const double ew = eps_weight(P, j, DX(i) * DX(i) + DY(i) * DY(i) + DZ(i) * DZ(i));
+          acc[LG_DINT] += ew * (double(v) - double(v1[j]));
+          acc[LG_QWALLX] -= ew * (double(v) + double(P.rref[j]) * double(P.W0_19[i]));
+        }
         v += P.rref[j] * P.W0_19[i];
         A[j] += v;
         Earr = fmaf(e2h * P.c2[j], v, Earr);
@@ -604,8 +636,11 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
         const float w = wr * scale[j];
-        pop_store3(dst + (long long)(j * Q19 + i) * pl, k, g, gh, w - P.rref[j] * P.W0_19[i], P.hs[j], seed,
-                   j * Q19 + i);
+        const float dv = w - P.rref[j] * P.W0_19[i];
+        pop_store3(dst + (long long)(j * Q19 + i) * pl, k, g, gh, dv, P.hs[j], seed, j * Q19 + i);
+        if constexpr (DET)  // FP32 storage: dv is the value stored
+          acc[LG_QWALLX] += eps_weight(P, j, DX(i) * DX(i) + DY(i) * DY(i) + DZ(i) * DZ(i)) *
+                            (double(dv) + double(P.rref[j]) * double(P.W0_19[i]));
         Eout = fmaf(e2h * P.c2[j], w, Eout);
       }
     }
@@ -620,20 +655,22 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
     acc[LG_QCOUPLE] += couple;
   }
   Ts_dst[n] = Tn;
+  if constexpr (DET) acc[LG_DH] += double(P.rhocp_s) * (double(Tn) - double(Tx));
 }
 
+template <int NQ = LG_BASIC>
 __device__ __forceinline__ void ledger_store3(double (&acc)[LG_COUNT], double* __restrict__ slot) {
-  __shared__ double sh[LG_BASIC][G3 / 32];
+  __shared__ double sh[NQ][G3 / 32];
 #pragma unroll
-  for (int q = 0; q < LG_BASIC; ++q)
+  for (int q = 0; q < NQ; ++q)
     if (__any_sync(0xffffffffu, acc[q] != 0.0))
       for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < LG_BASIC; ++q) sh[q][warp] = acc[q];
+    for (int q = 0; q < NQ; ++q) sh[q][warp] = acc[q];
   __syncthreads();
-  if (threadIdx.x < LG_BASIC) {
+  if (threadIdx.x < NQ) {
     double v = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
     if (v != 0.0) slot[threadIdx.x] += v;
@@ -641,7 +678,7 @@ __device__ __forceinline__ void ledger_store3(double (&acc)[LG_COUNT], double* _
 }
 
 // One time step in one launch (blocks: {role 0 gas / 1 solid, first, count, 0}).
-template <class PT, int NS, bool PHI>
+template <class PT, int NS, bool PHI, bool DET = false>
 __global__ void __launch_bounds__(G3, 4) step_kernel3(
     DevParams P, const PT* __restrict__ src, PT* __restrict__ dst, const uint64_t* __restrict__ code,
     const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
@@ -652,7 +689,22 @@ __global__ void __launch_bounds__(G3, 4) step_kernel3(
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
   if (d.x == 0) {
-    if (tid < d.z) {
+    if constexpr (DET) {
+      Acct ac{0.0, 0.0, 0.0, 0.0};
+      if (tid < d.z) {
+        const int2 g = __ldg(gas_list + d.y + tid);
+        gas_node3<PT, NS, PHI, 0, true>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid,
+                                        step, &ac);
+      }
+      double acc[LG_COUNT];
+#pragma unroll
+      for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
+      acc[LG_QIN] = ac.qin;
+      acc[LG_QOUT] = ac.qout;
+      acc[LG_DINT] = ac.dint;
+      acc[LG_DCOL] = ac.dcol;
+      ledger_store3<LG_COUNT>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+    } else if (tid < d.z) {
       const int2 g = __ldg(gas_list + d.y + tid);
       gas_node3<PT, NS, PHI, 0>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid, step);
     }
@@ -662,9 +714,9 @@ __global__ void __launch_bounds__(G3, 4) step_kernel3(
 #pragma unroll
   for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
   if (tid < d.z)
-    solid_node3<PT, NS>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
-                        d.y + tid, step);
-  ledger_store3(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+    solid_node3<PT, NS, DET>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
+                             d.y + tid, step);
+  ledger_store3<DET ? LG_COUNT : LG_BASIC>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
 // Pre-collision moments of the step that reads src (rho_j, ux, uy, uz, T into mom).
@@ -944,7 +996,7 @@ __global__ void residual_kernel3(DevParams P, const float* __restrict__ mom, con
   }
 }
 
-template <class PT, int NS, bool PHI>
+template <class PT, int NS, bool PHI, bool DET = false>
 cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
                          uint32_t step) {
   const size_t smem = smem3<NS>();
@@ -955,7 +1007,7 @@ cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool mo
   if (dev < 64 && !(configured[moments_only] & (1ull << dev))) {
     e = moments_only
             ? cudaFuncSetAttribute(moments_kernel3<PT, NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : cudaFuncSetAttribute(step_kernel3<PT, NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            : cudaFuncSetAttribute(step_kernel3<PT, NS, PHI, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured[moments_only] |= 1ull << dev;
   }
@@ -968,7 +1020,7 @@ cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool mo
   if (P.n_blocks <= 0) return cudaSuccess;
   const int dstb = 1 - src;
   const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
-  step_kernel3<PT, NS, PHI><<<P.n_blocks, G3, smem, st>>>(
+  step_kernel3<PT, NS, PHI, DET><<<P.n_blocks, G3, smem, st>>>(
       P, hs, static_cast<PT*>(S.h[dstb]), S.code64, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb],
       S.Ts[src], S.Ts[dstb], paper ? S.Tgas + (long long)src * P.n : nullptr,
       paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger, S.flags, S.rw, step);
@@ -977,6 +1029,9 @@ cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool mo
 
 template <class PT, int NS>
 cudaError_t step3_ns(const DevParams& P, const DevState& S, int src, bool mo, cudaStream_t st, uint32_t step) {
+  if constexpr (sizeof(PT) == 4) {
+    if (P.ledger_detail && !mo) return launch_step3_detail(P, S, src, st, step);
+  }
   return P.energy_correction ? step3_launch<PT, NS, true>(P, S, src, mo, st, step)
                              : step3_launch<PT, NS, false>(P, S, src, mo, st, step);
 }

@@ -350,9 +350,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
         if (k != j && !(species[j].D[k] > 0)) return fail(FDLBM_EINVAL, "species %d: D[%d] must be positive", j, k);
     }
   }
-  if (opts && opts->ledger_detail &&
-      (geom->lattice != FDLBM_D2Q9 || storage != FDLBM_STORAGE_FP32 || tr->local_tau))
-    return fail(FDLBM_EINVAL, "exact accounts need D2Q9, FP32 storage and constant relaxation times");
+  if (opts && opts->ledger_detail && (storage != FDLBM_STORAGE_FP32 || tr->local_tau))
+    return fail(FDLBM_EINVAL, "exact accounts need FP32 storage and constant relaxation times");
   if (geom->lattice == FDLBM_D3Q19) return create3(geom, species, n_species, tr, kin, init, opts, out);
 
   fdlbm_handle* h = new fdlbm_handle();
@@ -1023,6 +1022,7 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
   P.n_wall_list = (int)walls.size();
   for (int f = 0; f < 6; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
   set_physics_params(h, species, ns, tr, kin, storage, 3);
+  P.ledger_detail = (opts && opts->ledger_detail) ? 1 : 0;
   for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, h->T_inlet_lat);
 
   // Device state.
@@ -1132,6 +1132,11 @@ fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f) {
   for (int j = 0; j < ns; ++j) {
     h->mass0[j] = tot[2 + j];
     h->moles0[j] = tot[2 + ns + j];
+  }
+  h->E_pop0 = 0.0;
+  if (h->P.ledger_detail) {
+    st = read_pop_energy(h, &h->E_pop0);
+    if (st != FDLBM_OK) return st;
   }
   return FDLBM_OK;
 }

@@ -56,8 +56,12 @@ cudaError_t launch_step_detail(const DevParams& P, const DevState& S, int src, c
   }
 }
 
+// D3Q19 inventory (fdlbm3d_ledger_detail.cu).
+cudaError_t launch_pop_energy3(const DevParams& P, const DevState& S, int cur, double* out, cudaStream_t st);
+
 cudaError_t launch_pop_energy(const DevParams& P, const DevState& S, int cur, double* out, cudaStream_t st) {
-  if (P.storage != FDLBM_STORAGE_FP32 || P.dim == 3) return cudaErrorInvalidValue;
+  if (P.dim == 3) return launch_pop_energy3(P, S, cur, out, st);
+  if (P.storage != FDLBM_STORAGE_FP32) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
   pop_energy_kernel<<<(P.n + 255) / 256, 256, 0, st>>>(P, static_cast<const float*>(S.h[cur]), S.code, out);

@@ -172,7 +172,7 @@ class Solver:
     ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
     storage (FP32 arithmetic in every case). band_rows: rows per band of the step
     kernel's block order (0: 8; "auto": the autotuner's table). ledger_detail: every step
-    also keeps the exact energy accounts of ``balance()`` (D2Q9, FP32, constant
+    also keeps the exact energy accounts of ``balance()`` (FP32 storage, constant
     relaxation times)."""
 
     STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}

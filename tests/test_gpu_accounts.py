@@ -1,4 +1,4 @@
-"""Exact energy accounts of the D2Q9 step (handles created with ledger_detail): the FP64
+"""Exact energy accounts of the D2Q9 and D3Q19 steps (handles created with ledger_detail): the FP64
 ledger terms measured from the FP32 values the kernel stores and pulls close the energy
 balance to FP64 rounding, in closed and open systems and both coupling modes; the terms
 match the FP64 oracle's accounts; and keeping the accounts changes none of the step's
@@ -130,8 +130,56 @@ def test_accounts_rejected_where_not_built():
     with pytest.raises(fdlbm.FdlbmError):
         fdlbm.Solver(W.local_transport(chan()), ledger_detail=True)
     with pytest.raises(fdlbm.FdlbmError):
-        fdlbm.Solver(W.periodic_box3(8, 8, 8), ledger_detail=True)
+        fdlbm.Solver(W.periodic_box3(8, 8, 8), storage="fp16", ledger_detail=True)
     s = fdlbm.Solver(chan(), ledger_detail=True)
     with pytest.raises(fdlbm.FdlbmError):
         fdlbm.Batch([s])
     s.close()
+
+
+# ---------------------------------------------------------------------------------------
+# D3Q19
+# ---------------------------------------------------------------------------------------
+
+def _case3(name):
+    if name == "sphere_crop":
+        return W.crop3(W.config2(), 32, 16, 16), 60
+    kw = {"coupling": W.PAPER} if name == "closed_box_paper_coupling" else {}
+    p = W.periodic_box3(14, 10, 12, solid_layers=3, **kw)
+    p["init"] = W.random_fields(p, seed=3)
+    return p, 30
+
+
+CASES3 = ["closed_reactive_box", "closed_box_paper_coupling", "sphere_crop"]
+
+
+@pytest.mark.parametrize("name", CASES3)
+def test_exact_accounts3_close_and_match_oracle(name):
+    """The D3Q19 step's accounts close to FP64 rounding and match the D3Q19 oracle's."""
+    p, steps = _case3(name)
+    s = _fdlbm().Solver(p, ledger_detail=True)
+    o = oracle.Oracle3(p)
+    s.step(steps)
+    o.step(steps)
+    b, a = s.balance(), o.accounts()
+    s.close()
+    scale = abs(b["E_pop"]) + abs(b["H_solid"])
+    assert abs(b["closure"]) <= 1e-12 * scale, b
+    assert abs(b["D_solid"]) <= 1e-8 * scale
+    assert abs(b["E_pop"] - a["E_pop"]) <= 1e-6 * abs(a["E_pop"])
+    flux = max(abs(a["Q_inlet"]), abs(a["Q_outlet"]), abs(a["D_interp"]), abs(a["D_collision"]), 1e-30)
+    for k in ("Q_inlet", "Q_outlet", "D_interp", "D_collision"):
+        assert abs(b[k] - a[k]) <= 1e-4 * flux + 1e-9 * abs(a["E_pop"]), (k, b[k], a[k])
+    assert abs(b["D_coupling"] - a["D_coupling"]) <= 1e-4 * abs(a["D_coupling"]) + 1e-6 * scale
+
+
+def test_accounts3_change_no_result():
+    fdlbm = _fdlbm()
+    p, _ = _case3("sphere_crop")
+    s0, s1 = fdlbm.Solver(p), fdlbm.Solver(p, ledger_detail=True)
+    s0.step(40)
+    s1.step(40)
+    assert np.array_equal(s0.moments_host(), s1.moments_host())
+    assert np.array_equal(s0.populations(), s1.populations())
+    s0.close()
+    s1.close()
