@@ -183,3 +183,15 @@ def test_accounts3_change_no_result():
     assert np.array_equal(s0.populations(), s1.populations())
     s0.close()
     s1.close()
+
+
+def test_exact_accounts_close_on_the_bench_bed():
+    """The 1024x512 porous bed of the benchmark (inlet, outlet, 58,795 catalytic wall
+    nodes), 1000 steps: the exact accounts close to FP64 rounding at full size."""
+    s = _fdlbm().Solver(W.config1(), ledger_detail=True)
+    s.step(1000)
+    b = s.balance()
+    s.close()
+    scale = abs(b["E_pop"]) + abs(b["H_solid"])
+    assert abs(b["closure"]) <= 1e-12 * scale, b
+    assert b["Q_reaction"] > 0.0 and b["Q_inlet"] > 0.0
