@@ -699,3 +699,71 @@ def test_accounts_on_lattice_species_have_no_interpolation_defect():
     assert a["D_interp"] == 0.0
     assert np.all(a["Dm_interp"] == 0.0)
     assert abs(a["closure"]) <= 1e-12 * abs(a["E_pop"])
+
+
+@pytest.mark.parametrize("rate_form", [W.RATE_CONC_BILINEAR, W.RATE_XFRAC_REVERSIBLE])
+def test_single_wall_node_one_step_by_hand(rate_form):
+    """Brute force of one reactive-wall application (Sec. 4.3, Eqs. mass_balance, BC_gji,
+    showcase_Sj in the count form of reading R11) on a tiny lattice: one catalytic solid
+    node in a periodic 8x8 gas box, equal species masses so that every pull is a pure
+    shift. From the populations stored at t = 0 the test forms by hand the arrivals A_j,
+    the normalisation B of the rest-equilibrium emission shape f^eq(1, 0, T_w), the fixed
+    point rho_w = (A + m(rho_w)) / B of the water-gas-shift source m_j = M_j nu_j rate,
+    the emitted populations and the reaction heat, and compares them with the oracle
+    after one step."""
+    nx = ny = 8
+    x0 = y0 = 4
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[y0, x0] = W.CATALYTIC
+    rx = W.wgs_reaction(rate_form=rate_form)
+    p = W._base(2, nx, ny, 1, mask, [W.PERIODIC] * 4, reactions=[rx], rho_w_tol=1e-15, rho_w_maxit=500)
+    for s in p["species"]:
+        s["M_gmol"] = 2.016
+    p["init"] = W.random_fields(p, seed=7)
+    o = oracle.Oracle(p)
+    g0 = o.populations()
+    o.step(1)
+    g1 = o.populations()
+    b = o.balance()
+
+    ns = len(p["species"])
+    k = x0 + nx * y0
+    T0 = p["T0_K"]
+    Tw = p["init"]["Ts_K"][k] / (3.0 * T0)
+    # arrivals: every neighbour is gas, each population arrives from x - e_i unchanged
+    A = np.array([sum(g0[j, i, (x0 - EX[i]) % nx + nx * ((y0 - EY[i]) % ny)] for i in range(1, 9))
+                  for j in range(ns)])
+    wf = lambda e: 1.0 - Tw if e == 0 else 0.5 * Tw  # rest factor of the product form at u = 0
+    wr = np.array([wf(EX[i]) * wf(EY[i]) for i in range(9)])
+    B = wr[1:].sum()
+    nu = np.array(rx["nu"], dtype=float)
+    R = 8.314462618
+    kT = rx["k0"] * math.exp(-rx["Ea_Jmol"] / (R * 3.0 * T0 * Tw))
+
+    def rate(rw):
+        C = rw  # lattice molar masses are all 1
+        if rate_form == W.RATE_CONC_BILINEAR:
+            return kT * np.prod([C[j] ** (-nu[j]) for j in range(ns) if nu[j] < 0])
+        x = C / C.sum()
+        fwd = np.prod([x[j] ** (-nu[j]) for j in range(ns) if nu[j] < 0])
+        bwd = np.prod([x[j] ** nu[j] for j in range(ns) if nu[j] > 0])
+        return kT * (fwd - bwd / rx["Keq"])
+
+    rw = A / B
+    for _ in range(2000):
+        new = (A + nu * rate(rw)) / B
+        done = np.abs(new - rw).max() <= 1e-17
+        rw = new
+        if done:
+            break
+    r = rate(rw)
+    emitted = wr[None, 1:] * ((A + nu * r) / B)[:, None]
+    np.testing.assert_allclose(g1[:, 1:, k], emitted, rtol=1e-12)
+    q = -(rx["dH_Jmol"] / (3.0 * R * T0)) * r
+    assert r != 0.0 and abs(b["Q_reaction"] - q) <= 1e-12 * abs(q)
+    # energy the wall put into the gas: (1/2) |e_i|^2 (emitted - arrived), c_j = 1
+    e2 = (EX ** 2 + EY ** 2)[1:]
+    arrived = np.array([[g0[j, i, (x0 - EX[i]) % nx + nx * ((y0 - EY[i]) % ny)] for i in range(1, 9)]
+                        for j in range(ns)])
+    dE = 0.5 * np.sum(e2[None, :] * (emitted - arrived))
+    assert abs(b["Q_wall"] - dE) <= 1e-12 * np.abs(0.5 * e2[None, :] * emitted).sum()
