@@ -767,3 +767,24 @@ def test_single_wall_node_one_step_by_hand(rate_form):
                         for j in range(ns)])
     dE = 0.5 * np.sum(e2[None, :] * (emitted - arrived))
     assert abs(b["Q_wall"] - dE) <= 1e-12 * np.abs(0.5 * e2[None, :] * emitted).sum()
+
+
+def test_channel_develops_poiseuille_profile():
+    """Laminar channel flow (the channel test case of Sec. 6) with a plug inlet, no
+    reactions and isothermal walls: downstream of the entrance the velocity profile is the
+    Navier-Stokes solution of plane Poiseuille flow, a parabola symmetric about the
+    centre line that vanishes at the diffusive walls up to a first-order slip."""
+    n_gas, wall = 12, 3
+    p = W.channel(nx=48, n_gas=n_gas, wall=wall, u_inlet=0.02, profile=W.PLUG, reactions=[])
+    o = oracle.Oracle(p)
+    o.step(1500)
+    ns = len(p["species"])
+    ux = o.moments()[2 * ns].reshape(p["ny"], p["nx"])
+    col = ux[wall:wall + n_gas, 30]
+    y = np.arange(n_gas, dtype=float)
+    c = np.polyfit(y, col, 2)
+    assert c[0] < 0.0
+    assert np.abs(col - np.polyval(c, y)).max() <= 1e-3 * col.max()
+    assert abs(-c[1] / (2.0 * c[0]) - (n_gas - 1) / 2.0) <= 1e-6  # centre line
+    # the parabola at the wall nodes (one spacing outside the gas rows): small slip
+    assert abs(np.polyval(c, -1.0)) <= 0.05 * col.max()
