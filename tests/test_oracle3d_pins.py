@@ -436,3 +436,28 @@ def test_accounts3_close_exactly(name):
         assert abs(a["D_coupling"]) <= 1e-12 * scale
     if name == "sphere_crop":
         assert a["Q_inlet"] > 0.0 and a["Q_outlet"] < 0.0
+
+
+def test_channel3_develops_poiseuille_profile():
+    """D3Q19 laminar flow between two walls (periodic across the flow in z) from a plug
+    inlet: downstream the profile is the plane Poiseuille parabola, symmetric about the
+    mid-plane, uniform in z, vanishing at the diffusive walls up to a first-order slip."""
+    nx, ng, wall, nz = 24, 10, 2, 2
+    ny = ng + 2 * wall
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, :wall, :] = W.INERT
+    mask[:, wall + ng:, :] = W.INERT
+    p = W._base(3, nx, ny, nz, mask, [W.INLET, W.OUTLET, W.FIXED_T, W.FIXED_T, W.PERIODIC, W.PERIODIC],
+                u_inlet=0.02, inlet_profile=W.PLUG, reactions=[])
+    o = oracle.Oracle3(p)
+    o.step(900)
+    ns = len(p["species"])
+    ux = o.moments()[2 * ns].reshape(nz, ny, nx)
+    col = ux[0, wall:wall + ng, 16]
+    y = np.arange(ng, dtype=float)
+    c = np.polyfit(y, col, 2)
+    assert c[0] < 0.0
+    assert np.abs(col - np.polyval(c, y)).max() <= 1e-3 * col.max()
+    assert abs(-c[1] / (2.0 * c[0]) - (ng - 1) / 2.0) <= 1e-6
+    assert abs(np.polyval(c, -1.0)) <= 0.06 * col.max()
+    assert np.abs(ux[1, wall:wall + ng, 16] - col).max() <= 1e-12 * col.max()
