@@ -461,3 +461,87 @@ def test_channel3_develops_poiseuille_profile():
     assert abs(-c[1] / (2.0 * c[0]) - (ng - 1) / 2.0) <= 1e-6
     assert abs(np.polyval(c, -1.0)) <= 0.06 * col.max()
     assert np.abs(ux[1, wall:wall + ng, 16] - col).max() <= 1e-12 * col.max()
+
+
+@pytest.mark.parametrize("rate_form", [W.RATE_CONC_BILINEAR, W.RATE_XFRAC_REVERSIBLE])
+def test_single_wall_node3_one_step_by_hand(rate_form):
+    """Brute force of one reactive-wall application on the D3Q19 lattice (Sec. 4.3, count
+    form of reading R11): one catalytic solid node in a periodic 8x8x8 gas box, equal
+    species masses (every pull a pure shift). The emission shape at rest comes from the
+    folded product form (reading R1b): rest 1 - 3T + 3T^2, axis T/2 - T^2, face diagonal
+    T^2/4. From the populations at t = 0 the test forms the arrivals, the wall-density
+    fixed point, the emitted populations and the reaction heat by hand."""
+    n1 = 8
+    c0 = 4
+    mask = np.zeros((n1, n1, n1), np.uint8)
+    mask[c0, c0, c0] = W.CATALYTIC
+    rx = W.wgs_reaction(rate_form=rate_form)
+    p = W._base(3, n1, n1, n1, mask, [W.PERIODIC] * 6, reactions=[rx], rho_w_tol=1e-15, rho_w_maxit=500)
+    for s in p["species"]:
+        s["M_gmol"] = 2.016
+    p["init"] = W.random_fields(p, seed=7)
+    o = oracle.Oracle3(p)
+    g0 = o.populations()
+    o.step(1)
+    g1 = o.populations()
+    b = o.balance()
+
+    E = oracle.velocities3()  # direction order of the stored populations
+    ns = len(p["species"])
+    idx = lambda x, y, z: (x % n1) + n1 * ((y % n1) + n1 * (z % n1))
+    k = idx(c0, c0, c0)
+    T0 = p["T0_K"]
+    Tw = p["init"]["Ts_K"][k] / (3.0 * T0)
+    nnz = np.abs(E).sum(axis=1)
+    wr = np.where(nnz == 0, 1 - 3 * Tw + 3 * Tw ** 2, np.where(nnz == 1, Tw / 2 - Tw ** 2, Tw ** 2 / 4))
+    B = wr[1:].sum()
+    arrived = np.array([[g0[j, i, idx(c0 - E[i, 0], c0 - E[i, 1], c0 - E[i, 2])] for i in range(1, 19)]
+                        for j in range(ns)])
+    A = arrived.sum(axis=1)
+    nu = np.array(rx["nu"], dtype=float)
+    R = 8.314462618
+    kT = rx["k0"] * math.exp(-rx["Ea_Jmol"] / (R * 3.0 * T0 * Tw))
+
+    def rate(rw):
+        if rate_form == W.RATE_CONC_BILINEAR:
+            return kT * np.prod([rw[j] ** (-nu[j]) for j in range(ns) if nu[j] < 0])
+        x = rw / rw.sum()
+        fwd = np.prod([x[j] ** (-nu[j]) for j in range(ns) if nu[j] < 0])
+        bwd = np.prod([x[j] ** nu[j] for j in range(ns) if nu[j] > 0])
+        return kT * (fwd - bwd / rx["Keq"])
+
+    rw = A / B
+    for _ in range(2000):
+        new = (A + nu * rate(rw)) / B
+        done = np.abs(new - rw).max() <= 1e-17
+        rw = new
+        if done:
+            break
+    r = rate(rw)
+    emitted = wr[None, 1:] * ((A + nu * r) / B)[:, None]
+    np.testing.assert_allclose(g1[:, 1:, k], emitted, rtol=1e-12)
+    q = -(rx["dH_Jmol"] / (3.0 * R * T0)) * r
+    assert r != 0.0 and abs(b["Q_reaction"] - q) <= 1e-12 * abs(q)
+    dE = 0.5 * np.sum(nnz[None, 1:] * (emitted - arrived))
+    assert abs(b["Q_wall"] - dE) <= 1e-12 * np.abs(0.5 * nnz[None, 1:] * emitted).sum()
+
+
+def test_single_species_wall_density_closed_form():
+    """Non-reacting single species (reading R7's special case): the converged wall
+    density is the arrived mass over the emission normalisation, rho_w = A / B, and the
+    wall re-emits exactly what arrived."""
+    n1, c0 = 8, 4
+    mask = np.zeros((n1, n1, n1), np.uint8)
+    mask[c0, c0, c0] = W.INERT
+    p = W._base(3, n1, n1, n1, mask, [W.PERIODIC] * 6, reactions=[])
+    p["species"] = [dict(p["species"][3], X_init=1.0, X_inlet=1.0)]
+    p["init"] = W.random_fields(p, seed=8)
+    o = oracle.Oracle3(p)
+    g0 = o.populations()
+    o.step(1)
+    g1 = o.populations()
+    E = oracle.velocities3()
+    idx = lambda x, y, z: (x % n1) + n1 * ((y % n1) + n1 * (z % n1))
+    k = idx(c0, c0, c0)
+    A = sum(g0[0, i, idx(c0 - E[i, 0], c0 - E[i, 1], c0 - E[i, 2])] for i in range(1, 19))
+    assert abs(g1[0, 1:, k].sum() - A) <= 1e-14 * A
