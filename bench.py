@@ -213,11 +213,11 @@ def whole_job_value(ns: int, n_gas: int, steps: int, world: int, total_ms: float
     return ns * n_gas * steps * world / (total_ms * 1e-3) / 1e6
 
 
-def run_to_steady(fdlbm, p, init=None, tol=1e-6, every=500, max_steps=400_000, device=0):
+def run_to_steady(fdlbm, p, init=None, tol=1e-6, every=500, max_steps=400_000, device=0, storage="fp32"):
     """Steps and wall time (host clock around the whole loop, synchronised) for the solver
     to reach the steady-state residual tol, checked every `every` steps."""
     import torch
-    s = fdlbm.Solver(p, device=device)
+    s = fdlbm.Solver(p, device=device, storage=storage)
     if init is not None:
         s.set_fields(init)
     s.residual()
@@ -249,8 +249,20 @@ def time_to_steady(fdlbm, workloads, device=0):
     s.close()
     s, warm = run_to_steady(fdlbm, p, init=warm_init, device=device)
     s.close()
+    # Cold starts with 16-bit population storage (FP32 arithmetic), against the FP32 cold
+    # start above; stochastic rounding can hold the residual above the tolerance, so
+    # these runs are capped and report whether they converged.
+    reduced = {}
+    for storage in ("fp16", "bf16"):
+        try:
+            s, r = run_to_steady(fdlbm, p, device=device, storage=storage, max_steps=100_000)
+            s.close()
+            reduced[storage] = r
+        except Exception as e:  # reported in the line, the benchmark itself goes on
+            reduced[storage] = {"error": str(e)[:200]}
     return {"workload": "catalytic channel 128x32 gas + 2x8 solid rows, 5 species", "tol": 1e-6,
             "check_every": 500, "cold": cold, "warm": warm,
+            "cold_fp16_storage": reduced["fp16"], "cold_bf16_storage": reduced["bf16"],
             "warm_start": "steady state of the channel at inlet velocity 0.018 (a neighbouring "
                           "operating point); the learned warm start is not built"}
 
