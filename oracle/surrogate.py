@@ -194,3 +194,25 @@ def inputs(mask, u_in, T_in, X_in):
     chans = [solid, np.full(solid.shape, float(u_in)), np.full(solid.shape, float(T_in))]
     chans += [np.full(solid.shape, float(x)) for x in X_in]
     return np.stack(chans)
+
+
+# --- training -----------------------------------------------------------------------
+
+
+def adam_init(p):
+    """Zero first and second moments for every parameter, step count 0."""
+    return {"t": 0, "m": {k: np.zeros_like(v) for k, v in p.items()}, "v": {k: np.zeros_like(v) for k, v in p.items()}}
+
+
+def adam_step(p, g, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, 2015) of every parameter in place: moment
+    estimates m = beta1 m + (1 - beta1) g and v = beta2 v + (1 - beta2) g^2, bias
+    corrected by 1 - beta^t, step -lr m_hat / (sqrt(v_hat) + eps)."""
+    state["t"] += 1
+    t = state["t"]
+    for k in p:
+        m = state["m"][k] = beta1 * state["m"][k] + (1.0 - beta1) * g[k]
+        v = state["v"][k] = beta2 * state["v"][k] + (1.0 - beta2) * g[k] * g[k]
+        mh = m / (1.0 - beta1 ** t)
+        vh = v / (1.0 - beta2 ** t)
+        p[k] -= lr * mh / (np.sqrt(vh) + eps)

@@ -113,3 +113,42 @@ def test_network_shapes_and_inputs():
     # 16 -> 64 channels over four levels, the configuration's network
     n_par = sum(v.size for v in p.values())
     assert 100_000 < n_par < 1_000_000
+
+
+def test_adam_first_step_closed_form():
+    """After one step from zero moments the bias-corrected Adam step is -lr g / (|g| + eps)
+    for every element (m_hat = g, v_hat = g^2)."""
+    rng = np.random.default_rng(5)
+    p = {"a": rng.normal(size=(4, 3))}
+    p0 = p["a"].copy()
+    g = {"a": rng.normal(size=(4, 3))}
+    st = S.adam_init(p)
+    S.adam_step(p, g, st, lr=0.01)
+    np.testing.assert_allclose(p["a"], p0 - 0.01 * g["a"] / (np.abs(g["a"]) + 1e-8), rtol=1e-12)
+
+
+def test_training_reduces_the_loss():
+    """A small network learns a smooth target of the geometry (the solid indicator
+    averaged over its 3x3x3 neighbourhood, a stand-in for a field that follows the
+    geometry): 150 Adam steps on 4 seeded 8^3 masks cut the loss at least tenfold."""
+    rng = np.random.default_rng(6)
+    channels = [4, 6, 8]
+    p = S.init_params(1, 1, channels, seed=7)
+    data = []
+    box = np.ones((1, 1, 3, 3, 3)) / 27.0
+    for _ in range(4):
+        x = (rng.random((1, 8, 8, 8)) > 0.6).astype(float)
+        data.append((x, S.conv3(x, box, np.zeros(1))))
+    st = S.adam_init(p)
+
+    def total():
+        return sum(S.mse(S.forward(p, x, channels)[0], t)[0] for x, t in data) / len(data)
+
+    first = total()
+    for it in range(150):
+        x, t = data[it % len(data)]
+        y, cache = S.forward(p, x, channels)
+        _, gy = S.mse(y, t)
+        g, _ = S.backward(p, cache, gy, channels)
+        S.adam_step(p, g, st, lr=3e-3)
+    assert total() < 0.1 * first
