@@ -452,3 +452,23 @@ def batch_instances(n: int = 64, seed: int = 3000, nx_range=(256, 1024), ny_rang
         out.append(porous_disks(nx=nx, ny=ny, porosity=por, seed=seed + 1 + i, u_inlet=u, T0_K=T, T_init_K=T,
                                 T_inlet_K=T, T_solid_init_K=T, T_outer_K=T))
     return out
+
+
+def learning_instances(n: int = 576, seed: int = 4000, shape=(128, 64, 64), porosity=(0.4, 0.6),
+                       u_inlet=(0.005, 0.03), T_inlet_K=(450.0, 600.0)) -> list:
+    """Geometries and inlet conditions of the learned warm start's data: D3Q19 sphere
+    packings of the given shape (nx, ny, nz), r ~ U[5, 10], porosity uniform in its range
+    (overlapping spheres, so 0.4 is reachable), plug inlet velocity and inlet temperature
+    uniform in their ranges (the inlet temperature is also T0 and the initial gas and
+    solid temperature); instance i uses seed + i (the first 512 train, the last 64 test
+    by default)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    out = []
+    for i in range(n):
+        por = float(rng.uniform(*porosity))
+        u = float(rng.uniform(*u_inlet))
+        T = float(rng.uniform(*T_inlet_K))
+        out.append(porous_spheres(nx=nx, ny=ny, nz=nz, porosity=por, seed=seed + i, u_inlet=u, T0_K=T,
+                                  T_init_K=T, T_inlet_K=T, T_solid_init_K=T, T_outer_K=T))
+    return out

@@ -93,3 +93,18 @@ def test_species_and_kinetics_tables():
     rx = W.wgs_reaction()
     assert abs(sum(n * s["M_gmol"] for n, s in zip(rx["nu"], sp))) <= 1e-9
     assert rx["Ea_Jmol"] == 50e3 and rx["Keq"] == 10.0 and rx["dH_Jmol"] == -41e3
+
+
+def test_learning_instance_ranges():
+    """The warm start's geometries: 128x64x64 sphere packings, porosity in [0.4, 0.6]
+    (each percolating from inlet to outlet), inlet 0.005-0.03, 450-600 K; per-instance
+    seeds."""
+    inst = W.learning_instances(n=3)
+    assert len(inst) == 3
+    for p in inst:
+        assert (p["nx"], p["ny"], p["nz"], p["lattice"]) == (128, 64, 64, 19)
+        solid = p["mask"].reshape(64, 64, 128) > 0
+        assert 0.4 - 3e-3 <= 1.0 - solid.mean() <= 0.6 + 3e-3
+        assert W._percolates(~solid)
+        assert 0.005 <= p["u_inlet"] <= 0.03 and 450.0 <= p["T_inlet_K"] <= 600.0
+    assert len({p["mask"].tobytes() for p in inst}) == 3
