@@ -1,4 +1,6 @@
-"""ctypes wrapper of the plain FP64 CPU oracle (``fdlbm_oracle.c``).
+"""ctypes wrapper of the plain FP64 CPU oracles of the scheme (``fdlbm_oracle.c``,
+D2Q9, and ``fdlbm_oracle3d.c``, D3Q19); ``oracle.surrogate`` holds the FP64 oracle of
+the learned warm start's network.
 
 TEST INFRASTRUCTURE ONLY. Imported by the test-suite, the package smoke check and the
 benchmark's CPU-baseline / reference leg; the solver library never loads it. It builds
