@@ -68,6 +68,7 @@ class _Problem(C.Structure):
         ("init_C", C.POINTER(C.c_double)),
         ("local_tau", C.c_int), ("mu", C.c_double * MAX_NS), ("Djk", (C.c_double * MAX_NS) * MAX_NS),
         ("wall_u", C.POINTER(C.c_double)),
+        ("phi_lagged", C.c_int),
     ]
 
 
@@ -95,6 +96,7 @@ class _Problem3(C.Structure):
         ("init_X", C.POINTER(C.c_double)), ("init_u", C.POINTER(C.c_double)),
         ("init_T", C.POINTER(C.c_double)), ("init_Ts", C.POINTER(C.c_double)),
         ("init_C", C.POINTER(C.c_double)),
+        ("phi_lagged", C.c_int),
     ]
 
 
@@ -195,6 +197,7 @@ class Oracle:
             setattr(s, k, float(p[k]))
         for k in ("energy_correction", "inlet_profile", "coupling", "rho_w_maxit"):
             setattr(s, k, int(p[k]))
+        s.phi_lagged = int(p.get("phi_lagged", 0))
         rx = p["reactions"]
         s.nr = len(rx)
         for r, d in enumerate(rx):
@@ -228,6 +231,7 @@ class Oracle:
         self.ns = s.ns
         self.n = s.nx * s.ny
         self.nx, self.ny = s.nx, s.ny
+        self.T_inlet_K = float(p["T_inlet_K"])
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -371,6 +375,7 @@ def _fill_common(s, p, keep):
         setattr(s, k, float(p[k]))
     for k in ("energy_correction", "coupling", "rho_w_maxit"):
         setattr(s, k, int(p[k]))
+    s.phi_lagged = int(p.get("phi_lagged", 0))
     rx = p["reactions"]
     s.nr = len(rx)
     for r, d in enumerate(rx):
@@ -411,6 +416,7 @@ class Oracle3:
         self._h = C.c_void_p(h)
         self.ns = s.ns
         self.nx, self.ny, self.nz = s.nx, s.ny, s.nz
+        self.T_inlet_K = float(p["T_inlet_K"])
         self.n = s.nx * s.ny * s.nz
 
     def __del__(self):

@@ -21,8 +21,8 @@
  *   3. gas pass: every gas node pulls g*(t) (wall emissions w(t) included) with the
  *      off-lattice quadratic interpolation (Sec. 4.2), takes its moments (Eq.
  *      moments_of_g), the energy-correction divergence on its 4 axis neighbours (from
- *      the moments of the previous time level) and collides (Eq.
- *      final_kinetic_equation).
+ *      the moments of this step, reading R8; optionally those of the previous time
+ *      level) and collides (Eq. final_kinetic_equation).
  */
 #include "fdlbm_oracle.h"
 
@@ -64,6 +64,8 @@ struct ora_state {
   double* Cj_prev;           /* [ns][n] concentrations of the previous time level */
   double* divq;              /* scratch [ns][n] */
   double* tau1_prev;         /* [ns][n] local tau1 of the previous time level (local_tau) */
+  double* tau1_cur;          /* [ns][n] tau1 of every gas node at this step */
+  double* tau2_cur;          /* [ns][n] tau2 of every gas node at this step */
   double* wall_u;            /* [2][n] wall velocity of solid nodes */
   double* q;                 /* [n] reaction heat of the step at wall nodes */
   double* dE;                /* [n] energy the wall put into the gas this step */
@@ -520,6 +522,8 @@ ora_state* ora_create(const ora_problem* p, char* err, int errlen) {
   s->Cj_prev = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->divq = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->tau1_prev = (double*)xcalloc((size_t)ns * n, sizeof(double));
+  s->tau1_cur = (double*)xcalloc((size_t)ns * n, sizeof(double));
+  s->tau2_cur = (double*)xcalloc((size_t)ns * n, sizeof(double));
   s->q = (double*)xcalloc((size_t)n, sizeof(double));
   s->dE = (double*)xcalloc((size_t)n, sizeof(double));
   s->snap = (double*)xcalloc((size_t)(ns + 4) * n, sizeof(double));
@@ -648,6 +652,8 @@ void ora_destroy(ora_state* s) {
   free(s->Cj_prev);
   free(s->divq);
   free(s->tau1_prev);
+  free(s->tau1_cur);
+  free(s->tau2_cur);
   free(s->wall_u);
   free(s->q);
   free(s->dE);
@@ -776,6 +782,25 @@ static void gas_pass(ora_state* s) {
         }
       s->Tg[k] = g_temperature(ns, s->M, gl, Cj);
       for (int j = 0; j < ns; ++j) s->Cj[(size_t)j * n + k] = Cj[j];
+      /* relaxation times of this step: constants, or (reading R18) from the node's
+       * pulled (g) densities and g-temperature */
+      double t1[ORA_MAX_NS], t2[ORA_MAX_NS];
+      for (int j = 0; j < ns; ++j) {
+        t1[j] = s->p.tau1[j];
+        t2[j] = s->p.tau2[j];
+      }
+      if (s->p.local_tau) {
+        double rl[ORA_MAX_NS];
+        for (int j = 0; j < ns; ++j) {
+          rl[j] = 0.0;
+          for (int i = 0; i < Q; ++i) rl[j] += gl[j * Q + i];
+        }
+        ora_local_tau(ns, s->M, s->p.mu, &s->p.Djk[0][0], rl, s->Tg[k], t1, t2);
+      }
+      for (int j = 0; j < ns; ++j) {
+        s->tau1_cur[(size_t)j * n + k] = t1[j];
+        s->tau2_cur[(size_t)j * n + k] = t2[j];
+      }
     }
   /* 2b: divergence of the energy-correction flux q_j = K_j grad T. It is the sum of
    *  - q^Pr_j of Eq. q_Pr, (2 c_pj / Pr - 4 / M_j) tau1_j C_j T grad T with
@@ -789,9 +814,14 @@ static void gas_pass(ora_state* s) {
    * K_j = (2 c_pj / Pr - 1 / M_j) tau1_j C_j T. The divergence is the compact
    * second-order conservative difference on the 4 axis neighbours (reading R8: face
    * coefficients are the mean of the two nodes; faces towards non-gas nodes carry no
-   * correction flux), evaluated on the g-temperature and concentrations of the previous
-   * time level (the moments every gas node computed in the previous step; the initial
-   * fields at the first step). The paper does not fix the time level of the gradients. */
+   * correction flux). The right-hand side of Eq. final_kinetic_equation is taken at time
+   * t, so the gradients use the g-temperature, concentrations and tau1 every gas node
+   * formed in 2a of this step. Option phi_lagged takes them from the previous time
+   * level instead (the moments of the previous step; the initial fields at the first
+   * step). */
+  const double* Tgv = s->p.phi_lagged ? s->Tg_prev : s->Tg;
+  const double* Cjv = s->p.phi_lagged ? s->Cj_prev : s->Cj;
+  const double* t1v = s->p.phi_lagged ? s->tau1_prev : s->tau1_cur;
   for (int y = 0; y < s->ny; ++y)
     for (int x = 0; x < s->nx; ++x) {
       int k = x + s->nx * y;
@@ -801,12 +831,12 @@ static void gas_pass(ora_state* s) {
         if (s->p.energy_correction) {
           double cp = 2.0 / s->M[j]; /* (D + 2) / (2 M_j), D = 2 */
           double coef = (2.0 * cp / Pr - 1.0 / s->M[j]); /* times tau1 of the node */
-          double Kc = coef * s->tau1_prev[(size_t)j * n + k] * s->Cj_prev[(size_t)j * n + k] * s->Tg_prev[k];
+          double Kc = coef * t1v[(size_t)j * n + k] * Cjv[(size_t)j * n + k] * Tgv[k];
           for (int i = 1; i <= 4; ++i) {
             int kn = node_at(s, x + EX[i], y + EY[i]);
             if (kn < 0 || s->cls[kn] != CL_GAS) continue;
-            double Kn = coef * s->tau1_prev[(size_t)j * n + kn] * s->Cj_prev[(size_t)j * n + kn] * s->Tg_prev[kn];
-            dq += 0.5 * (Kc + Kn) * (s->Tg_prev[kn] - s->Tg_prev[k]);
+            double Kn = coef * t1v[(size_t)j * n + kn] * Cjv[(size_t)j * n + kn] * Tgv[kn];
+            dq += 0.5 * (Kc + Kn) * (Tgv[kn] - Tgv[k]);
           }
         }
         s->divq[(size_t)j * n + k] = dq;
@@ -822,19 +852,9 @@ static void gas_pass(ora_state* s) {
     }
     double t1[ORA_MAX_NS], t2[ORA_MAX_NS];
     for (int j = 0; j < ns; ++j) {
-      t1[j] = s->p.tau1[j];
-      t2[j] = s->p.tau2[j];
+      t1[j] = s->tau1_cur[(size_t)j * n + k];
+      t2[j] = s->tau2_cur[(size_t)j * n + k];
     }
-    if (s->p.local_tau) {
-      /* reading R18: the node's pulled (g) densities and g-temperature of this step */
-      double rl[ORA_MAX_NS];
-      for (int j = 0; j < ns; ++j) {
-        rl[j] = 0.0;
-        for (int i = 0; i < Q; ++i) rl[j] += gl[j * Q + i];
-      }
-      ora_local_tau(ns, s->M, s->p.mu, &s->p.Djk[0][0], rl, s->Tg[k], t1, t2);
-    }
-    for (int j = 0; j < ns; ++j) s->tau1_prev[(size_t)j * n + k] = t1[j];
     ora_collide(ns, s->M, t1, t2, gl, dq, go, mom);
     for (int j = 0; j < ns; ++j)
       for (int i = 0; i < Q; ++i) {
@@ -850,6 +870,7 @@ static void gas_pass(ora_state* s) {
   /* The moments of this step become the previous time level of the next one. */
   memcpy(s->Tg_prev, s->Tg, sizeof(double) * (size_t)n);
   memcpy(s->Cj_prev, s->Cj, sizeof(double) * (size_t)ns * n);
+  memcpy(s->tau1_prev, s->tau1_cur, sizeof(double) * (size_t)ns * n);
   /* Outlet (reading R13; the paper fixes only the inlet): equilibrium at the inlet
    * pressure p = C_in T_in (C_in = 1) with the composition, velocity and temperature of
    * the upstream gas node, so that the outlet gives the open channel its pressure

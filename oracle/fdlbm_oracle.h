@@ -51,6 +51,10 @@ typedef struct {
   /* Optional [2][n] velocity of solid nodes (lattice): a moving diffusive wall emits
    * f^eq(1, U_w, T_w) (Eq. BC_g_ji_1 with the wall velocity); NULL: walls at rest. */
   const double* wall_u;
+  /* Time level of the energy-correction gradients (reading R8): 0, the moments of this
+   * step (the plain reading of Eq. final_kinetic_equation); 1, those of the previous
+   * step. */
+  int phi_lagged;
 } ora_problem;
 
 typedef struct ora_state ora_state;

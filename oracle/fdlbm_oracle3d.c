@@ -25,7 +25,7 @@
  * (reactive diffusive wall, Sec. 4.3), solid pass (explicit FD heat step with the
  * interface coupling, Sec. 5), gas pass (pull with the off-lattice interpolation of
  * Sec. 4.2 along each link, moments, energy-correction divergence on the 6 axis
- * neighbours from the previous time level, collision of Eq. final_kinetic_equation).
+ * neighbours from the moments of this step, collision of Eq. final_kinetic_equation).
  */
 #include "fdlbm_oracle3d.h"
 
@@ -697,7 +697,10 @@ static void gas_pass(ora3_state* s) {
         for (int j = 0; j < ns; ++j) s->Cj[(size_t)j * n + k] = Cj[j];
       }
   /* Energy-correction divergence (readings R8, R9, R10 with D = 3) on the 6 axis
-   * neighbours from the previous time level; faces to non-gas nodes carry no flux. */
+   * neighbours from the moments of this step (option phi_lagged: of the previous time
+   * level); faces to non-gas nodes carry no flux. */
+  const double* Tgv = s->p.phi_lagged ? s->Tg_prev : s->Tg;
+  const double* Cjv = s->p.phi_lagged ? s->Cj_prev : s->Cj;
   for (int z = 0; z < s->nz; ++z)
     for (int y = 0; y < s->ny; ++y)
       for (int x = 0; x < s->nx; ++x) {
@@ -708,12 +711,12 @@ static void gas_pass(ora3_state* s) {
           if (s->p.energy_correction) {
             double cp = (D + 2.0) / (2.0 * s->M[j]);
             double coef = (2.0 * cp / Pr - (D - 1.0) / s->M[j]) * s->p.tau1[j];
-            double Kc = coef * s->Cj_prev[(size_t)j * n + k] * s->Tg_prev[k];
+            double Kc = coef * Cjv[(size_t)j * n + k] * Tgv[k];
             for (int i = 1; i <= 6; ++i) {
               int kn = node_at(s, x + EX[i], y + EY[i], z + EZ[i]);
               if (kn < 0 || s->cls[kn] != CL_GAS) continue;
-              double Kn = coef * s->Cj_prev[(size_t)j * n + kn] * s->Tg_prev[kn];
-              dq += 0.5 * (Kc + Kn) * (s->Tg_prev[kn] - s->Tg_prev[k]);
+              double Kn = coef * Cjv[(size_t)j * n + kn] * Tgv[kn];
+              dq += 0.5 * (Kc + Kn) * (Tgv[kn] - Tgv[k]);
             }
           }
           s->divq[(size_t)j * n + k] = dq;

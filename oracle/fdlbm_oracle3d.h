@@ -44,6 +44,9 @@ typedef struct {
   const double* init_T;   /* optional [n], K */
   const double* init_Ts;  /* optional [n], K */
   const double* init_C;   /* optional [n], lattice molar concentration (default 1) */
+  /* Time level of the energy-correction gradients (reading R8): 0, the moments of this
+   * step; 1, those of the previous step. */
+  int phi_lagged;
 } ora3_problem;
 
 typedef struct ora3_state ora3_state;
