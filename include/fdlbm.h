@@ -163,11 +163,17 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, size_t bytes, void* ctx);
   void* alloc_ctx;
-  int band_rows;           /* rows per band of the step kernel's block order (gas blocks of a
-                              band, then its wall blocks); 0: 8 */
+  int band_rows;           /* D2Q9: rows per band of the step kernel's block order (the gas
+                              tiles of a band, then its wall blocks) and height of the gas
+                              tiles, at most 64; 0: 16 */
   int ledger_detail;       /* 1: every step also keeps the exact accounts of fdlbm_balance
                               (E_pop ... closure); FP32 storage and constant relaxation
                               times only (else EINVAL); slower steps, same results */
+  int strict_geometry;     /* 1: reject (EGEOM, naming the first such node) geometries whose
+                              pulls need the linear or no-interpolation fallbacks, i.e.
+                              concave corners and one- or two-node gaps; the paper
+                              restricts its walls to planar and convex corner nodes
+                              (Sec. 4.2, Sec. 4.3). 0: accept them, with the fallbacks */
 } fdlbm_options;
 
 /* Counts and derived constants of a handle. */
@@ -230,10 +236,12 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
                           const fdlbm_transport* tr, const fdlbm_kinetics* kin,
                           const fdlbm_fields* init, const fdlbm_options* opts, fdlbm_handle** out);
 
-/* Enqueue n >= 0 time steps on the handle's stream (asynchronous). Each step is one
- * launch of the fused step kernel: gas nodes (streaming, moments, corrections and
- * collision, Sec. 4), interface wall nodes (reactive diffusive wall, Sec. 4.3) and
- * solid nodes (FD heat step and coupling, Sec. 5) in one grid. */
+/* Enqueue n >= 0 time steps on the handle's stream (asynchronous). A D2Q9 step is one
+ * launch of the fused step kernel: gas tiles (streaming, moments, the energy-correction
+ * divergence from this step's moments, collision, Sec. 4), interface wall nodes
+ * (reactive diffusive wall, Sec. 4.3) and solid nodes (FD heat step and coupling,
+ * Sec. 5) in one grid. A D3Q19 step with the energy correction first writes this step's
+ * moment field in a pass over the gas nodes, then launches the step kernel. */
 fdlbm_status fdlbm_step(fdlbm_handle* h, int64_t n);
 
 /* Wait for the handle's stream and report sticky device errors (EUNSTABLE). */
@@ -243,6 +251,14 @@ fdlbm_status fdlbm_sync(fdlbm_handle* h);
  * uy (, uz), T (K) on gas nodes, T_s (K) on solid nodes, 0 elsewhere. dst_on_device
  * selects a device or host destination; a host copy is synchronous. */
 fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device);
+
+/* fdlbm_moments with flags. FDLBM_MOMENTS_T_DEVIATION writes T and T_s as deviations
+ * from the inlet temperature, in K: the solver keeps temperatures as deviations from its
+ * reference state, and a float32 absolute temperature (ulp 3e-5 K at 500 K) would drop
+ * the digits of a small departure (a 2 K deviation carries only 5 of them). Other flag
+ * bits: EINVAL. */
+#define FDLBM_MOMENTS_T_DEVIATION 1u
+fdlbm_status fdlbm_moments_ex(fdlbm_handle* h, unsigned flags, float* dst, int dst_on_device);
 
 /* Stored populations g* (post-collision on gas, inlet and outlet nodes, emissions on
  * wall nodes), [ns][Q][n] float32 (Q = 9 or 19; absolute values, not deviations). */
@@ -311,8 +327,8 @@ int fdlbm_batch_size(const fdlbm_batch* b);
 void fdlbm_batch_destroy(fdlbm_batch* b);
 
 /* Checkpoint and restore (the paper has none: a library facility). fdlbm_save writes
- * the state the next step reads (current populations, lagged moment field, solid
- * temperature, moments, residual snapshot, ledger, step count) to the file at path;
+ * the state the next step reads (current populations, solid temperature, moments,
+ * residual snapshot, ledger, wall densities, step count) to the file at path;
  * fdlbm_load restores it into a handle created from the same geometry, species,
  * transport and kinetics (checked by a fingerprint of the node codes and device
  * parameters: EINVAL otherwise). Steps after a load give the same bits as steps after

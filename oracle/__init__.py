@@ -120,6 +120,8 @@ def lib():
         L.ora_residual.argtypes = [C.c_void_p, C.c_int]
         L.ora_residual.restype = C.c_double
         L.ora_counts.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
+        L.ora_get_state.argtypes = [C.c_void_p, dp, dp, dp]
+        L.ora_set_state.argtypes = [C.c_void_p, dp, dp, dp]
         L.ora_classes.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
         L.ora_equilibrium.argtypes = [C.c_double] * 5 + [dp]
         L.ora_interp.argtypes = [C.c_int] + [C.c_double] * 6
@@ -253,6 +255,21 @@ class Oracle:
         out = np.zeros((self.ns, Q, self.n))
         lib().ora_populations(self._h, _dptr(out))
         return out
+
+    def get_state(self):
+        """(g [ns][9][n], Ts [n], T [n]) of the current time level (lattice units)."""
+        g = np.empty((self.ns, Q, self.n))
+        Ts = np.empty(self.n)
+        T = np.empty(self.n)
+        lib().ora_get_state(self._h, _dptr(g), _dptr(Ts), _dptr(T))
+        return g, Ts, T
+
+    def set_state(self, g, Ts, T):
+        g = np.ascontiguousarray(g, np.float64)
+        Ts = np.ascontiguousarray(Ts, np.float64)
+        T = np.ascontiguousarray(T, np.float64)
+        assert g.size == self.ns * Q * self.n and Ts.size == self.n and T.size == self.n
+        lib().ora_set_state(self._h, _dptr(g), _dptr(Ts), _dptr(T))
 
     def balance(self) -> dict:
         out = np.zeros(B_MASS + 4 * self.ns)

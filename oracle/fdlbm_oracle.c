@@ -988,6 +988,21 @@ void ora_populations(const ora_state* s, double* out) {
   memcpy(out, s->g, sizeof(double) * (size_t)s->ns * Q * s->n);
 }
 
+/* The state a step reads (with the energy correction at the current time level): the
+ * stored populations g, the solid temperature and the gas mixture temperature T(f) of the
+ * previous step (read by the paper's coupling law). NULL arrays are skipped. */
+void ora_get_state(const ora_state* s, double* g, double* Ts, double* T) {
+  if (g) memcpy(g, s->g, sizeof(double) * (size_t)s->ns * Q * s->n);
+  if (Ts) memcpy(Ts, s->Ts, sizeof(double) * (size_t)s->n);
+  if (T) memcpy(T, s->T, sizeof(double) * (size_t)s->n);
+}
+
+void ora_set_state(ora_state* s, const double* g, const double* Ts, const double* T) {
+  if (g) memcpy(s->g, g, sizeof(double) * (size_t)s->ns * Q * s->n);
+  if (Ts) memcpy(s->Ts, Ts, sizeof(double) * (size_t)s->n);
+  if (T) memcpy(s->T, T, sizeof(double) * (size_t)s->n);
+}
+
 /* Gas energy sum_gas (D/2) C T + rho u^2 / 2 from the f-moments plus the energy
  * 1/2 sum c^2 w of the populations the walls have emitted but the gas has not yet
  * pulled in; solid enthalpy sum_solid (rho c_p)_s T_s; per-species mass and moles on

@@ -83,6 +83,11 @@ int ora_step(ora_state* s, int nsteps);
 int ora_nfields(const ora_state* s);                 /* 2*ns + 4 */
 void ora_moments(const ora_state* s, double* out);   /* [field][n]: rho_j, X_j, ux, uy, T_K, Ts_K */
 void ora_populations(const ora_state* s, double* out); /* [ns][9][n] stored post-collision / wall-emitted */
+/* The state a step reads: populations g [ns][9][n], solid temperature Ts [n] and gas
+ * temperature T [n] (lattice units); NULL arrays are skipped. Used to exchange the ghost
+ * columns of slabs that each run their own oracle (the slab decomposition's check). */
+void ora_get_state(const ora_state* s, double* g, double* Ts, double* T);
+void ora_set_state(ora_state* s, const double* g, const double* Ts, const double* T);
 void ora_balance(const ora_state* s, double* out);
 /* Exact accounts (energy, then per-species mass; layout ORA_A_*). */
 void ora_accounts(const ora_state* s, double* out);

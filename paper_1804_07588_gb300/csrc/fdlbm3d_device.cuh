@@ -202,6 +202,11 @@ __device__ __forceinline__ float wrest3(int i, float T) {
   if (nz == 1) return 0.5f * T * (1.f - 2.f * T);
   return 0.25f * T * T;
 }
+// wrest3(i, Tr + d) - wrest3(i, Tr) for the emitted (non-rest) directions, formed from the
+// deviation d: axis links 1/2 d (1 - 4 Tr - 2 d), face diagonals 1/4 d (2 Tr + d).
+__device__ __forceinline__ float dwrest3(int i, float Tr, float d) {
+  return NNZ(i) == 1 ? 0.5f * d * (1.f - 4.f * Tr - 2.f * d) : 0.25f * d * (2.f * Tr + d);
+}
 
 __device__ __forceinline__ double block_sum3(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -216,8 +221,10 @@ __device__ __forceinline__ double block_sum3(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Gas node: pull, moments, energy-correction divergence, collision (MODE 0), or the
-// pre-collision moments only (MODE 1).
+// Gas node: pull, moments, energy-correction divergence, collision (MODE 0), the
+// pre-collision moments only (MODE 1), or the moment field of the current step (MODE 2:
+// dTg and K_j into Fdst with ghost copies; written by a pass over all gas nodes before
+// the step, read by MODE 0 and 1 through Fsrc: reading R8 at the current time level).
 // ---------------------------------------------------------------------------------------
 template <class PT, int NS, bool PHI, int MODE, bool DET = false>
 __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
@@ -235,7 +242,7 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
     const float v = pop_ld(src + (j * Q19) * pl + k, P.hsi[j]);
-    s_h[(j * Q19) * G3 + tid] = v;
+    if (MODE == 0) s_h[(j * Q19) * G3 + tid] = v;
     dr[j] = v;
     ax[j] = ay[j] = az[j] = 0.f;
     ee[j] = ec0 * v;
@@ -291,7 +298,7 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
           else ac->qout -= own;
         }
       }
-      s_h[(j * Q19 + i) * G3 + tid] = v;
+      if (MODE == 0) s_h[(j * Q19 + i) * G3 + tid] = v;
       dr[j] += v;
       ax[j] = fmaf(fx, v, ax[j]);
       ay[j] = fmaf(fy, v, ay[j]);
@@ -312,8 +319,22 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     de = fmaf(P.c2[j], ee[j], de);
   }
   const float dTg = (de - (jx * jx + jy * jy + jz * jz) / r) * (1.f / 3.f) / C;
-  // Energy-correction divergence from the moment field of the previous time level on
-  // the 6 axis neighbours (faces to non-gas nodes carry no flux).
+  if (MODE == 2) {
+    const bool gh = (aux & GAS_AUX_GHOST) != 0;
+    Ghost3 g{{0, 0, 0}};
+    if (gh) {
+      int x = 0, y = 0, z = 0;
+      xyz_of(P, n, x, y, z);
+      g = ghost3(P, x, y, z);
+    }
+    store3(Fdst, k, g, gh, dTg);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+      store3(Fdst + (long long)(1 + j) * pl, k, g, gh, P.kcoef[j] * ((P.rref[j] + dr[j]) * P.invM[j]) * (Tr + dTg));
+    return;
+  }
+  // Energy-correction divergence from the moment field of this step on the 6 axis
+  // neighbours (faces to non-gas nodes carry no flux).
   float divq[NS];
   float sdq = 0.f;
 #pragma unroll
@@ -342,7 +363,7 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     mom[(long long)NS * P.n + n] = ux;
     mom[(long long)(NS + 1) * P.n + n] = uy;
     mom[(long long)(NS + 2) * P.n + n] = uz;
-    mom[(long long)(NS + 3) * P.n + n] = T;
+    mom[(long long)(NS + 3) * P.n + n] = dT;  // T - T_ref
     return;
   }
   const bool gh = (aux & GAS_AUX_GHOST) != 0;
@@ -350,13 +371,7 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
   int x = 0, y = 0, z = 0;
   if (gh || (aux & GAS_AUX_OUTLET)) xyz_of(P, n, x, y, z);
   if (gh) g = ghost3(P, x, y, z);
-  if (PHI) {
-    store3(Fdst, k, g, gh, dTg);
-#pragma unroll
-    for (int j = 0; j < NS; ++j)
-      store3(Fdst + (long long)(1 + j) * pl, k, g, gh, P.kcoef[j] * ((P.rref[j] + dr[j]) * P.invM[j]) * (Tr + dTg));
-  }
-  if (Tgas != nullptr) Tgas[n] = T;
+  if (Tgas != nullptr) Tgas[n] = dT;  // T - T_ref
   if (!(r > 0.f) || !(T > 0.f) || !isfinite(ux + uy + uz + T)) atomicOr(flags, 1);
 
   // Corrective diffusion velocity (reading R3).
@@ -523,7 +538,7 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
       }
       continue;
     }
-    if (Tgas != nullptr && node_class3(__ldg(code + k + (int)poff(P, d))) == GAS) gas_term += Tgas[nb] - (P.Tref + Tx);
+    if (Tgas != nullptr && node_class3(__ldg(code + k + (int)poff(P, d))) == GAS) gas_term += Tgas[nb] - Tx;
   }
   float Tn = fmaf(P.alpha_s, lap, Tx);
   if (node_class3(cw) == WALL) {
@@ -532,13 +547,17 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
     uint32_t arr = 0;
     for (int i = 1; i < Q19; ++i)
       if (stencil_of3(cw, i) != ST_NOT_ARRIVAL) arr |= 1u << i;
-    float B = 0.f;
+    // emitted shape W0_i + dW_i at the wall temperature; dW from the deviation Tx
+    float B = 0.f, dB = 0.f;
     for (int i = 1; i < Q19; ++i)
-      if (arr & (1u << OPP3(i))) B += wrest3(i, Tw);
-    float A[NS], rw[NS], mj[NS];
-    float Earr = 0.f;
+      if (arr & (1u << OPP3(i))) {
+        B += wrest3(i, Tw);
+        dB += dwrest3(i, P.Tref, Tx);
+      }
+    float A[NS], Ah[NS], rw[NS], mj[NS];
+    float Earr = 0.f, W0arr = 0.f;
 #pragma unroll
-    for (int j = 0; j < NS; ++j) A[j] = 0.f;
+    for (int j = 0; j < NS; ++j) Ah[j] = 0.f;
 #pragma unroll 1
     for (int i = 1; i < Q19; ++i) {
       if (!(arr & (1u << i))) continue;
@@ -549,6 +568,7 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
       const int2 cm = c3_m[st];
       const int dA = cm.x * off, dB = cm.y * off;
       const float e2h = 0.5f * float(DX(i) * DX(i) + DY(i) * DY(i) + DZ(i) * DZ(i));
+      W0arr += P.W0_19[i];
       float v1[NS], vA[NS], vB[NS];
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
@@ -570,14 +590,14 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
           acc[LG_DINT] += ew * (double(v) - double(v1[j]));
           acc[LG_QWALLX] -= ew * (double(v) + double(P.rref[j]) * double(P.W0_19[i]));
         }
-        v += P.rref[j] * P.W0_19[i];
-        A[j] += v;
+        Ah[j] += v;  // deviations; the rest part rref W0 is added below
         Earr = fmaf(e2h * P.c2[j], v, Earr);
       }
     }
     const float iB = 1.f / B;
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
+      A[j] = fmaf(P.rref[j], W0arr, Ah[j]);
       rw[j] = A[j] * iB;
       mj[j] = 0.f;
     }
@@ -625,23 +645,25 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
     const bool gh = g.d[0] || g.d[1] || g.d[2];
     const uint32_t seed = sizeof(PT) == 4 ? 0U : node_seed(k, step);
     float Eout = 0.f;
-    float scale[NS];
+    // emitted deviation dscale W0_i + (rref + dscale) dW_i, dscale = (A + m) / B - rref
+    // = (sum of arrived deviations - rref dB + m) / B (the rest parts of the mirrored
+    // arrival and emission sets cancel)
+    float dsc[NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iB;
+    for (int j = 0; j < NS; ++j) dsc[j] = (Ah[j] - P.rref[j] * dB + mj[j]) * iB;
 #pragma unroll 1
     for (int i = 1; i < Q19; ++i) {
       if (!(arr & (1u << OPP3(i)))) continue;
-      const float wr = wrest3(i, Tw);
+      const float dwr = dwrest3(i, P.Tref, Tx);
       const float e2h = 0.5f * float(DX(i) * DX(i) + DY(i) * DY(i) + DZ(i) * DZ(i));
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
-        const float w = wr * scale[j];
-        const float dv = w - P.rref[j] * P.W0_19[i];
+        const float dv = fmaf(dsc[j], P.W0_19[i], (P.rref[j] + dsc[j]) * dwr);
         pop_store3(dst + (long long)(j * Q19 + i) * pl, k, g, gh, dv, P.hs[j], seed, j * Q19 + i);
         if constexpr (DET)  // FP32 storage: dv is the value stored
           acc[LG_QWALLX] += eps_weight(P, j, DX(i) * DX(i) + DY(i) * DY(i) + DZ(i) * DZ(i)) *
                             (double(dv) + double(P.rref[j]) * double(P.W0_19[i]));
-        Eout = fmaf(e2h * P.c2[j], w, Eout);
+        Eout = fmaf(e2h * P.c2[j], dv, Eout);
       }
     }
     float q = 0.f;
@@ -719,17 +741,20 @@ __global__ void __launch_bounds__(G3, 4) step_kernel3(
   ledger_store3<DET ? LG_COUNT : LG_BASIC>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
 }
 
-// Pre-collision moments of the step that reads src (rho_j, ux, uy, uz, T into mom).
-template <class PT, int NS, bool PHI>
-__global__ void __launch_bounds__(G3) moments_kernel3(DevParams P, const PT* __restrict__ src,
-                                                     const uint64_t* __restrict__ code,
-                                                     const int2* __restrict__ gas_list,
-                                                     const float* __restrict__ Fsrc, float* __restrict__ mom) {
+// A pass over every gas node: MODE 1, the pre-collision moments of the step that reads
+// src (rho_j, ux, uy, uz, T into mom); MODE 2, that step's moment field (into Fdst).
+template <class PT, int NS, bool PHI, int MODE>
+__global__ void __launch_bounds__(G3) gas_pass_kernel3(DevParams P, const PT* __restrict__ src,
+                                                      const uint64_t* __restrict__ code,
+                                                      const int2* __restrict__ gas_list,
+                                                      const float* __restrict__ Fsrc, float* __restrict__ Fdst,
+                                                      float* __restrict__ mom) {
   extern __shared__ float smem[];
   const int t = blockIdx.x * G3 + threadIdx.x;
   if (t >= P.n_gas) return;
   const int2 g = __ldg(gas_list + t);
-  gas_node3<PT, NS, PHI, 1>(P, src, nullptr, code, g.x, g.y, Fsrc, nullptr, mom, nullptr, nullptr, smem, threadIdx.x, 0U);
+  gas_node3<PT, NS, PHI, MODE>(P, src, nullptr, code, g.x, g.y, Fsrc, Fdst, mom, nullptr, nullptr, smem, threadIdx.x,
+                               0U);
 }
 
 template <int NS>
@@ -828,8 +853,8 @@ __global__ void init_kernel3(DevParams P, PT* __restrict__ h0, PT* __restrict__ 
       if (c == GAS && real) {
         for (int j = 0; j < P.ns; ++j) mom[(long long)j * P.n + n] = float(C * Xn[j] * P.M[j]);
         for (int a = 0; a < 3; ++a) mom[(long long)(P.ns + a) * P.n + n] = float(uu[a]);
-        mom[(long long)(P.ns + 3) * P.n + n] = float(T);
-        Tgas[n] = Tgas[P.n + n] = float(T);
+        mom[(long long)(P.ns + 3) * P.n + n] = float(T - double(P.Tref));
+        Tgas[n] = Tgas[P.n + n] = float(T - double(P.Tref));
       }
     } else if (c == WALL || c == SOLID) {
       const double Ts = Tsl[n];
@@ -851,8 +876,9 @@ __global__ void init_kernel3(DevParams P, PT* __restrict__ h0, PT* __restrict__ 
 // ---------------------------------------------------------------------------------------
 // Outputs and reductions
 // ---------------------------------------------------------------------------------------
+// T and T_s in kelvin, or with dev as deviations from the inlet temperature (kelvin).
 __global__ void moments_out_kernel3(DevParams P, const float* __restrict__ mom, const float* __restrict__ Ts,
-                                    const uint64_t* __restrict__ code, float* __restrict__ dst) {
+                                    const uint64_t* __restrict__ code, float* __restrict__ dst, int dev) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P.n) return;
   int x, y, z;
@@ -869,9 +895,9 @@ __global__ void moments_out_kernel3(DevParams P, const float* __restrict__ mom, 
       dst[(ns + j) * N + n] = mom[j * N + n] * P.invM[j] / C;
     }
     for (int a = 0; a < 3; ++a) dst[(2 * ns + a) * N + n] = mom[(ns + a) * N + n];
-    dst[(2 * ns + 3) * N + n] = mom[(ns + 3) * N + n] * P.T3T0;
+    dst[(2 * ns + 3) * N + n] = (dev ? mom[(ns + 3) * N + n] + P.Tdev_off : P.Tref + mom[(ns + 3) * N + n]) * P.T3T0;
   } else if (c == WALL || c == SOLID) {
-    dst[(2 * ns + 4) * N + n] = (P.Tref + Ts[n]) * P.T3T0;
+    dst[(2 * ns + 4) * N + n] = (dev ? Ts[n] + P.Tdev_off : P.Tref + Ts[n]) * P.T3T0;
   }
 }
 
@@ -918,7 +944,7 @@ __global__ void totals_kernel3(DevParams P, const float* __restrict__ mom, const
         const double v = mom[(ns + a) * N + n];
         u2 += v * v;
       }
-      E = 1.5 * C * double(mom[(ns + 3) * N + n]) + 0.5 * r * u2;
+      E = 1.5 * C * (double(P.Tref) + double(mom[(ns + 3) * N + n])) + 0.5 * r * u2;
     } else if (c == WALL || c == SOLID) {
       H = double(P.rhocp_s) * (double(P.Tref) + double(Ts[n]));
       if (c == WALL)
@@ -977,12 +1003,12 @@ __global__ void residual_kernel3(DevParams P, const float* __restrict__ mom, con
         const int j = f - 3;
         v = mom[j * N + n] * P.invM[j] / C;
         ref = P.Xin[j];
-      } else if (f == 3 + ns) {
+      } else if (f == 3 + ns) {  // temperatures as deviations from T_ref
         v = mom[(ns + 3) * N + n];
-        ref = P.Tin_lat;
+        ref = -P.Tdev_off;
       } else {
-        v = P.Tref + Ts[n];
-        ref = P.Tin_lat;
+        v = Ts[n];
+        ref = -P.Tdev_off;
       }
       const float o = snap[f * N + n];
       d2 = double(v - o) * double(v - o);
@@ -996,32 +1022,46 @@ __global__ void residual_kernel3(DevParams P, const float* __restrict__ mom, con
   }
 }
 
+template <class K>
+cudaError_t opt_in_smem3(K kernel, size_t smem, unsigned long long& configured) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !(configured & (1ull << dev))) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  return cudaSuccess;
+}
+
+// One step: with the energy correction, first the moment field of the step into F[0]
+// (every gas node), then the step kernel (or the moments pass) reading it.
 template <class PT, int NS, bool PHI, bool DET = false>
 cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
                          uint32_t step) {
   const size_t smem = smem3<NS>();
-  static unsigned long long configured[2] = {0, 0};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 64 && !(configured[moments_only] & (1ull << dev))) {
-    e = moments_only
-            ? cudaFuncSetAttribute(moments_kernel3<PT, NS, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : cudaFuncSetAttribute(step_kernel3<PT, NS, PHI, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[moments_only] |= 1ull << dev;
-  }
+  static unsigned long long configured[3] = {0, 0, 0};
   const PT* hs = static_cast<const PT*>(S.h[src]);
+  cudaError_t e;
+  const int gas_grid = (P.n_gas + G3 - 1) / G3;
+  if (PHI && P.n_gas > 0) {
+    if ((e = opt_in_smem3(gas_pass_kernel3<PT, NS, PHI, 2>, smem, configured[2])) != cudaSuccess) return e;
+    gas_pass_kernel3<PT, NS, PHI, 2><<<gas_grid, G3, smem, st>>>(P, hs, S.code64, S.gas_list, nullptr, S.F[0], nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (moments_only) {
     if (P.n_gas <= 0) return cudaSuccess;
-    moments_kernel3<PT, NS, PHI><<<(P.n_gas + G3 - 1) / G3, G3, smem, st>>>(P, hs, S.code64, S.gas_list, S.F[src], S.mom);
+    if ((e = opt_in_smem3(gas_pass_kernel3<PT, NS, PHI, 1>, smem, configured[1])) != cudaSuccess) return e;
+    gas_pass_kernel3<PT, NS, PHI, 1><<<gas_grid, G3, smem, st>>>(P, hs, S.code64, S.gas_list, S.F[0], nullptr, S.mom);
     return cudaGetLastError();
   }
   if (P.n_blocks <= 0) return cudaSuccess;
+  if ((e = opt_in_smem3(step_kernel3<PT, NS, PHI, DET>, smem, configured[0])) != cudaSuccess) return e;
   const int dstb = 1 - src;
   const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
   step_kernel3<PT, NS, PHI, DET><<<P.n_blocks, G3, smem, st>>>(
-      P, hs, static_cast<PT*>(S.h[dstb]), S.code64, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb],
+      P, hs, static_cast<PT*>(S.h[dstb]), S.code64, S.gas_list, S.solid_list, S.blocks, S.F[0], nullptr,
       S.Ts[src], S.Ts[dstb], paper ? S.Tgas + (long long)src * P.n : nullptr,
       paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger, S.flags, S.rw, step);
   return cudaGetLastError();

@@ -30,8 +30,9 @@ cudaError_t launch_init3(const DevParams& P, const DevState& S, const double* X,
   }
 }
 
-cudaError_t launch_moments_out3(const DevParams& P, const DevState& S, int cur, float* dst, cudaStream_t st) {
-  moments_out_kernel3<<<(P.n + 255) / 256, 256, 0, st>>>(P, S.mom, S.Ts[cur], S.code64, dst);
+cudaError_t launch_moments_out3(const DevParams& P, const DevState& S, int cur, float* dst, bool t_dev,
+                                cudaStream_t st) {
+  moments_out_kernel3<<<(P.n + 255) / 256, 256, 0, st>>>(P, S.mom, S.Ts[cur], S.code64, dst, t_dev ? 1 : 0);
   return cudaGetLastError();
 }
 

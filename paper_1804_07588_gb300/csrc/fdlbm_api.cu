@@ -192,6 +192,7 @@ void set_physics_params(fdlbm_handle* h, const fdlbm_species* species, int ns, c
   P.p_out = (float)Tref;  // C_in T_in with C_in = 1
   P.u_inlet = (float)tr->u_inlet;
   P.Tin_lat = (float)Tref;
+  P.Tdev_off = (float)(double(P.Tref) - Tref);
   h->X_init.resize(ns);
   h->X_inlet.resize(ns);
   for (int j = 0; j < ns; ++j) {
@@ -352,6 +353,32 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   }
   if (opts && opts->ledger_detail && (storage != FDLBM_STORAGE_FP32 || tr->local_tau))
     return fail(FDLBM_EINVAL, "exact accounts need FP32 storage and constant relaxation times");
+  {
+    // Mole fractions: each in [0, 1], summing to 1 (initial and inlet composition).
+    double sx0 = 0.0, sx1 = 0.0;
+    for (int j = 0; j < n_species; ++j) {
+      if (!(species[j].X_init >= 0 && species[j].X_init <= 1) || !(species[j].X_inlet >= 0 && species[j].X_inlet <= 1))
+        return fail(FDLBM_EINVAL, "species %d: mole fractions must lie in [0, 1]", j);
+      sx0 += species[j].X_init;
+      sx1 += species[j].X_inlet;
+    }
+    if (std::fabs(sx0 - 1.0) > 1e-6 || std::fabs(sx1 - 1.0) > 1e-6)
+      return fail(FDLBM_EINVAL, "mole fractions must sum to 1 (initial %.9g, inlet %.9g)", sx0, sx1);
+    // The product-form equilibrium (Eq. eq_state_pop) needs a positive rest factor
+    // 1 - M_j u^2 - T for every species (M_j relative to the lightest species, T in
+    // lattice units T_K / (3 T0)).
+    double Mmin = species[0].M_gmol, Mmax = species[0].M_gmol;
+    for (int j = 1; j < n_species; ++j) {
+      Mmin = std::min(Mmin, species[j].M_gmol);
+      Mmax = std::max(Mmax, species[j].M_gmol);
+    }
+    const double Mr = Mmax / Mmin, u = tr->u_inlet;
+    const double Tin = tr->T_inlet_K / (3.0 * tr->T0_K), T0 = tr->T_init_K / (3.0 * tr->T0_K);
+    if (!(Mr * u * u + Tin < 1.0))
+      return fail(FDLBM_EINVAL, "inlet state outside the equilibrium's range: 1 - M u^2 - T = %.6g <= 0 "
+                  "(T_lat %.6g, u %.6g, heaviest M %.6g)", 1.0 - Mr * u * u - Tin, Tin, u, Mr);
+    if (!(T0 < 1.0)) return fail(FDLBM_EINVAL, "initial temperature outside the equilibrium's range: T_lat %.6g >= 1", T0);
+  }
   if (geom->lattice == FDLBM_D3Q19) return create3(geom, species, n_species, tr, kin, init, opts, out);
 
   fdlbm_handle* h = new fdlbm_handle();
@@ -454,6 +481,23 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       h->code[k] = w;
       h->counts[c]++;
     }
+  if (opts && opts->strict_geometry) {
+    // Reading R6: the linear and no-interpolation fallbacks serve concave corners and one-
+    // or two-node gaps, which the paper's geometries exclude.
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const uint32_t w = h->code[x + nx * y], c = node_class(w);
+        if (c != GAS && c != WALL) continue;
+        for (int i = 1; i < Q; ++i) {
+          const uint32_t st = stencil_of(w, i);
+          if (st == ST_NONE || st == ST_LIN_S0 || st == ST_LIN_S2) {
+            delete h;
+            return fail(FDLBM_EGEOM, "strict geometry: %s node (%d,%d) pulls direction %d without a quadratic "
+                        "stencil (concave corner or narrow gap)", c == GAS ? "gas" : "wall", x, y, i);
+          }
+        }
+      }
+  }
   std::vector<int32_t> solid_list(walls);
   solid_list.insert(solid_list.end(), solids.begin(), solids.end());
 
@@ -491,42 +535,96 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       }
       pcode[(size_t)px + (size_t)py * P.pitch] = h->code[x + nx * y];
     }
-  // Gas nodes row-major: a warp writes contiguous runs of every population plane.
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x)
-      if (G.cls[x + nx * y] == GAS) {
-        const bool near_x = G.px && (x < GHOST || x >= nx - GHOST);
-        const bool near_y = G.py && (y < GHOST || y >= ny - GHOST);
-        const bool outlet = x + 1 == nx - 1 && G.cls[x + 1 + nx * y] == OUTLET;
-        const int aux = (x + nx * y) | (outlet ? GAS_AUX_OUTLET : 0) | (near_x || near_y ? GAS_AUX_GHOST : 0);
-        gas_list.push_back(make_int2((x + XOFF) + (y + YOFF) * P.pitch, aux));
-      }
-  P.n_gas = (int)gas_list.size();
-  // Step-kernel blocks, interleaved by bands of 8 rows: the gas blocks of a band, then
-  // the wall blocks of the same band; the interior solid blocks come last.
+  // Gas tiles and step-kernel blocks. Rows are taken in bands of `band` rows; each band
+  // is split along x into column ranges whose gas nodes (the tile's interior) plus the
+  // gas nodes of the one-node ring around it that neighbour them along an axis (its
+  // halo, needed for the energy-correction divergence at the current time level) fit
+  // one block, and whose moment map ((columns + 2) x (rows + 2) slots) fits
+  // GAS_MAP_SLOTS. Ring positions wrap on periodic axes (a range spanning a whole
+  // periodic axis repeats nodes of its own interior in the ring). Without the energy
+  // correction tiles have no halo. Blocks of a band: its gas tiles, then its wall
+  // blocks; the interior solid blocks come last.
+  const bool phi = tr->energy_correction != 0;
   std::vector<int4> blocks;
+  std::vector<uint16_t> gas_slot;
   {
-    std::vector<int> gas_row(ny + 1, 0), wall_row(ny + 1, 0);
-    for (int y = 0, g = 0, w = 0; y <= ny; ++y) {
-      gas_row[y] = g;
+    const int band = std::min(64, (opts && opts->band_rows > 0) ? opts->band_rows : 16);
+    auto is_gas = [&](int x, int y) { return G.cls_at(x, y) == GAS; };
+    std::vector<int> wall_row(ny + 1, 0);
+    for (int y = 0, w = 0; y <= ny; ++y) {
       wall_row[y] = w;
       if (y == ny) break;
-      for (int x = 0; x < nx; ++x) {
-        g += G.cls[x + nx * y] == GAS;
-        w += G.cls[x + nx * y] == WALL;
-      }
+      for (int x = 0; x < nx; ++x) w += G.cls[x + nx * y] == WALL;
     }
-    auto chunks = [&](int role, int first, int last) {
-      for (int s0 = first; s0 < last; s0 += STEP_BLOCK) blocks.push_back(make_int4(role, s0, std::min(STEP_BLOCK, last - s0), 0));
+    auto chunks = [&](int first, int last) {
+      for (int s0 = first; s0 < last; s0 += STEP_BLOCK) blocks.push_back(make_int4(1, s0, std::min(STEP_BLOCK, last - s0), 0));
     };
-    const int band = (opts && opts->band_rows > 0) ? opts->band_rows : 8;
+    auto push_entry = [&](int x, int y, int aux, int slot) {
+      const int wx = ((x % nx) + nx) % nx, wy = ((y % ny) + ny) % ny;
+      gas_list.push_back(make_int2((wx + XOFF) + (wy + YOFF) * P.pitch, aux));
+      gas_slot.push_back((uint16_t)slot);
+    };
+    std::vector<int> col_int(nx), col_tb(nx);
     for (int y0 = 0; y0 < ny; y0 += band) {
-      const int y1 = std::min(ny, y0 + band);
-      chunks(0, gas_row[y0], gas_row[y1]);
-      chunks(1, wall_row[y0], wall_row[y1]);
+      const int y1 = std::min(ny, y0 + band), H = y1 - y0;
+      // per column: interior gas nodes, and top/bottom ring nodes it needs
+      for (int x = 0; x < nx; ++x) {
+        int c = 0;
+        for (int y = y0; y < y1; ++y) c += is_gas(x, y);
+        col_int[x] = c;
+        col_tb[x] = phi ? int(is_gas(x, y0 - 1) && is_gas(x, y0)) + int(is_gas(x, y1) && is_gas(x, y1 - 1)) : 0;
+      }
+      auto side = [&](int xs, int xin) {  // ring column xs beside interior column xin
+        if (!phi) return 0;
+        int c = 0;
+        for (int y = y0; y < y1; ++y) c += is_gas(xs, y) && is_gas(xin, y);
+        return c;
+      };
+      for (int x0 = 0; x0 < nx;) {
+        const int left = side(x0 - 1, x0);
+        int x1 = x0 + 1, inner = col_int[x0] + col_tb[x0];
+        while (x1 < nx) {
+          const int more = inner + col_int[x1] + col_tb[x1];
+          if (left + more + side(x1 + 1, x1) > STEP_BLOCK) break;
+          if (phi && (x1 + 1 - x0 + 2) * (H + 2) > GAS_MAP_SLOTS) break;
+          inner = more;
+          ++x1;
+        }
+        const int W = x1 - x0, Wp = W + 2;
+        const int first = (int)gas_list.size();
+        for (int y = y0; y < y1; ++y)
+          for (int x = x0; x < x1; ++x)
+            if (G.cls[x + nx * y] == GAS) {
+              const bool near_x = G.px && (x < GHOST || x >= nx - GHOST);
+              const bool near_y = G.py && (y < GHOST || y >= ny - GHOST);
+              const bool outlet = x + 1 == nx - 1 && G.cls[x + 1 + nx * y] == OUTLET;
+              const int aux = (x + nx * y) | (outlet ? GAS_AUX_OUTLET : 0) | (near_x || near_y ? GAS_AUX_GHOST : 0);
+              push_entry(x, y, aux, phi ? (x - x0 + 1) + (y - y0 + 1) * Wp : 0);
+            }
+        const int n_int = (int)gas_list.size() - first;
+        if (phi) {
+          for (int x = x0; x < x1; ++x) {
+            if (is_gas(x, y0 - 1) && is_gas(x, y0)) push_entry(x, y0 - 1, 0, x - x0 + 1);
+            if (is_gas(x, y1) && is_gas(x, y1 - 1)) push_entry(x, y1, 0, (x - x0 + 1) + (H + 1) * Wp);
+          }
+          for (int y = y0; y < y1; ++y) {
+            if (is_gas(x0 - 1, y) && is_gas(x0, y)) push_entry(x0 - 1, y, 0, (y - y0 + 1) * Wp);
+            if (is_gas(x1, y) && is_gas(x1 - 1, y)) push_entry(x1, y, 0, (W + 1) + (y - y0 + 1) * Wp);
+          }
+        }
+        const int n_tot = (int)gas_list.size() - first;
+        if (n_int > 0) blocks.push_back(make_int4(0, first, (n_int << 16) | n_tot, Wp));
+        else {
+          gas_list.resize(first);
+          gas_slot.resize(first);
+        }
+        x0 = x1;
+      }
+      chunks(wall_row[y0], wall_row[y1]);
     }
-    chunks(1, (int)walls.size(), (int)solid_list.size());
+    chunks((int)walls.size(), (int)solid_list.size());
   }
+  P.n_gas = h->counts[GAS];
   P.n_blocks = (int)blocks.size();
   h->blocks_host = blocks;
   P.ns = ns;
@@ -580,9 +678,8 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   ALLOC(S.code, uint32_t, P.plane);
   ALLOC(S.solid_list, int32_t, std::max<size_t>(solid_list.size(), 1));
   ALLOC(S.gas_list, int2, std::max<size_t>(gas_list.size(), 1));
+  ALLOC(S.gas_slot, uint16_t, std::max<size_t>(gas_slot.size(), 1));
   ALLOC(S.blocks, int4, std::max<size_t>(blocks.size(), 1));
-  ALLOC(S.F[0], float, (size_t)(ns + 1) * P.plane);
-  ALLOC(S.F[1], float, (size_t)(ns + 1) * P.plane);
   ALLOC(S.mom, float, (size_t)(ns + 3) * n);
   ALLOC(S.Tgas, float, 2 * (size_t)n);
   ALLOC(S.snap, float, (size_t)(ns + 4) * n);
@@ -609,6 +706,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
     e = cudaMemcpyAsync(S.blocks, blocks.data(), sizeof(int4) * blocks.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && !gas_list.empty())
     e = cudaMemcpyAsync(S.gas_list, gas_list.data(), sizeof(int2) * gas_list.size(), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess && !gas_slot.empty())
+    e = cudaMemcpyAsync(S.gas_slot, gas_slot.data(), sizeof(uint16_t) * gas_slot.size(), cudaMemcpyHostToDevice,
                         h->stream);
   if (e == cudaSuccess && !wall_u.empty())
     e = cudaMemcpyAsync(S.wall_u, wall_u.data(), sizeof(float2) * wall_u.size(), cudaMemcpyHostToDevice, h->stream);
@@ -696,6 +796,31 @@ fdlbm_status read_pop_energy(fdlbm_handle* h, double* out) {
 
 fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f);
 
+// Initial fields the equilibrium can represent: mole fractions >= 0 summing to 1, and a
+// positive rest factor 1 - M_j u_a^2 - T on every axis for the heaviest species (Eq.
+// eq_state_pop; T and u in lattice units).
+fdlbm_status check_initial_state(const fdlbm_handle* h, const std::vector<double>& X, const std::vector<double>& u,
+                                 const std::vector<double>& T, long n, int dim) {
+  float Mmax = 0.f;
+  for (int j = 0; j < h->ns; ++j) Mmax = std::max(Mmax, h->P.M[j]);
+  for (long k = 0; k < n; ++k) {
+    double sx = 0.0;
+    for (int j = 0; j < h->ns; ++j) {
+      const double x = X[(size_t)j * n + k];
+      if (!(x >= 0.0)) return fail(FDLBM_EINVAL, "initial mole fraction %d at node %ld is negative", j, k);
+      sx += x;
+    }
+    if (std::fabs(sx - 1.0) > 1e-6) return fail(FDLBM_EINVAL, "initial mole fractions at node %ld sum to %.9g", k, sx);
+    for (int a = 0; a < dim; ++a) {
+      const double ua = u[(size_t)a * n + k];
+      if (!(1.0 - double(Mmax) * ua * ua - T[k] > 0.0))
+        return fail(FDLBM_EINVAL, "initial state at node %ld outside the equilibrium's range: "
+                    "1 - M u^2 - T = %.6g <= 0", k, 1.0 - double(Mmax) * ua * ua - T[k]);
+    }
+  }
+  return FDLBM_OK;
+}
+
 fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
   if (h->dim == 3) return upload_and_init3(h, f);
   const int n = h->nx * h->ny, ns = h->ns;
@@ -710,6 +835,7 @@ fdlbm_status upload_and_init(fdlbm_handle* h, const fdlbm_fields* f) {
     if (f && f->C) C[k] = f->C[k];
     if (!(T[k] > 0) || !(C[k] > 0)) return fail(FDLBM_EINVAL, "initial T and C must be positive (node %d)", k);
   }
+  if (fdlbm_status st = check_initial_state(h, X, u, T, n, 2); st != FDLBM_OK) return st;
   std::vector<double> inlet(h->inlet_u);
   inlet.insert(inlet.end(), h->X_inlet.begin(), h->X_inlet.end());
   inlet.push_back(h->T_inlet_lat);
@@ -945,6 +1071,19 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
   }
   gas_z[nz] = (int)gcount;
   wall_z[nz] = (int)walls.size();
+  if (opts && opts->strict_geometry)
+    for (long k = 0; k < (long)n; ++k) {
+      const uint64_t w = code[k];
+      const uint32_t c = node_class3(w);
+      if (c != GAS && c != WALL) continue;
+      for (int i = 1; i < Q19; ++i) {
+        const uint32_t st = stencil_of3(w, i);
+        if (st == ST_NONE || st == ST_LIN_S0 || st == ST_LIN_S2)
+          return bail(fail(FDLBM_EGEOM, "strict geometry: %s node (%ld,%ld,%ld) pulls direction %d without a "
+                           "quadratic stencil (concave corner or narrow gap)", c == GAS ? "gas" : "wall",
+                           k % nx, (k / nx) % ny, k / ((long)nx * ny), i));
+      }
+    }
   std::vector<int32_t> solid_list(walls);
   solid_list.insert(solid_list.end(), solids.begin(), solids.end());
 
@@ -1086,6 +1225,7 @@ fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f) {
     if (f && f->C) C[k] = f->C[k];
     if (!(T[k] > 0) || !(C[k] > 0)) return fail(FDLBM_EINVAL, "initial T and C must be positive (node %ld)", k);
   }
+  if (fdlbm_status st = check_initial_state(h, X, u, T, n, 3); st != FDLBM_OK) return st;
   // inlet: X_inlet[ns], T_inlet (lattice), u_inlet (plug)
   std::vector<double> inlet(h->X_inlet);
   inlet.push_back(h->T_inlet_lat);
@@ -1153,14 +1293,20 @@ fdlbm_status fdlbm_set_fields(fdlbm_handle* h, const fdlbm_fields* f) {
 }
 
 fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device) {
+  return fdlbm_moments_ex(h, 0u, dst, dst_on_device);
+}
+
+fdlbm_status fdlbm_moments_ex(fdlbm_handle* h, unsigned flags, float* dst, int dst_on_device) {
   if (!h || !dst) return fail(FDLBM_EINVAL, "bad handle or destination");
+  if (flags & ~unsigned(FDLBM_MOMENTS_T_DEVIATION)) return fail(FDLBM_EINVAL, "unknown moments flags 0x%x", flags);
+  const bool t_dev = (flags & FDLBM_MOMENTS_T_DEVIATION) != 0;
   DeviceGuard guard(h->device);
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
   const size_t count = (size_t)(2 * h->ns + 2 + h->dim) * h->nx * h->ny * h->nz;
   auto out = [&](float* d) {
-    return h->dim == 3 ? launch_moments_out3(h->P, h->S, h->cur, d, h->stream)
-                       : launch_moments_out(h->P, h->S, h->cur, d, h->stream);
+    return h->dim == 3 ? launch_moments_out3(h->P, h->S, h->cur, d, t_dev, h->stream)
+                       : launch_moments_out(h->P, h->S, h->cur, d, t_dev, h->stream);
   };
   if (dst_on_device) {
     CK(out(dst), "moments output");
@@ -1359,7 +1505,6 @@ std::vector<std::pair<void*, size_t>> ck_buffers(fdlbm_handle* h) {
   const DevParams& P = h->P;
   const size_t n = (size_t)P.n, ns = (size_t)P.ns, plane = (size_t)P.plane;
   return {{h->S.h[h->cur], pop_bytes_per_value(P.storage) * ns * Q * plane},
-          {h->S.F[h->cur], sizeof(float) * (1 + ns) * plane},
           {h->S.Ts[h->cur], sizeof(float) * n},
           {h->S.Tgas + (size_t)h->cur * n, sizeof(float) * n},
           {h->S.mom, sizeof(float) * (ns + 3) * n},
@@ -1571,7 +1716,8 @@ fdlbm_status batch_upload(fdlbm_batch* b) {
     mem[i] = make_int2(h->cur, int(uint32_t(h->steps)));
     for (size_t q = 0; q < h->blocks_host.size(); ++q) {
       const int4 d = h->blocks_host[q];
-      blocks.push_back(make_int4(int(2 * i) + d.x, d.y, d.z, int(q)));
+      // gas tiles keep their map row stride; solid blocks take their ledger slot
+      blocks.push_back(make_int4(int(2 * i) + d.x, d.y, d.z, d.x == 0 ? d.w : int(q)));
     }
   }
   b->n_blocks = (int)blocks.size();

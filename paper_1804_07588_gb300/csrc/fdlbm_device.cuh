@@ -404,62 +404,109 @@ __device__ __forceinline__ void flag_bad(int* flags, const Mom<NS>& m, float T) 
 }
 
 // ---------------------------------------------------------------------------------------
-// Gas kernel
+// Gas tiles
 // ---------------------------------------------------------------------------------------
-// MODE 0: full step (collide, write populations and this step's moment field).
-// MODE 1: moments only (recomputes the pre-collision moments of the step that read
-// src / Fsrc into mom[] at compact indices; writes nothing else).
-// Moment field F: [1 + NS][plane]: dTg and K_j = kcoef_j C_j T_g of every gas node.
+// A gas block is a tile: the gas nodes of a band of rows and a range of columns (its
+// interior, row-major), followed by the gas nodes of the one-node ring around it that
+// are axis neighbours of interior gas nodes (its halo). Descriptor {role 0, first list
+// entry, interior count << 16 | total count, map row stride}; gas_slot holds each
+// entry's position in the tile's moment map (row stride Wp, the ring at the edges).
+//
+// Phase 1, every entry: pull streaming with the off-lattice interpolation (Sec. 4.2) into
+// the thread's shared-memory column, moments (Eq. moments_of_g), and T_g and
+// K_j = kcoef_j C_j T_g into the map. Phase 2, after a block barrier, interior entries
+// only: divergence of the energy-correction flux K_j grad T_g on the 4 axis neighbours
+// from the map, i.e. from the moments of the current time level (reading R8), the
+// two-step collision (Eq. final_kinetic_equation), the outlet equilibrium and the
+// streaming stores.
+// MODE 0: full step. MODE 1: moments only (the pre-collision moments of the step that
+// reads src into mom[] at compact indices; nothing else is written).
 // LT: relaxation times updated per node from its pulled densities and g-temperature
 // (Sec. 3, Eqs. tau1s with Wilke's rule, tau2_approx_text, D_j_text); they also enter
-// K_j, so the lagged field carries each node's own tau1.
+// K_j.
+
 template <class PT, int NS, bool PHI, int MODE, bool LT = false, bool DET = false>
-__device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
-                                         const uint32_t* __restrict__ code, int k, int aux,
-                                         const float* __restrict__ Fsrc, float* __restrict__ Fdst,
+__device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
+                                         const uint32_t* __restrict__ code, const int2* __restrict__ gas_list,
+                                         const uint16_t* __restrict__ gas_slot, const int4 d,
                                          float* __restrict__ mom, float* __restrict__ Tgas, int* __restrict__ flags,
-                                         float* __restrict__ s_h, int tid, uint32_t step, Acct* ac = nullptr) {
-  const uint32_t cw = __ldg(code + k);
+                                         float* __restrict__ smem, uint32_t step, Acct* ac = nullptr) {
+  const int tid = threadIdx.x;
+  const int n_tot = d.z & 0xFFFF, n_int = d.z >> 16, Wp = d.w;
+  float* s_h = smem;                                  // [NS Q][GB] pulled populations
+  float* s_m = s_h + NS * Q * GB;                     // [NS][GB]; with LT then tau1, tau2
+  float* s_map = s_m + (LT ? 3 : 1) * NS * GB;        // [1 + NS][GAS_MAP_SLOTS]: dTg, K_j
+  uint32_t cw = 0;
+  int k = 0, aux = 0, slot = 0;
+  Acc<NS> acc;
+  Mom<NS> m;
+  float t1l[NS], t2l[NS];
+  if (tid < n_tot) {
+    const int2 g = __ldg(gas_list + d.y + tid);
+    k = g.x;
+    aux = g.y;
+    if (PHI) slot = __ldg(gas_slot + d.y + tid);
+    cw = __ldg(code + k);
+    issue_pulls<PT, NS>(P, src, k, s_h, tid);
+    cp_async_wait_all();
+    Acct halo_acct{0.0, 0.0, 0.0, 0.0};  // halo entries are counted by their own tile
+    interp_node<PT, NS, DET>(P, src, code, k, cw, acc, s_h, tid, tid < n_int ? ac : &halo_acct);
+    finish_moments<NS>(P, acc, m);
+    // Local relaxation times: tau1_j = mu_j / (C T sum_k X_k phi_jk), tau2_j = rho_j D_j /
+    // (X_j C T) = M_j (1 - Y_j) / (T sum_{k != j} X_k / D_jk), T the g-temperature.
+    if constexpr (LT) {
+      const float Tg = P.Tref + m.dTg;
+      const float iC = 1.f / m.C;
+      float X[NS];
+#pragma unroll
+      for (int j = 0; j < NS; ++j) X[j] = (P.rref[j] + m.drho[j]) * P.invM[j] * iC;
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        float sphi = 0.f, sd = 0.f;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          sphi = fmaf(X[q], P.phi_w[j][q], sphi);
+          sd = fmaf(X[q], P.invD[j][q], sd);
+        }
+        t1l[j] = P.mu_l[j] / (m.C * Tg * sphi);
+        t2l[j] = P.M[j] * (1.f - (P.rref[j] + m.drho[j]) / m.r) / (Tg * sd);
+      }
+    }
+    if (PHI) {
+      s_map[slot] = m.dTg;
+#pragma unroll
+      for (int j = 0; j < NS; ++j)
+        s_map[(1 + j) * GAS_MAP_SLOTS + slot] = (LT ? P.kcoef0[j] * t1l[j] : P.kcoef[j]) *
+                                                ((P.rref[j] + m.drho[j]) * P.invM[j]) * (P.Tref + m.dTg);
+    }
+  }
+  if (PHI) __syncthreads();
+  if (tid >= n_int) return;
   const int n = aux & GAS_AUX_N;
   const uint32_t seed = sizeof(PT) == 4 ? 0U : node_seed(k, step);
 
-  Acc<NS> acc;
-  Mom<NS> m;
-  if (MODE == 0)
-    issue_pulls<PT, NS>(P, src, k, s_h, tid);
-  else
-    pull_node<PT, NS, false>(P, src, k, cw, acc, s_h, tid);
-
-  // Divergence of the energy-correction flux K_j grad T on the 4 axis neighbours, from
-  // the moment field of the previous time level (reading R8); faces to non-gas nodes
-  // carry no flux. Independent of this step's populations: computed while the pulls
-  // are in flight.
+  // Divergence of the energy-correction flux K_j grad T on the 4 axis neighbours (+x, +y,
+  // -x, -y: map slots +1, +Wp, -1, -Wp); faces to non-gas nodes carry no flux.
   float divq[NS];
   float sdq = 0.f;
 #pragma unroll
   for (int j = 0; j < NS; ++j) divq[j] = 0.f;
   if (PHI) {
-    const float Tc = __ldg(Fsrc + k);
+    const float Tc = s_map[slot];
     float Kc[NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) Kc[j] = __ldg(Fsrc + (long long)(1 + j) * P.plane + k);
+    for (int j = 0; j < NS; ++j) Kc[j] = s_map[(1 + j) * GAS_MAP_SLOTS + slot];
 #pragma unroll
-    for (int d = 1; d <= 4; ++d) {
-      if (!((cw >> (NBR_GAS_SHIFT + d - 1)) & 1u)) continue;
-      const int kn = k + EX(d) + EY(d) * P.pitch;
-      const float dTn = __ldg(Fsrc + kn) - Tc;
+    for (int dd = 1; dd <= 4; ++dd) {
+      if (!((cw >> (NBR_GAS_SHIFT + dd - 1)) & 1u)) continue;
+      const int sn = slot + (dd == 1 ? 1 : dd == 2 ? Wp : dd == 3 ? -1 : -Wp);
+      const float dTn = s_map[sn] - Tc;
 #pragma unroll
-      for (int j = 0; j < NS; ++j)
-        divq[j] = fmaf(0.5f * (Kc[j] + __ldg(Fsrc + (long long)(1 + j) * P.plane + kn)), dTn, divq[j]);
+      for (int j = 0; j < NS; ++j) divq[j] = fmaf(0.5f * (Kc[j] + s_map[(1 + j) * GAS_MAP_SLOTS + sn]), dTn, divq[j]);
     }
 #pragma unroll
     for (int j = 0; j < NS; ++j) sdq += divq[j];
   }
-  if (MODE == 0) {
-    cp_async_wait_all();
-    interp_node<PT, NS, DET>(P, src, code, k, cw, acc, s_h, tid, ac);
-  }
-  finish_moments<NS>(P, acc, m);
 
   const float ux = m.jx / m.r, uy = m.jy / m.r;
   const float dT = m.dTg + sdq / (4.f * m.C);
@@ -469,41 +516,12 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
     for (int j = 0; j < NS; ++j) mom[(long long)j * P.n + n] = P.rref[j] + m.drho[j];
     mom[(long long)NS * P.n + n] = ux;
     mom[(long long)(NS + 1) * P.n + n] = uy;
-    mom[(long long)(NS + 2) * P.n + n] = T;
+    mom[(long long)(NS + 2) * P.n + n] = dT;  // T - T_ref
     return;
   }
   Ghost gh{0, 0};
   if (aux & GAS_AUX_GHOST) gh = ghost_of(P, n % P.nx, n / P.nx);
-  // Local relaxation times: tau1_j = mu_j / (C T sum_k X_k phi_jk), tau2_j = rho_j D_j /
-  // (X_j C T) = M_j (1 - Y_j) / (T sum_{k != j} X_k / D_jk), T the g-temperature.
-  float t1l[NS], t2l[NS];
-  if constexpr (LT) {
-    const float Tg = P.Tref + m.dTg;
-    const float iC = 1.f / m.C;
-    float X[NS];
-#pragma unroll
-    for (int j = 0; j < NS; ++j) X[j] = (P.rref[j] + m.drho[j]) * P.invM[j] * iC;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      float sphi = 0.f, sd = 0.f;
-#pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        sphi = fmaf(X[q], P.phi_w[j][q], sphi);
-        sd = fmaf(X[q], P.invD[j][q], sd);
-      }
-      t1l[j] = P.mu_l[j] / (m.C * Tg * sphi);
-      t2l[j] = P.M[j] * (1.f - (P.rref[j] + m.drho[j]) / m.r) / (Tg * sd);
-    }
-  }
-  if (PHI) {
-    store_with_ghosts(Fdst, k, gh, m.dTg);
-#pragma unroll
-    for (int j = 0; j < NS; ++j)
-      store_with_ghosts(Fdst + (long long)(1 + j) * P.plane, k, gh,
-                        (LT ? P.kcoef0[j] * t1l[j] : P.kcoef[j]) * ((P.rref[j] + m.drho[j]) * P.invM[j]) *
-                            (P.Tref + m.dTg));
-  }
-  if (Tgas != nullptr) Tgas[n] = T;
+  if (Tgas != nullptr) Tgas[n] = dT;  // T - T_ref
   flag_bad<NS>(flags, m, T);
 
   // Corrective diffusion velocity (reading R3: weights 1/(tau2 + 1/2)).
@@ -520,10 +538,9 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   const float Ucx = ncx * iden, Ucy = ncy * iden;
 
   // The species loop below is not unrolled (keeps the live register set small). Its
-  // inputs: the lagged divergence, parked in this thread's shared-memory column, and the
+  // inputs: the divergence, parked in this thread's shared-memory column, and the
   // species' density and momentum, formed again from the pulled values in the pull's
   // order (the same FP32 sums).
-  float* s_m = s_h + NS * Q * GB;  // [NS][GB]; with LT then tau1 [NS][GB], tau2 [NS][GB]
 #pragma unroll
   for (int j = 0; j < NS; ++j) s_m[j * GB + tid] = divq[j];
   if constexpr (LT) {
@@ -652,24 +669,9 @@ __device__ __forceinline__ void gas_node(const DevParams& P, const PT* __restric
   }
 }
 
-template <class PT, int NS, bool PHI, int MODE>
-__global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) gas_kernel(DevParams P, const PT* __restrict__ src,
-                                                                 PT* __restrict__ dst,
-                                                                 const uint32_t* __restrict__ code,
-                                                                 const int2* __restrict__ gas_list,
-                                                                 const float* __restrict__ Fsrc,
-                                                                 float* __restrict__ Fdst, float* __restrict__ mom,
-                                                                 float* __restrict__ Tgas, int* __restrict__ flags) {
-  extern __shared__ float smem[];
-  const int t = blockIdx.x * GB + threadIdx.x;
-  if (t >= P.n_gas) return;
-  const int2 g = __ldg(gas_list + t);
-  gas_node<PT, NS, PHI, MODE>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, mom, Tgas, flags, smem, threadIdx.x, 0U);
-}
-
-template <int NS, int MODE, bool LT = false>
+template <int NS, bool LT = false>
 size_t gas_smem_bytes() {
-  return sizeof(float) * (MODE == 0 ? (NS * Q + (LT ? 3 : 1) * NS) * GB : 1);
+  return sizeof(float) * ((NS * Q + (LT ? 3 : 1) * NS) * GB + (1 + NS) * GAS_MAP_SLOTS);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -729,6 +731,22 @@ __device__ __forceinline__ float wmove(int i, float sM, float M, float2 u, float
   return fx * fy;
 }
 
+// Deviations of the emitted shapes from the rest weights W0_i at T_ref, formed from the
+// wall temperature's deviation d = T_w - T_ref: with 1D factors f = f0 + df, the product
+// f_x f_y - f0_x f0_y = f0_x df_y + df_x f0_y + df_x df_y.
+__device__ __forceinline__ float dwrest(const DevParams& P, int i, float d) {
+  const float fx0 = EX(i) == 0 ? 1.f - P.Tref : 0.5f * P.Tref, fy0 = EY(i) == 0 ? 1.f - P.Tref : 0.5f * P.Tref;
+  const float dfx = EX(i) == 0 ? -d : 0.5f * d, dfy = EY(i) == 0 ? -d : 0.5f * d;
+  return fmaf(fx0, dfy, dfx * (fy0 + dfy));
+}
+__device__ __forceinline__ float dwmove(const DevParams& P, int i, float sM, float M, float2 u, float d) {
+  const float fx0 = EX(i) == 0 ? 1.f - P.Tref : 0.5f * P.Tref, fy0 = EY(i) == 0 ? 1.f - P.Tref : 0.5f * P.Tref;
+  const float mx = M * u.x * u.x, my = M * u.y * u.y;
+  const float dfx = EX(i) == 0 ? -(mx + d) : 0.5f * (float(EX(i)) * sM * u.x + mx + d);
+  const float dfy = EY(i) == 0 ? -(my + d) : 0.5f * (float(EY(i)) * sM * u.y + my + d);
+  return fmaf(fx0, dfy, dfx * (fy0 + dfy));
+}
+
 template <class PT, int NS, bool DET = false>
 __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restrict__ src, PT* __restrict__ dst,
                                            const float* __restrict__ Ts_src, float* __restrict__ Ts_dst,
@@ -762,7 +780,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
         continue;
       }
       if (Tgas != nullptr && node_class(__ldg(code + k + ox + oy * P.pitch)) == GAS)
-        gas_term += Tgas[nb] - (P.Tref + Tx);
+        gas_term += Tgas[nb] - Tx;
     }
     float Tn = fmaf(P.alpha_s, lap, Tx);
     if (node_class(cw) == WALL) {
@@ -772,13 +790,18 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
       uint32_t arr = 0;
       for (int i = 1; i < Q; ++i)
         if (stencil_of(cw, i) != ST_NOT_ARRIVAL) arr |= 1u << i;
-      float B = 0.f;
+      // Emitted shape at the wall temperature, W0_i + dW_i, with dW_i formed from the
+      // deviation Tx so that FP32 keeps its digits; B = sum of the shape, dB of dW.
+      float B = 0.f, dB = 0.f;
       for (int i = 1; i < Q; ++i)
-        if (arr & (1u << OPP(i))) B += wrest(i, Tw);
-      float A[NS], rw[NS], mj[NS];
-      float Earr = 0.f;
+        if (arr & (1u << OPP(i))) {
+          B += wrest(i, Tw);
+          dB += dwrest(P, i, Tx);
+        }
+      float A[NS], Ah[NS], rw[NS], mj[NS];
+      float Earr = 0.f, W0arr = 0.f;
 #pragma unroll
-      for (int j = 0; j < NS; ++j) A[j] = 0.f;
+      for (int j = 0; j < NS; ++j) Ah[j] = 0.f;
       // Populations arriving from the gas: all lanes of a warp step through the directions
       // together, so that their loads of one direction plane coalesce; branch-free
       // stencils, loads of all species issued together.
@@ -789,6 +812,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
         const StencilCoef sc = stencil_coef(stencil_of(cw, i));
         const int dA = sc.mA * off, dB = sc.mB * off;
         const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
+        W0arr += P.W0[i];
         float v1[NS], vA[NS], vB[NS];
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
@@ -810,31 +834,38 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
             acc[LG_DINT] += e * (double(v) - double(v1[j]));
             acc[LG_QWALLX] -= e * (double(v) + double(P.rref[j]) * double(P.W0[i]));
           }
-          v += P.rref[j] * P.W0[i];
-          A[j] += v;
+          Ah[j] += v;  // deviations; the rest part rref W0 is added below
           Earr = fmaf(e2h * P.c2[j], v, Earr);
         }
       }
       // normalisation of the emitted shape: 1 / B, per species for a moving wall
-      float iBj[NS];
+      float iBj[NS], dBj[NS];
       const bool moving = wall_u != nullptr;
       float2 uw = make_float2(0.f, 0.f);
       if (moving) {
         uw = wall_u[idx];
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          float Bj = 0.f;
+          float Bj = 0.f, dbj = 0.f;
           for (int i = 1; i < Q; ++i)
-            if (arr & (1u << OPP(i))) Bj += wmove(i, P.sqrtM[j], P.M[j], uw, Tw);
+            if (arr & (1u << OPP(i))) {
+              Bj += wmove(i, P.sqrtM[j], P.M[j], uw, Tw);
+              dbj += dwmove(P, i, P.sqrtM[j], P.M[j], uw, Tx);
+            }
           iBj[j] = 1.f / Bj;
+          dBj[j] = dbj;
         }
       } else {
         const float iB = 1.f / B;
 #pragma unroll
-        for (int j = 0; j < NS; ++j) iBj[j] = iB;
+        for (int j = 0; j < NS; ++j) {
+          iBj[j] = iB;
+          dBj[j] = dB;
+        }
       }
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
+        A[j] = fmaf(P.rref[j], W0arr, Ah[j]);
         rw[j] = A[j] * iBj[j];
         mj[j] = 0.f;
       }
@@ -881,30 +912,34 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
       const Ghost gh = ghost_of(P, x, y);
       const uint32_t seed = sizeof(PT) == 4 ? 0U : node_seed(k, step);
       float Eout = 0.f;
-      float scale[NS];
+      // emitted deviation dscale W0_i + (rref + dscale) dW_i with dscale = (A + m) / B -
+      // rref = (sum of arrived deviations - rref dB + m) / B: the rest parts rref W0 of
+      // the arrivals and of the emissions cancel (the two direction sets mirror each
+      // other), so only small quantities are rounded.
+      float dsc[NS];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) scale[j] = (A[j] + mj[j]) * iBj[j];
+      for (int j = 0; j < NS; ++j) dsc[j] = (Ah[j] - P.rref[j] * dBj[j] + mj[j]) * iBj[j];
       // Emissions towards the gas neighbours (the directions opposite to the arrivals).
 #pragma unroll 1
       for (int i = 1; i < Q; ++i) {
         if (!(arr & (1u << OPP(i)))) continue;
-        const float wr = wrest(i, Tw);
+        const float dwr = dwrest(P, i, Tx);
         const float e2h = 0.5f * float(EX(i) * EX(i) + EY(i) * EY(i));
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-          const float w = (moving ? wmove(i, P.sqrtM[j], P.M[j], uw, Tw) : wr) * scale[j];
-          const float dv = w - P.rref[j] * P.W0[i];
+          const float dw = moving ? dwmove(P, i, P.sqrtM[j], P.M[j], uw, Tx) : dwr;
+          const float dv = fmaf(dsc[j], P.W0[i], (P.rref[j] + dsc[j]) * dw);
           pop_store_ghosts(dst + (long long)(j * Q + i) * P.plane, k, gh, dv, P.hs[j], seed, j * Q + i);
           if constexpr (DET)  // FP32 storage: dv is the value stored
             acc[LG_QWALLX] += eps_weight(P, j, EX(i) * EX(i) + EY(i) * EY(i)) *
                               (double(dv) + double(P.rref[j]) * double(P.W0[i]));
-          Eout = fmaf(e2h * P.c2[j], w, Eout);
+          Eout = fmaf(e2h * P.c2[j], dv, Eout);
         }
       }
       float q = 0.f;
       if (cat)
         for (int r = 0; r < P.nr; ++r) q += P.heat[r] * rate[r];
-      const float dE = Eout - Earr;
+      const float dE = Eout - Earr;  // energy the wall put into the gas (deviation sums)
       const float couple = P.coupling == FDLBM_COUPLING_PAPER ? P.kappa_f * gas_term : -dE;
       Tn += (q + couple) * P.inv_rhocp_s;
       acc[LG_QRXN] += q;
@@ -941,16 +976,17 @@ __device__ __forceinline__ void ledger_block_store(double (&acc)[LG_COUNT], doub
   }
 }
 
-// One time step in one launch. Every block takes a role from its descriptor {role,
-// first list entry, count}: gas blocks run the gas update of consecutive gas nodes,
-// solid blocks the wall + FD update of consecutive solid nodes. The host interleaves
-// the descriptors by row bands so that wall blocks follow the gas blocks of the same
-// rows and find their neighbours' populations in L2.
-template <class PT, int NS, bool PHI, bool LT = false, bool DET = false>
+// One time step in one launch. Every block takes a role from its descriptor: gas blocks
+// run a gas tile (its interior and halo entries of the gas list), solid blocks {1, first
+// list entry, count} the wall + FD update of consecutive solid nodes. The host
+// interleaves the descriptors by row bands so that wall blocks follow the gas tiles of
+// the same rows and find their neighbours' populations in L2. MODE 1: only the gas tiles
+// run, recomputing the pre-collision moments into mom.
+template <class PT, int NS, bool PHI, bool LT = false, bool DET = false, int MODE = 0>
 __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
     DevParams P, const PT* __restrict__ src, PT* __restrict__ dst, const uint32_t* __restrict__ code,
-    const int2* __restrict__ gas_list, const int32_t* __restrict__ solid_list, const int4* __restrict__ blocks,
-    const float* __restrict__ Fsrc, float* __restrict__ Fdst, const float* __restrict__ Ts_src,
+    const int2* __restrict__ gas_list, const uint16_t* __restrict__ gas_slot, const int32_t* __restrict__ solid_list,
+    const int4* __restrict__ blocks, float* __restrict__ mom, const float* __restrict__ Ts_src,
     float* __restrict__ Ts_dst, const float* __restrict__ Tgas_src, float* __restrict__ Tgas_dst,
     double* __restrict__ ledger, int* __restrict__ flags, float* __restrict__ rw_prev, uint32_t step,
     const float2* __restrict__ wall_u) {
@@ -958,13 +994,10 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
   const int4 d = __ldg(blocks + blockIdx.x);
   const int tid = threadIdx.x;
   if (d.x == 0) {
-    if constexpr (DET) {
+    if constexpr (DET && MODE == 0) {
       Acct ac{0.0, 0.0, 0.0, 0.0};
-      if (tid < d.z) {
-        const int2 g = __ldg(gas_list + d.y + tid);
-        gas_node<PT, NS, PHI, 0, LT, true>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid,
-                                           step, &ac);
-      }
+      gas_tile<PT, NS, PHI, 0, LT, true>(P, src, dst, code, gas_list, gas_slot, d, nullptr, Tgas_dst, flags, smem,
+                                         step, &ac);
       double acc[LG_COUNT];
 #pragma unroll
       for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
@@ -973,19 +1006,20 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel(
       acc[LG_DINT] = ac.dint;
       acc[LG_DCOL] = ac.dcol;
       ledger_block_store<LG_COUNT>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
-    } else if (tid < d.z) {
-      const int2 g = __ldg(gas_list + d.y + tid);
-      gas_node<PT, NS, PHI, 0, LT>(P, src, dst, code, g.x, g.y, Fsrc, Fdst, nullptr, Tgas_dst, flags, smem, tid, step);
+    } else {
+      gas_tile<PT, NS, PHI, MODE, LT>(P, src, dst, code, gas_list, gas_slot, d, mom, Tgas_dst, flags, smem, step);
     }
     return;
   }
-  double acc[LG_COUNT];
+  if constexpr (MODE == 0) {
+    double acc[LG_COUNT];
 #pragma unroll
-  for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
-  if (tid < d.z)
-    solid_node<PT, NS, DET>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
-                            d.y + tid, step, wall_u);
-  ledger_block_store<DET ? LG_COUNT : LG_BASIC>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+    for (int q = 0; q < LG_COUNT; ++q) acc[q] = 0.0;
+    if (tid < d.z)
+      solid_node<PT, NS, DET>(P, src, dst, Ts_src, Ts_dst, code, Tgas_src, __ldg(solid_list + d.y + tid), acc, rw_prev,
+                              d.y + tid, step, wall_u);
+    ledger_block_store<DET ? LG_COUNT : LG_BASIC>(acc, ledger + (long long)blockIdx.x * LG_COUNT);
+  }
 }
 
 // Batched time step: several independent lattices (members of a batch) advance in one
@@ -1019,11 +1053,8 @@ __global__ void __launch_bounds__(GB, GAS_MIN_BLOCKS) step_kernel_batch(
   const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
   const int tid = threadIdx.x;
   if ((d.x & 1) == 0) {
-    if (tid < d.z) {
-      const int2 g = __ldg(S.gas_list + d.y + tid);
-      gas_node<PT, NS, PHI, 0>(P, hs, hd, S.code, g.x, g.y, S.F[src], S.F[dstb], nullptr,
-                               paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.flags, smem, tid, step);
-    }
+    gas_tile<PT, NS, PHI, 0>(P, hs, hd, S.code, S.gas_list, S.gas_slot, d, nullptr,
+                             paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.flags, smem, step);
     return;
   }
   double acc[LG_COUNT];
@@ -1047,7 +1078,6 @@ __device__ double wfac_d(int e, double v, double M, double T) {
 
 template <class PT>
 __global__ void init_kernel(DevParams P, PT* __restrict__ h0, PT* __restrict__ h1,
-                            float* __restrict__ F0, float* __restrict__ F1,
                             float* __restrict__ Ts0, float* __restrict__ Ts1, float* __restrict__ mom,
                             float* __restrict__ Tgas, const uint32_t* __restrict__ code,
                             const double* __restrict__ X, const double* __restrict__ u,
@@ -1062,7 +1092,6 @@ __global__ void init_kernel(DevParams P, PT* __restrict__ h0, PT* __restrict__ h
       h0[(long long)(j * Q + i) * P.plane + k] = pop_enc<PT>(0.f, 1.f);
       h1[(long long)(j * Q + i) * P.plane + k] = pop_enc<PT>(0.f, 1.f);
     }
-  for (int f = 0; f <= P.ns; ++f) F0[(long long)f * P.plane + k] = F1[(long long)f * P.plane + k] = 0.f;
   if (k >= P.pitch * (P.ny + 2 * P.yoff)) return;
   const int px = k % P.pitch, py = k / P.pitch;
   int x = px - P.xoff, y = py - P.yoff;
@@ -1101,28 +1130,12 @@ __global__ void init_kernel(DevParams P, PT* __restrict__ h0, PT* __restrict__ h
         h1[(long long)(j * Q + i) * P.plane + k] = v;
       }
     }
-    if (c == GAS) {
-      // Moment field of the time level before the first step: the initial fields.
-      F0[k] = F1[k] = float(T - Tref);
-      // K_j = kcoef_j C_j T; with local relaxation times kcoef0_j tau1_j of this node's
-      // initial composition and temperature (Eq. tau1s)
-      double Ct = 0.0, t1l[MAX_NS];
-      for (int j = 0; j < P.ns; ++j) Ct += C * Xn[j];
-      for (int j = 0; j < P.ns; ++j) {
-        double sphi = 0.0;
-        for (int q = 0; q < P.ns; ++q) sphi += (C * Xn[q] / Ct) * double(P.phi_w[j][q]);
-        t1l[j] = double(P.mu_l[j]) / (Ct * T * sphi);
-      }
-      for (int j = 0; j < P.ns; ++j)
-        F0[(long long)(1 + j) * P.plane + k] = F1[(long long)(1 + j) * P.plane + k] =
-            float((P.local_tau ? double(P.kcoef0[j]) * t1l[j] : double(P.kcoef[j])) * C * Xn[j] * T);
-    }
     if (c == GAS && real) {
       for (int j = 0; j < P.ns; ++j) mom[(long long)j * P.n + n] = float(C * Xn[j] * P.M[j]);
       mom[(long long)P.ns * P.n + n] = float(ux);
       mom[(long long)(P.ns + 1) * P.n + n] = float(uy);
-      mom[(long long)(P.ns + 2) * P.n + n] = float(T);
-      Tgas[n] = Tgas[P.n + n] = float(T);
+      mom[(long long)(P.ns + 2) * P.n + n] = float(T - Tref);
+      Tgas[n] = Tgas[P.n + n] = float(T - Tref);
     }
   } else if (c == WALL || c == SOLID) {
     const double Ts = Tsl[n];
@@ -1181,7 +1194,7 @@ __global__ void totals_kernel(DevParams P, const float* __restrict__ mom, const 
         C += rj / double(P.M[j]);
         r += rj;
       }
-      const double ux = mom[ns * N + n], uy = mom[(ns + 1) * N + n], T = mom[(ns + 2) * N + n];
+      const double ux = mom[ns * N + n], uy = mom[(ns + 1) * N + n], T = double(P.Tref) + mom[(ns + 2) * N + n];
       E = C * T + 0.5 * r * (ux * ux + uy * uy);
     } else if (c == WALL || c == SOLID) {
       H = double(P.rhocp_s) * (double(P.Tref) + double(Ts[n]));
@@ -1210,91 +1223,53 @@ __global__ void totals_kernel(DevParams P, const float* __restrict__ mom, const 
   }
 }
 
-template <class PT, int NS, bool PHI, int MODE>
-cudaError_t gas_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  if (P.n_gas <= 0) return cudaSuccess;
-  const size_t smem = gas_smem_bytes<NS, MODE>();
-  // Opt in to the dynamic shared memory once per device and instantiation.
-  static unsigned long long configured = 0;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 64 && !(configured & (1ull << dev))) {
-    e = cudaFuncSetAttribute(gas_kernel<PT, NS, PHI, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
-  const int dstb = 1 - src;
-  const int grid = (P.n_gas + GB - 1) / GB;
-  float* Tg = (MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER) ? S.Tgas + (long long)dstb * P.n : nullptr;
-  gas_kernel<PT, NS, PHI, MODE><<<grid, GB, smem, st>>>(P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.F[src], S.F[dstb],
-                                                    MODE == 1 ? S.mom : nullptr, Tg, S.flags);
-  return cudaGetLastError();
-}
-
-// Moments-only pass (the full step runs in step_kernel).
-template <class PT, int NS>
-cudaError_t gas_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  return P.energy_correction ? gas_launch<PT, NS, true, 1>(P, S, src, st) : gas_launch<PT, NS, false, 1>(P, S, src, st);
-}
-
-template <class PT>
-cudaError_t dispatch_gas(const DevParams& P, const DevState& S, int src, cudaStream_t st) {
-  switch (P.ns) {
-    case 1: return gas_ns<PT, 1>(P, S, src, st);
-    case 2: return gas_ns<PT, 2>(P, S, src, st);
-    case 3: return gas_ns<PT, 3>(P, S, src, st);
-    case 4: return gas_ns<PT, 4>(P, S, src, st);
-    case 5: return gas_ns<PT, 5>(P, S, src, st);
-    case 6: return gas_ns<PT, 6>(P, S, src, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <class PT, int NS, bool PHI, bool LT = false, bool DET = false>
+template <class PT, int NS, bool PHI, bool LT = false, bool DET = false, int MODE = 0>
 cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   if (P.n_blocks <= 0) return cudaSuccess;
-  const size_t smem = gas_smem_bytes<NS, 0, LT>();
+  const size_t smem = gas_smem_bytes<NS, LT>();
   static unsigned long long configured = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 64 && !(configured & (1ull << dev))) {
-    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI, LT, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(step_kernel<PT, NS, PHI, LT, DET, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
     if (e != cudaSuccess) return e;
     configured |= 1ull << dev;
   }
   const int dstb = 1 - src;
-  const bool paper = P.coupling == FDLBM_COUPLING_PAPER;
-  step_kernel<PT, NS, PHI, LT, DET><<<P.n_blocks, GB, smem, st>>>(
-      P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.solid_list, S.blocks, S.F[src], S.F[dstb], S.Ts[src], S.Ts[dstb],
-      paper ? S.Tgas + (long long)src * P.n : nullptr, paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger,
-      S.flags, S.rw, step, S.wall_u);
+  const bool paper = MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER;
+  step_kernel<PT, NS, PHI, LT, DET, MODE><<<P.n_blocks, GB, smem, st>>>(
+      P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.gas_slot, S.solid_list, S.blocks,
+      MODE == 1 ? S.mom : nullptr, S.Ts[src], S.Ts[dstb], paper ? S.Tgas + (long long)src * P.n : nullptr,
+      paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger, S.flags, S.rw, step, S.wall_u);
   return cudaGetLastError();
 }
 
 // Locally updated relaxation times and the exact-accounts step run the FP32 kernels
 // instantiated in fdlbm_local_tau.cu and fdlbm_ledger_detail.cu (the host rejects other
 // storage types).
-template <class PT, int NS>
+// MODE 1 is the moments-only pass (the pre-collision moments of the step that reads src).
+template <class PT, int NS, int MODE>
 cudaError_t step_ns(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   const bool phi = P.energy_correction != 0;
   if constexpr (sizeof(PT) == 4) {
-    if (P.ledger_detail) return launch_step_detail(P, S, src, st, step);
-    if (P.local_tau) return launch_step_local_tau(P, S, src, st, step);
+    if (MODE == 0 && P.ledger_detail) return launch_step_detail(P, S, src, st, step);
+    if (P.local_tau) return launch_step_local_tau(P, S, src, MODE == 1, st, step);
   }
-  return phi ? step_launch<PT, NS, true>(P, S, src, st, step) : step_launch<PT, NS, false>(P, S, src, st, step);
+  return phi ? step_launch<PT, NS, true, false, false, MODE>(P, S, src, st, step)
+             : step_launch<PT, NS, false, false, false, MODE>(P, S, src, st, step);
 }
 
-template <class PT>
+template <class PT, int MODE>
 cudaError_t dispatch_step(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step) {
   switch (P.ns) {
-    case 1: return step_ns<PT, 1>(P, S, src, st, step);
-    case 2: return step_ns<PT, 2>(P, S, src, st, step);
-    case 3: return step_ns<PT, 3>(P, S, src, st, step);
-    case 4: return step_ns<PT, 4>(P, S, src, st, step);
-    case 5: return step_ns<PT, 5>(P, S, src, st, step);
-    case 6: return step_ns<PT, 6>(P, S, src, st, step);
+    case 1: return step_ns<PT, 1, MODE>(P, S, src, st, step);
+    case 2: return step_ns<PT, 2, MODE>(P, S, src, st, step);
+    case 3: return step_ns<PT, 3, MODE>(P, S, src, st, step);
+    case 4: return step_ns<PT, 4, MODE>(P, S, src, st, step);
+    case 5: return step_ns<PT, 5, MODE>(P, S, src, st, step);
+    case 6: return step_ns<PT, 6, MODE>(P, S, src, st, step);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1331,7 +1306,7 @@ totals_partial_kernel(DevParams P, const float* __restrict__ mom, const PT* __re
         C += rj / double(P.M[j]);
         r += rj;
       }
-      const double ux = mom[ns * N + n], uy = mom[(ns + 1) * N + n], T = mom[(ns + 2) * N + n];
+      const double ux = mom[ns * N + n], uy = mom[(ns + 1) * N + n], T = double(P.Tref) + mom[(ns + 2) * N + n];
       E = C * T + 0.5 * r * (ux * ux + uy * uy);
     } else if (c == WALL || c == SOLID) {
       H = double(P.rhocp_s) * (double(P.Tref) + double(Ts[n]));
@@ -1365,7 +1340,7 @@ totals_partial_kernel(DevParams P, const float* __restrict__ mom, const PT* __re
 template <class PT, int NS, bool PHI>
 cudaError_t batch_launch(const BatchLaunch& B, cudaStream_t st) {
   if (B.n_blocks <= 0) return cudaSuccess;
-  const size_t smem = gas_smem_bytes<NS, 0>();
+  const size_t smem = gas_smem_bytes<NS>();
   static unsigned long long configured = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1403,7 +1378,7 @@ cudaError_t storage_init(const DevParams& P, const DevState& S, const double* X,
                          cudaStream_t st) {
   const double* X_inlet = inlet + P.ny;
   const long long nb = (P.plane + 255) / 256;
-  init_kernel<PT><<<(unsigned)nb, 256, 0, st>>>(P, (PT*)S.h[0], (PT*)S.h[1], S.F[0], S.F[1], S.Ts[0], S.Ts[1], S.mom,
+  init_kernel<PT><<<(unsigned)nb, 256, 0, st>>>(P, (PT*)S.h[0], (PT*)S.h[1], S.Ts[0], S.Ts[1], S.mom,
                                                S.Tgas, S.code, X, u, T_lat, Ts_lat, C, inlet, X_inlet,
                                                double(P.Tref));
   return cudaGetLastError();
@@ -1412,8 +1387,8 @@ cudaError_t storage_init(const DevParams& P, const DevState& S, const double* X,
 template <class PT>
 cudaError_t storage_step(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
                          uint32_t step) {
-  if (moments_only) return dispatch_gas<PT>(P, S, src, st);
-  return dispatch_step<PT>(P, S, src, st, step);
+  if (moments_only) return dispatch_step<PT, 1>(P, S, src, st, step);
+  return dispatch_step<PT, 0>(P, S, src, st, step);
 }
 
 template <class PT>

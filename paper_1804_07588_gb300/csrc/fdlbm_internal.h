@@ -73,6 +73,7 @@ struct DevParams {
   // steady-state residual references
   float Xin[MAX_NS];
   float Tin_lat;
+  float Tdev_off;       // float(T_ref) - T_inlet (lattice): the float reference's own rounding
   // D3Q19 lattice (dim 3): node (x, y, z) at (x + xoff) + (y + yoff) pitch + (z + zoff) slab
   int dim;              // 2 (D2Q9) or 3 (D3Q19)
   int nz, zoff, periodic_z;
@@ -95,9 +96,12 @@ struct DevState {
   float* Ts[2];         // solid temperature deviation from Tref, [n]
   uint32_t* code;       // node code words on the padded lattice, [plane]
   int32_t* solid_list;  // wall nodes first, then interior solid nodes (compact indices)
-  int2* gas_list;       // gas nodes, row-major: {padded index, aux} (aux: GAS_AUX_*)
-  float* F[2];          // moment fields [1 + ns][plane]: dTg, K_j (ping-pong with h)
-  int4* blocks;         // step-kernel block descriptors {role (0 gas, 1 solid), first, count, 0}
+  int2* gas_list;       // gas nodes {padded index, aux} (aux: GAS_AUX_*); D2Q9: per tile, its
+                        // interior row-major, then its halo
+  float* F[2];          // D3Q19: moment field [1 + ns][plane] of the current step: dTg, K_j
+  int4* blocks;         // step-kernel block descriptors: gas tiles {0, first, interior << 16 | total,
+                        // map row stride}, solid blocks {1, first, count, 0}
+  uint16_t* gas_slot;   // D2Q9: moment-map slot of every gas-list entry within its tile
   float* mom;           // moments of the last step: rho_j [ns], ux, uy, T(lattice) per node, [(ns+3)][n]
   float* Tgas;          // gas temperature (lattice) for the paper coupling, [2][n] ping-pong with h
   float* snap;          // residual snapshot [(ns + 4)][n]
@@ -135,6 +139,8 @@ cudaError_t launch_step(const DevParams& P, const DevState& S, int src, bool mom
                         cudaStream_t st, uint32_t step = 0);
 // Step-kernel block size: one gas, wall or solid node per thread.
 constexpr int STEP_BLOCK = 256;
+// Moment-map slots of one D2Q9 gas tile: the host keeps (columns + 2)(rows + 2) within it.
+constexpr int GAS_MAP_SLOTS = 640;
 // Second word of a gas-list entry: the compact lattice index n = x + nx y in the low 29
 // bits; GAS_AUX_GHOST marks a node (or its outlet neighbour) within GHOST of a periodic
 // face, which also writes ghost copies; GAS_AUX_OUTLET a node whose +x neighbour is an
@@ -145,7 +151,8 @@ constexpr int GAS_AUX_GHOST = 1 << 30;
 // Per-block ledger slots of the step kernel and their sum (LG_COUNT doubles into out).
 int ledger_slots(const DevParams& P);
 cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out, cudaStream_t st);
-cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst,
+// Moment fields (FDLBM_MOMENTS layout); t_dev: T and T_s as deviations from T_inlet (K).
+cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst, bool t_dev,
                                cudaStream_t st);
 cudaError_t launch_populations_out(const DevParams& P, const DevState& S, int cur, float* dst,
                                    cudaStream_t st);
@@ -190,14 +197,17 @@ cudaError_t launch_init3(const DevParams& P, const DevState& S, const double* X,
 // rounding of 16-bit storage); with moments_only the pre-collision moments into S.mom.
 cudaError_t launch_step3(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
                          uint32_t step = 0);
-cudaError_t launch_moments_out3(const DevParams& P, const DevState& S, int cur, float* dst, cudaStream_t st);
+cudaError_t launch_moments_out3(const DevParams& P, const DevState& S, int cur, float* dst, bool t_dev,
+                                cudaStream_t st);
 cudaError_t launch_populations_out3(const DevParams& P, const DevState& S, int cur, float* dst,
                                     cudaStream_t st);
 cudaError_t launch_totals3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 cudaError_t launch_residual3(const DevParams& P, const DevState& S, int cur, cudaStream_t st);
 
-// One D2Q9 step with locally updated relaxation times (FP32 storage; fdlbm_local_tau.cu).
-cudaError_t launch_step_local_tau(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
+// One D2Q9 step with locally updated relaxation times (FP32 storage; fdlbm_local_tau.cu);
+// with moments_only the pre-collision moments of the step that reads src into S.mom.
+cudaError_t launch_step_local_tau(const DevParams& P, const DevState& S, int src, bool moments_only, cudaStream_t st,
+                                  uint32_t step);
 // One D2Q9 step that also keeps the exact accounts (FP32 storage; fdlbm_ledger_detail.cu).
 cudaError_t launch_step_detail(const DevParams& P, const DevState& S, int src, cudaStream_t st, uint32_t step);
 // Energy sum (1/2) c_j^2 |e_i|^2 g of the stored populations of gas nodes and of the wall

@@ -47,8 +47,9 @@ __global__ void zero_solid_ts(DevParams P, float* __restrict__ Ts0, float* __res
 // ---------------------------------------------------------------------------------------
 // Outputs and reductions (compact node indices)
 // ---------------------------------------------------------------------------------------
+// T and T_s in kelvin, or with dev as deviations from the inlet temperature (kelvin).
 __global__ void moments_out_kernel(DevParams P, const float* __restrict__ mom, const float* __restrict__ Ts,
-                                   const uint32_t* __restrict__ code, float* __restrict__ dst) {
+                                   const uint32_t* __restrict__ code, float* __restrict__ dst, int dev) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= P.n) return;
   const int ns = P.ns;
@@ -64,9 +65,9 @@ __global__ void moments_out_kernel(DevParams P, const float* __restrict__ mom, c
     }
     dst[(2 * ns) * N + n] = mom[ns * N + n];
     dst[(2 * ns + 1) * N + n] = mom[(ns + 1) * N + n];
-    dst[(2 * ns + 2) * N + n] = mom[(ns + 2) * N + n] * P.T3T0;
+    dst[(2 * ns + 2) * N + n] = (dev ? mom[(ns + 2) * N + n] + P.Tdev_off : P.Tref + mom[(ns + 2) * N + n]) * P.T3T0;
   } else if (c == WALL || c == SOLID) {
-    dst[(2 * ns + 3) * N + n] = (P.Tref + Ts[n]) * P.T3T0;
+    dst[(2 * ns + 3) * N + n] = (dev ? Ts[n] + P.Tdev_off : P.Tref + Ts[n]) * P.T3T0;
   }
 }
 
@@ -92,15 +93,15 @@ __global__ void residual_kernel(DevParams P, const float* __restrict__ mom, cons
       cur[0] = mom[ns * N + n];
       cur[1] = mom[(ns + 1) * N + n];
       for (int j = 0; j < ns; ++j) cur[2 + j] = mom[j * N + n] * P.invM[j] / C;
-      cur[2 + ns] = mom[(ns + 2) * N + n];
+      cur[2 + ns] = mom[(ns + 2) * N + n];  // T - T_ref
     }
-    if (on_solid) cur[3 + ns] = P.Tref + Ts[n];
+    if (on_solid) cur[3 + ns] = Ts[n];
   }
   for (int f = 0; f < nf; ++f) {
     const bool on = f == nf - 1 ? on_solid : on_gas;
     double dd = 0.0, dr = 0.0;
     if (on) {
-      const double ref = f < 2 ? 0.0 : (f < 2 + ns ? double(P.Xin[f - 2]) : double(P.Tin_lat));
+      const double ref = f < 2 ? 0.0 : (f < 2 + ns ? double(P.Xin[f - 2]) : -double(P.Tdev_off));
       const double a = cur[f], b = snap[f * N + n];
       dd = (a - b) * (a - b);
       dr = (a - ref) * (a - ref);
@@ -166,9 +167,10 @@ cudaError_t launch_ledger_sum(const DevParams& P, const DevState& S, double* out
   return cudaGetLastError();
 }
 
-cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst, cudaStream_t st) {
+cudaError_t launch_moments_out(const DevParams& P, const DevState& S, int cur, float* dst, bool t_dev,
+                               cudaStream_t st) {
   const int nb = (P.n + 255) / 256;
-  moments_out_kernel<<<nb, 256, 0, st>>>(P, S.mom, S.Ts[cur], S.code, dst);
+  moments_out_kernel<<<nb, 256, 0, st>>>(P, S.mom, S.Ts[cur], S.code, dst, t_dev ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Options(C.Structure):
     _fields_ = [("storage", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("band_rows", C.c_int),
-                ("ledger_detail", C.c_int)]
+                ("ledger_detail", C.c_int), ("strict_geometry", C.c_int)]
 
 
 class Info(C.Structure):
@@ -95,7 +95,10 @@ class Balance(C.Structure):
 
 
 _lib = None
-EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_populations",
+# fdlbm_moments_ex flag: T and T_s as deviations from the inlet temperature (K).
+MOMENTS_T_DEVIATION = 1
+
+EXPORTS = ("fdlbm_create", "fdlbm_step", "fdlbm_sync", "fdlbm_moments", "fdlbm_moments_ex", "fdlbm_populations",
            "fdlbm_enthalpy_balance", "fdlbm_residual", "fdlbm_set_fields", "fdlbm_info",
            "fdlbm_profile", "fdlbm_kernel_times", "fdlbm_totals_static", "fdlbm_save",
            "fdlbm_load", "fdlbm_batch_create", "fdlbm_batch_step", "fdlbm_batch_remove",
@@ -121,6 +124,7 @@ def load(build_if_missing: bool = True):
     L.fdlbm_step.argtypes = [C.c_void_p, C.c_int64]
     L.fdlbm_sync.argtypes = [C.c_void_p]
     L.fdlbm_moments.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+    L.fdlbm_moments_ex.argtypes = [C.c_void_p, C.c_uint, C.c_void_p, C.c_int]
     L.fdlbm_populations.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
     L.fdlbm_enthalpy_balance.argtypes = [C.c_void_p, P(Balance)]
     L.fdlbm_residual.argtypes = [C.c_void_p, P(C.c_double)]
@@ -167,18 +171,61 @@ def _fields(init, keep):
     return f
 
 
+def create_args(p: dict, keep: list):
+    """The C structs of fdlbm_create for a problem dict: geometry, species array, species
+    count, transport, kinetics and initial fields (argument marshalling only; arrays the
+    structs point into are appended to ``keep``)."""
+    g = Geometry()
+    g.nx, g.ny, g.lattice = p["nx"], p["ny"], p["lattice"]
+    g.nz = p["nz"] if p["dim"] == 3 else 1
+    mask = np.ascontiguousarray(p["mask"], dtype=np.uint8)
+    keep.append(mask)
+    g.mask = mask.ctypes.data_as(C.POINTER(C.c_uint8))
+    for f in range(6):
+        g.face_bc[f] = p["face_bc"][f] if f < len(p["face_bc"]) else 0
+    if p.get("wall_u") is not None:
+        wu = np.ascontiguousarray(p["wall_u"], dtype=np.float64)
+        keep.append(wu)
+        g.wall_u = _dptr(wu)
+    sp = p["species"]
+    ns = len(sp)
+    spec = (Species * ns)()
+    for j, d in enumerate(sp):
+        Drow = (C.c_double * MAX_NS)(*[float(v) for v in d.get("D", [])][:MAX_NS])
+        spec[j] = Species(d["M_gmol"], d["tau1"], d["tau2"], d["X_init"], d["X_inlet"],
+                          float(d.get("mu", 0.0)), Drow)
+    tr = Transport(p["Pr"], int(p["energy_correction"]), p["T0_K"], p["T_init_K"],
+                   p["T_inlet_K"], p["T_solid_init_K"], p["T_outer_K"], p["u_inlet"],
+                   int(p["inlet_profile"]), p["alpha_s"], p["rhocp_s"], p["kappa_f"],
+                   int(p["coupling"]), int(p.get("local_tau", 0)))
+    kin = Kinetics()
+    kin.n_react = len(p["reactions"])
+    for r, d in enumerate(p["reactions"]):
+        for j, v in enumerate(d["nu"]):
+            kin.nu[r][j] = int(v)
+        kin.k0[r], kin.Ea_Jmol[r], kin.Keq[r], kin.dH_Jmol[r] = (
+            d["k0"], d["Ea_Jmol"], d["Keq"], d["dH_Jmol"])
+        kin.rate_form[r] = int(d["rate_form"])
+    kin.rho_w_tol = p["rho_w_tol"]
+    kin.rho_w_maxit = int(p["rho_w_maxit"])
+    fields = _fields(p.get("init"), keep)
+    return g, spec, ns, tr, kin, fields
+
+
 class Solver:
     """One coupled FD-LBM problem on one GPU, built from a problem dict (see
     ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
     storage (FP32 arithmetic in every case). band_rows: rows per band of the step
-    kernel's block order (0: 8; "auto": the autotuner's table). ledger_detail: every step
-    also keeps the exact energy accounts of ``balance()`` (FP32 storage, constant
-    relaxation times)."""
+    kernel's block order and height of the D2Q9 gas tiles (0: 16; "auto": the
+    autotuner's table). ledger_detail: every step also keeps the exact energy accounts of
+    ``balance()`` (FP32 storage, constant relaxation times). strict_geometry: reject
+    geometries whose pulls need the linear or no-interpolation fallbacks (concave corners,
+    narrow gaps) with FDLBM_EGEOM."""
 
     STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
 
     def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32", band_rows: int = 0,
-                 ledger_detail: bool = False):
+                 ledger_detail: bool = False, strict_geometry: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
@@ -190,40 +237,7 @@ class Solver:
         torch.cuda.set_device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(device)
         keep = []
-        g = Geometry()
-        g.nx, g.ny, g.lattice = p["nx"], p["ny"], p["lattice"]
-        g.nz = p["nz"] if p["dim"] == 3 else 1
-        mask = np.ascontiguousarray(p["mask"], dtype=np.uint8)
-        keep.append(mask)
-        g.mask = mask.ctypes.data_as(C.POINTER(C.c_uint8))
-        for f in range(6):
-            g.face_bc[f] = p["face_bc"][f] if f < len(p["face_bc"]) else 0
-        if p.get("wall_u") is not None:
-            wu = np.ascontiguousarray(p["wall_u"], dtype=np.float64)
-            keep.append(wu)
-            g.wall_u = _dptr(wu)
-        sp = p["species"]
-        ns = len(sp)
-        spec = (Species * ns)()
-        for j, d in enumerate(sp):
-            Drow = (C.c_double * MAX_NS)(*[float(v) for v in d.get("D", [])][:MAX_NS])
-            spec[j] = Species(d["M_gmol"], d["tau1"], d["tau2"], d["X_init"], d["X_inlet"],
-                              float(d.get("mu", 0.0)), Drow)
-        tr = Transport(p["Pr"], int(p["energy_correction"]), p["T0_K"], p["T_init_K"],
-                       p["T_inlet_K"], p["T_solid_init_K"], p["T_outer_K"], p["u_inlet"],
-                       int(p["inlet_profile"]), p["alpha_s"], p["rhocp_s"], p["kappa_f"],
-                       int(p["coupling"]), int(p.get("local_tau", 0)))
-        kin = Kinetics()
-        kin.n_react = len(p["reactions"])
-        for r, d in enumerate(p["reactions"]):
-            for j, v in enumerate(d["nu"]):
-                kin.nu[r][j] = int(v)
-            kin.k0[r], kin.Ea_Jmol[r], kin.Keq[r], kin.dH_Jmol[r] = (
-                d["k0"], d["Ea_Jmol"], d["Keq"], d["dH_Jmol"])
-            kin.rate_form[r] = int(d["rate_form"])
-        kin.rho_w_tol = p["rho_w_tol"]
-        kin.rho_w_maxit = int(p["rho_w_maxit"])
-        fields = _fields(p.get("init"), keep)
+        g, spec, ns, tr, kin, fields = create_args(p, keep)
 
         # torch's caching allocator on the solver's stream
         self._blocks = {}
@@ -251,7 +265,7 @@ class Solver:
             band_rows = autotune.lookup(p, storage)
         self.band_rows = int(band_rows)
         opts = Options(self.STORAGE[storage], device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
-                       self._free_cb, None, self.band_rows, int(bool(ledger_detail)))
+                       self._free_cb, None, self.band_rows, int(bool(ledger_detail)), int(bool(strict_geometry)))
         h = C.c_void_p()
         _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
                               C.byref(opts), C.byref(h)))
@@ -262,6 +276,7 @@ class Solver:
         self.nx, self.ny = p["nx"], p["ny"]
         self.nz = p["nz"] if self.dim == 3 else 1
         self.n = self.nx * self.ny * self.nz
+        sp = p["species"]
         m = np.array([d["M_gmol"] for d in sp], np.float64)
         self._M_lat = m / m.min()
         self._X_init = np.array([d["X_init"] for d in sp], np.float64)
@@ -291,24 +306,26 @@ class Solver:
     def nfields(self) -> int:
         return 2 * self.ns + 2 + self.dim
 
-    def moments(self, out=None):
-        """[2 ns + 2 + D, n] float32: rho_j, X_j, ux, uy (, uz), T (K), T_s (K). Returns a
-        CUDA tensor (``out`` may be a preallocated CUDA tensor or a numpy float32 array)."""
+    def moments(self, out=None, t_dev: bool = False):
+        """[2 ns + 2 + D, n] float32: rho_j, X_j, ux, uy (, uz), T (K), T_s (K); with
+        ``t_dev`` T and T_s are deviations from the inlet temperature (K). Returns a CUDA
+        tensor (``out`` may be a preallocated CUDA tensor or a numpy float32 array)."""
         torch = self._torch
         nf = self.nfields
+        flags = MOMENTS_T_DEVIATION if t_dev else 0
         if out is None:
             out = torch.empty((nf, self.n), dtype=torch.float32, device=f"cuda:{self.device}")
         if isinstance(out, np.ndarray):
             assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == nf * self.n
-            _check(load().fdlbm_moments(self._h, out.ctypes.data_as(C.c_void_p), 0))
+            _check(load().fdlbm_moments_ex(self._h, flags, out.ctypes.data_as(C.c_void_p), 0))
             return out
         assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous() and out.numel() == nf * self.n
-        _check(load().fdlbm_moments(self._h, C.c_void_p(out.data_ptr()), 1))
+        _check(load().fdlbm_moments_ex(self._h, flags, C.c_void_p(out.data_ptr()), 1))
         return out
 
-    def moments_host(self) -> np.ndarray:
+    def moments_host(self, t_dev: bool = False) -> np.ndarray:
         out = np.empty((self.nfields, self.n), np.float32)
-        return self.moments(out)
+        return self.moments(out, t_dev)
 
     def populations(self) -> np.ndarray:
         out = np.empty((self.ns, self.Q, self.n), np.float32)

@@ -150,14 +150,14 @@ def test_single_species_and_no_solid():
 
 
 def test_unstable_state_is_reported_not_faulted():
-    """A state far outside the equilibrium's validity blows up to NaN; the kernel's
+    """An explicit energy correction past its stability limit (pure H2 at Pr 0.7: K/C =
+    ((D + 2)/Pr - (D - 1)) tau1 T is about 0.94, above 1/2) blows up to NaN; the kernel's
     sticky flag turns that into FDLBM_EUNSTABLE on the host (no device trap)."""
     fdlbm = _fdlbm()
-    p = W.periodic_box(32, 16, reactions=[])
-    n = 32 * 16
-    p["init"] = {"u": np.vstack([np.full(n, 0.6), np.zeros(n)])}
+    p = _species_subset(W.periodic_box(32, 16, reactions=[], Pr=0.7), 1)
+    p["init"] = W.random_fields(p, seed=81)
     s = fdlbm.Solver(p)
-    s.step(200)
+    s.step(400)
     with pytest.raises(fdlbm.FdlbmError) as ei:
         s.sync()
     assert ei.value.status == -4

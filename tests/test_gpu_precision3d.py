@@ -16,9 +16,10 @@ pytestmark = pytest.mark.gpu
 
 STEPS = 200
 TRACE = (2, 3)  # CO2, H2: inlet mole fraction 1e-6
-# measured on GB300 (FP16): major rho/X 5.5e-5, trace CO2/H2 6.8e-4, u 4.8e-4, T 2.9e-5,
-# Ts 6.0e-6; BF16 about 8 times these; FP32 1.1e-6
-FP16_BOUND = {"major": 2e-4, "trace": 2.5e-3, "u": 1.5e-3, "T": 1e-4, "Ts": 2e-5}
+# measured on GB300 (FP16; T and T_s as deviations from T_in, normalised by the oracle's
+# largest deviation): major rho/X 6.3e-5, trace CO2/H2 4.5e-4, u 4.7e-4, T 6.4e-4, Ts 4.0e-4;
+# BF16 about 8 times these
+FP16_BOUND = {"major": 2e-4, "trace": 2.5e-3, "u": 1.5e-3, "T": 2e-3, "Ts": 1.2e-3}
 BOUNDS = {"fp32": None, "fp16": FP16_BOUND, "bf16": {k: 8 * v for k, v in FP16_BOUND.items()}}
 
 
@@ -47,7 +48,7 @@ def test_storage3_field_errors(storage, oracle_crop):
     p, o = oracle_crop
     s = fdlbm.Solver(p, storage=storage)
     s.step(STEPS)
-    errs = errors3(s.moments_host(), o.moments(), o.classes(), o.ns)
+    errs = errors3(s.moments_host(t_dev=True), o.moments(), o.classes(), o.ns, T_in=o.T_inlet_K)
     print(storage, {k: f"{v:.2e}" for k, v in errs.items()})
     bad = {k: v for k, v in errs.items() if v > _bound(k, BOUNDS[storage])}
     assert not bad, f"{storage}: {bad}"

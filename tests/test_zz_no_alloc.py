@@ -30,13 +30,15 @@ def _compare(t, b):
         np.testing.assert_allclose(t[k], b[k], rtol=RTOL, atol=RTOL * np.abs(b[k]).sum())
 
 
-def test_totals_static_two_calls_match_balance():
+@pytest.mark.parametrize("storage", ["fp32", "bf16", "fp16"])
+def test_totals_static_two_calls_match_balance(storage):
     """Reactive closed box with interface walls (wall emissions in transit count):
-    two consecutive calls, then one more after further steps."""
+    two consecutive calls, then one more after further steps; FP32, BF16 and FP16
+    population storage (the 16-bit forms decode the wall emissions in transit)."""
     fdlbm = _fdlbm()
     p = W.periodic_box(60, 20, solid_rows=6)
     p["init"] = W.random_fields(p, seed=31)
-    s = fdlbm.Solver(p)
+    s = fdlbm.Solver(p, storage=storage)
     s.step(25)
     t1 = s.totals_static()
     t2 = s.totals_static()
@@ -48,6 +50,26 @@ def test_totals_static_two_calls_match_balance():
     assert np.array_equal(t1["mass"], t2["mass"]) and np.array_equal(t1["moles"], t2["moles"])
     s.step(10)
     _compare(s.totals_static(), s.balance())
+    s.close()
+
+
+def test_totals_static_matches_oracle():
+    """The same totals from the FP64 oracle after the same steps: the FP32 state's
+    inventories agree with the oracle's to the parity level of the ledger (1e-6 of the
+    energy inventories, 1e-6 of the total mass and moles)."""
+    import oracle
+    fdlbm = _fdlbm()
+    p = W.periodic_box(60, 20, solid_rows=6)
+    p["init"] = W.random_fields(p, seed=31)
+    s = fdlbm.Solver(p)
+    o = oracle.Oracle(p)
+    s.step(25)
+    o.step(25)
+    t, b = s.totals_static(), o.balance()
+    for k in ("E_gas", "H_solid"):
+        assert abs(t[k] - b[k]) <= 1e-6 * abs(b[k]), (k, t[k], b[k])
+    for k in ("mass", "moles"):
+        np.testing.assert_allclose(t[k], b[k], rtol=0, atol=1e-6 * np.abs(b[k]).sum())
     s.close()
 
 
