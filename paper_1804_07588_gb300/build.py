@@ -41,7 +41,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nv = nvcc()
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+    # -fmad=false: no implicit contraction of a * b + c; the kernels write their fused
+    # multiply-adds explicitly (fmaf), so every instantiation of the same arithmetic (plain
+    # or exact-accounts step, single or batched lattice) rounds identically.
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
                     "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
     # extra nvcc flags, e.g. -DFDLBM_THREADS_PER_SM=1024 to change the register budget
     flags += os.environ.get("FDLBM_NVCC_FLAGS", "").split()

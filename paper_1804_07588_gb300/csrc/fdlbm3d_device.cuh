@@ -205,7 +205,7 @@ __device__ __forceinline__ float wrest3(int i, float T) {
 // wrest3(i, Tr + d) - wrest3(i, Tr) for the emitted (non-rest) directions, formed from the
 // deviation d: axis links 1/2 d (1 - 4 Tr - 2 d), face diagonals 1/4 d (2 Tr + d).
 __device__ __forceinline__ float dwrest3(int i, float Tr, float d) {
-  return NNZ(i) == 1 ? 0.5f * d * (1.f - 4.f * Tr - 2.f * d) : 0.25f * d * (2.f * Tr + d);
+  return NNZ(i) == 1 ? 0.5f * d * fmaf(-2.f, d, fmaf(-4.f, Tr, 1.f)) : 0.25f * d * fmaf(2.f, Tr, d);
 }
 
 __device__ __forceinline__ double block_sum3(double v, double* sh) {
@@ -282,8 +282,8 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     for (int j = 0; j < NS; ++j) {
       float v = v1[j];
       if (!P.onlattice[j]) {
-        const float d1 = fmaf(cp.x, vA[j], cp.y * vB[j]) - cp.z * v1[j];
-        const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1[j];
+        const float d1 = fmaf(-cp.z, v1[j], fmaf(cp.x, vA[j], cp.y * vB[j]));
+        const float d2 = fmaf(-cq.y, v1[j], fmaf(cp.w, vA[j], cq.x * vB[j]));
         v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
       }
       if constexpr (DET) {
@@ -581,8 +581,8 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
       for (int j = 0; j < NS; ++j) {
         float v = v1[j];
         if (!P.onlattice[j]) {
-          const float d1 = fmaf(cp.x, vA[j], cp.y * vB[j]) - cp.z * v1[j];
-          const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1[j];
+          const float d1 = fmaf(-cp.z, v1[j], fmaf(cp.x, vA[j], cp.y * vB[j]));
+          const float d2 = fmaf(-cq.y, v1[j], fmaf(cp.w, vA[j], cq.x * vB[j]));
           v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
         }
         if constexpr (DET) {  // arrival's departure from the shift; its energy, exactly
@@ -650,7 +650,7 @@ __device__ __forceinline__ void solid_node3(const DevParams& P, const PT* __rest
     // arrival and emission sets cancel)
     float dsc[NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) dsc[j] = (Ah[j] - P.rref[j] * dB + mj[j]) * iB;
+    for (int j = 0; j < NS; ++j) dsc[j] = (fmaf(-P.rref[j], dB, Ah[j]) + mj[j]) * iB;
 #pragma unroll 1
     for (int i = 1; i < Q19; ++i) {
       if (!(arr & (1u << OPP3(i)))) continue;

@@ -796,9 +796,10 @@ fdlbm_status read_pop_energy(fdlbm_handle* h, double* out) {
 
 fdlbm_status upload_and_init3(fdlbm_handle* h, const fdlbm_fields* f);
 
-// Initial fields the equilibrium can represent: mole fractions >= 0 summing to 1, and a
-// positive rest factor 1 - M_j u_a^2 - T on every axis for the heaviest species (Eq.
-// eq_state_pop; T and u in lattice units).
+// Initial fields the equilibrium can represent: mole fractions summing to 1 (a trace
+// species may sit slightly below zero, as the solver's own fields can after the
+// interpolation's undershoot), and a positive rest factor 1 - M_j u_a^2 - T on every axis
+// for the heaviest species (Eq. eq_state_pop; T and u in lattice units).
 fdlbm_status check_initial_state(const fdlbm_handle* h, const std::vector<double>& X, const std::vector<double>& u,
                                  const std::vector<double>& T, long n, int dim) {
   float Mmax = 0.f;
@@ -807,7 +808,7 @@ fdlbm_status check_initial_state(const fdlbm_handle* h, const std::vector<double
     double sx = 0.0;
     for (int j = 0; j < h->ns; ++j) {
       const double x = X[(size_t)j * n + k];
-      if (!(x >= 0.0)) return fail(FDLBM_EINVAL, "initial mole fraction %d at node %ld is negative", j, k);
+      if (!(x >= -1e-3)) return fail(FDLBM_EINVAL, "initial mole fraction %d at node %ld is negative (%.3g)", j, k, x);
       sx += x;
     }
     if (std::fabs(sx - 1.0) > 1e-6) return fail(FDLBM_EINVAL, "initial mole fractions at node %ld sum to %.9g", k, sx);

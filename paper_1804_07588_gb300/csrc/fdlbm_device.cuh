@@ -18,7 +18,7 @@ namespace {
 
 constexpr int GB = 256;  // gas kernel block size (threads = gas nodes)
 #ifndef GAS_MIN_BLOCKS
-#define GAS_MIN_BLOCKS 3
+#define GAS_MIN_BLOCKS 2
 #endif
 
 __host__ __device__ constexpr int EX(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0; }
@@ -163,75 +163,6 @@ __device__ __forceinline__ StencilCoef stencil_coef(uint32_t st) {
   return c;
 }
 
-template <class PT, int NS, int I, bool STORE>
-__device__ __forceinline__ void pull_dir_all(const DevParams& P, const PT* __restrict__ src, int k,
-                                             uint32_t cw, Acc<NS>& a, float* __restrict__ s_h, int tid,
-                                             const float (&ecoef)[3]) {
-  constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
-  if (I == 0) {
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const float v = pop_ld(src + ((j * Q) * (int)P.plane + k), P.hsi[j]);
-      if (STORE) s_h[(j * Q) * GB + tid] = v;
-      a.dr[j] += v;
-      a.e[j] = fmaf(ecoef[0], v, a.e[j]);
-    }
-    return;
-  }
-  const int off = EX(I) + EY(I) * P.pitch;
-  const StencilCoef sc = stencil_coef(stencil_of(cw, I));
-  const int dA = sc.mA * off, dB = sc.mB * off;
-  // Issue the three loads of every species first so that all of them are in flight.
-  float v1[NS], vA[NS], vB[NS];
-#pragma unroll
-  for (int j = 0; j < NS; ++j) {
-    const int b = (j * Q + I) * (int)P.plane + k;
-    v1[j] = pop_ld(src + (b - off), P.hsi[j]);
-    vA[j] = pop_ld(src + (b + dA), P.hsi[j]);
-    vB[j] = pop_ld(src + (b + dB), P.hsi[j]);
-  }
-#pragma unroll
-  for (int j = 0; j < NS; ++j) {
-    float v = v1[j];
-    if (!P.onlattice[j]) {
-      const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1[j];
-      const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1[j];
-      v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
-    }
-    if (STORE) s_h[(j * Q + I) * GB + tid] = v;
-    a.dr[j] += v;
-    if (EX(I) > 0) a.ax[j] += v;
-    if (EX(I) < 0) a.ax[j] -= v;
-    if (EY(I) > 0) a.ay[j] += v;
-    if (EY(I) < 0) a.ay[j] -= v;
-    a.e[j] = fmaf(ecoef[e2], v, a.e[j]);
-  }
-}
-
-// Stream all populations into the gas node at padded index k and accumulate moments;
-// with STORE the pulled values also go to shared memory.
-template <class PT, int NS, bool STORE>
-__device__ __forceinline__ void pull_node(const DevParams& P, const PT* __restrict__ src, int k, uint32_t cw,
-                                          Acc<NS>& a, float* __restrict__ s_h, int tid) {
-  const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
-#pragma unroll
-  for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
-  pull_dir_all<PT, NS, 0, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 1, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 2, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 3, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 4, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 5, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 6, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 7, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-  pull_dir_all<PT, NS, 8, STORE>(P, src, k, cw, a, s_h, tid, ecoef);
-}
-
-// Asynchronous form of the pull for the full step: every thread first issues the 9 NS
-// loads of its upstream populations s1 = h_i(x - e_i) as cp.async copies into its own
-// shared-memory column (no registers held while they are in flight), then, once they
-// have landed, applies the interpolation with the two further stencil points of each
-// off-lattice species and accumulates the moments.
 // Streaming stencil coefficients by stencil code (the values of stencil_coef): {pA, pB,
 // p1, qA}, {qB, q1} and the integer offsets {mA, mB} in units of e_i.
 __constant__ float4 c_st_p[8] = {{0.f, 0.f, 0.f, 0.f},   {-1.f, 1.f, 0.f, 1.f}, {4.f, -1.f, 3.f, -2.f},
@@ -241,41 +172,21 @@ __constant__ float2 c_st_q[8] = {{0.f, 0.f}, {1.f, 2.f}, {1.f, -1.f}, {1.f, -1.f
                                  {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f},  {0.f, 0.f}};
 __constant__ int2 c_st_m[8] = {{0, 0}, {-2, 0}, {0, 1}, {-2, -3}, {0, 0}, {-2, -2}, {0, 0}, {0, 0}};
 
-__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-template <class PT, int NS>
-__device__ __forceinline__ void issue_pulls(const DevParams& P, const PT* __restrict__ src, int k,
-                                            float* __restrict__ s_h, int tid) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int off = EX(i) + EY(i) * P.pitch;
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const PT* g = src + ((j * Q + i) * (int)P.plane + k - off);
-      if constexpr (sizeof(PT) == 4)
-        cp_async4(s_h + (j * Q + i) * GB + tid, g);
-      else  // 2-byte values: plain loads, converted into the FP32 column
-        s_h[(j * Q + i) * GB + tid] = pop_ld(g, P.hsi[j]);
-    }
-  }
-  cp_async_commit();
-}
-
+// Pull direction I of every species into the gas node at padded index k: the upstream
+// value s1 = h_I(x - e_I) and, for off-lattice species, the two further stencil points,
+// all loads of the direction issued together; the interpolated value goes to the
+// thread's register array hv[j Q + I] and into the moment accumulators. DET: the exact
+// accounts of the pull (departure from the shift, inlet/outlet face fluxes).
 template <class PT, int NS, int I, bool DET>
-__device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restrict__ src,
-                                           const uint32_t* __restrict__ code, int k, uint32_t cw,
-                                           Acc<NS>& a, float* __restrict__ s_h, int tid,
-                                           const float (&ecoef)[3], Acct* ac) {
+__device__ __forceinline__ void pull_dir(const DevParams& P, const PT* __restrict__ src,
+                                         const uint32_t* __restrict__ code, int k, uint32_t cw, Acc<NS>& a,
+                                         float (&hv)[NS * Q], const float (&ecoef)[3], Acct* ac) {
   constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
   if (I == 0) {
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-      const float v = s_h[(j * Q) * GB + tid];
+      const float v = pop_ld(src + ((j * Q) * (int)P.plane + k), P.hsi[j]);
+      hv[j * Q] = v;
       a.dr[j] += v;
       a.e[j] = fmaf(ecoef[0], v, a.e[j]);
     }
@@ -283,7 +194,7 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
   }
   const int off = EX(I) + EY(I) * P.pitch;
   // exact accounts: classes of the upstream node (source of s1) and of the node this
-  // node's own population i streams into
+  // node's own population I streams into
   uint32_t cu = GAS, cd = GAS;
   if constexpr (DET) {
     cu = node_class(__ldg(code + k - off));
@@ -294,38 +205,38 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
   const float2 cq = c_st_q[st];
   const int2 cm = c_st_m[st];
   const int dA = cm.x * off, dB = cm.y * off;
-  float vA[NS], vB[NS];
+  float v1[NS], vA[NS], vB[NS];
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
+    const int b = (j * Q + I) * (int)P.plane + k;
+    v1[j] = pop_ld(src + (b - off), P.hsi[j]);
     vA[j] = vB[j] = 0.f;
     if (!P.onlattice[j]) {
-      const int b = (j * Q + I) * (int)P.plane + k;
       vA[j] = pop_ld(src + (b + dA), P.hsi[j]);
       vB[j] = pop_ld(src + (b + dB), P.hsi[j]);
     }
   }
 #pragma unroll
   for (int j = 0; j < NS; ++j) {
-    const float v1 = s_h[(j * Q + I) * GB + tid];
-    float v = v1;
+    float v = v1[j];
     if (!P.onlattice[j]) {
-      const float d1 = fmaf(cp.x, vA[j], cp.y * vB[j]) - cp.z * v1;
-      const float d2 = fmaf(cp.w, vA[j], cq.x * vB[j]) - cq.y * v1;
-      v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1));
-      s_h[(j * Q + I) * GB + tid] = v;
+      const float d1 = fmaf(-cp.z, v1[j], fmaf(cp.x, vA[j], cp.y * vB[j]));
+      const float d2 = fmaf(-cq.y, v1[j], fmaf(cp.w, vA[j], cq.x * vB[j]));
+      v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
     }
     if constexpr (DET) {
       const double e = eps_weight(P, j, e2);
-      ac->dint += e * (double(v) - double(v1));
+      ac->dint += e * (double(v) - double(v1[j]));
       const double off0 = double(P.rref[j]) * double(P.W0[I]);
-      if (cu == INLET) ac->qin += e * (double(v1) + off0);
-      if (cu == OUTLET) ac->qout += e * (double(v1) + off0);
+      if (cu == INLET) ac->qin += e * (double(v1[j]) + off0);
+      if (cu == OUTLET) ac->qout += e * (double(v1[j]) + off0);
       if (cd == INLET || cd == OUTLET) {
         const double own = e * (double(pop_ld(src + ((j * Q + I) * (int)P.plane + k), P.hsi[j])) + off0);
         if (cd == INLET) ac->qin -= own;
         else ac->qout -= own;
       }
     }
+    hv[j * Q + I] = v;
     a.dr[j] += v;
     if (EX(I) > 0) a.ax[j] += v;
     if (EX(I) < 0) a.ax[j] -= v;
@@ -335,22 +246,24 @@ __device__ __forceinline__ void interp_dir(const DevParams& P, const PT* __restr
   }
 }
 
+// Stream all populations into the gas node at padded index k (pull streaming with the
+// off-lattice interpolation of Sec. 4.2) and accumulate the species moments.
 template <class PT, int NS, bool DET>
-__device__ __forceinline__ void interp_node(const DevParams& P, const PT* __restrict__ src,
-                                            const uint32_t* __restrict__ code, int k, uint32_t cw,
-                                            Acc<NS>& a, float* __restrict__ s_h, int tid, Acct* ac) {
+__device__ __forceinline__ void pull_node(const DevParams& P, const PT* __restrict__ src,
+                                          const uint32_t* __restrict__ code, int k, uint32_t cw, Acc<NS>& a,
+                                          float (&hv)[NS * Q], Acct* ac) {
   const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
 #pragma unroll
   for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
-  interp_dir<PT, NS, 0, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 1, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 2, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 3, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 4, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 5, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 6, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 7, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
-  interp_dir<PT, NS, 8, DET>(P, src, code, k, cw, a, s_h, tid, ecoef, ac);
+  pull_dir<PT, NS, 0, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 1, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 2, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 3, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 4, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 5, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 6, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 7, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 8, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
 }
 
 // Mixture moments from the species accumulators (Eq. moments_of_g, Eq. moments_of_f):
@@ -377,7 +290,7 @@ __device__ __forceinline__ void finish_moments(const DevParams& P, const Acc<NS>
     m.C = fmaf(rho, P.invM[j], m.C);
     de = fmaf(P.c2[j], a.e[j], de);
   }
-  m.dTg = (de - (m.jx * m.jx + m.jy * m.jy) / m.r) * (0.5f / m.C);
+  m.dTg = (de - fmaf(m.jx, m.jx, m.jy * m.jy) / m.r) * (0.5f / m.C);
 }
 
 // One axis of the product-form equilibrium (Eq. eq_state_pop, positive-sign form) for
@@ -433,24 +346,21 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
                                          float* __restrict__ smem, uint32_t step, Acct* ac = nullptr) {
   const int tid = threadIdx.x;
   const int n_tot = d.z & 0xFFFF, n_int = d.z >> 16, Wp = d.w;
-  float* s_h = smem;                                  // [NS Q][GB] pulled populations
-  float* s_m = s_h + NS * Q * GB;                     // [NS][GB]; with LT then tau1, tau2
-  float* s_map = s_m + (LT ? 3 : 1) * NS * GB;        // [1 + NS][GAS_MAP_SLOTS]: dTg, K_j
+  float* s_map = smem;  // [1 + NS][GAS_MAP_SLOTS]: dTg, K_j of the tile and its halo
   uint32_t cw = 0;
   int k = 0, aux = 0, slot = 0;
   Acc<NS> acc;
   Mom<NS> m;
   float t1l[NS], t2l[NS];
+  float hv[NS * Q];  // the pulled populations, in registers until the collision
   if (tid < n_tot) {
     const int2 g = __ldg(gas_list + d.y + tid);
     k = g.x;
     aux = g.y;
     if (PHI) slot = __ldg(gas_slot + d.y + tid);
     cw = __ldg(code + k);
-    issue_pulls<PT, NS>(P, src, k, s_h, tid);
-    cp_async_wait_all();
     Acct halo_acct{0.0, 0.0, 0.0, 0.0};  // halo entries are counted by their own tile
-    interp_node<PT, NS, DET>(P, src, code, k, cw, acc, s_h, tid, tid < n_int ? ac : &halo_acct);
+    pull_node<PT, NS, DET>(P, src, code, k, cw, acc, hv, tid < n_int ? ac : &halo_acct);
     finish_moments<NS>(P, acc, m);
     // Local relaxation times: tau1_j = mu_j / (C T sum_k X_k phi_jk), tau2_j = rho_j D_j /
     // (X_j C T) = M_j (1 - Y_j) / (T sum_{k != j} X_k / D_jk), T the g-temperature.
@@ -530,41 +440,21 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
   for (int j = 0; j < NS; ++j) {
     const float rho = P.rref[j] + m.drho[j];
     const float w = LT ? 1.f / (t2l[j] + 0.5f) : P.uc_w[j];
-    ncx = fmaf(w, m.Jx[j] - rho * ux, ncx);
-    ncy = fmaf(w, m.Jy[j] - rho * uy, ncy);
+    ncx = fmaf(w, fmaf(-rho, ux, m.Jx[j]), ncx);
+    ncy = fmaf(w, fmaf(-rho, uy, m.Jy[j]), ncy);
     den = fmaf(w, rho, den);
   }
   const float iden = 1.f / den;
   const float Ucx = ncx * iden, Ucy = ncy * iden;
 
-  // The species loop below is not unrolled (keeps the live register set small). Its
-  // inputs: the divergence, parked in this thread's shared-memory column, and the
-  // species' density and momentum, formed again from the pulled values in the pull's
-  // order (the same FP32 sums).
+  // Collision species by species; the species' density and momentum are the pull's sums.
 #pragma unroll
-  for (int j = 0; j < NS; ++j) s_m[j * GB + tid] = divq[j];
-  if constexpr (LT) {
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      s_m[(NS + j) * GB + tid] = t1l[j];
-      s_m[(2 * NS + j) * GB + tid] = t2l[j];
-    }
-  }
-#pragma unroll 1
   for (int j = 0; j < NS; ++j) {
     float h[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = s_h[(j * Q + i) * GB + tid];
-    float drj = 0.f, axj = 0.f, ayj = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      drj += h[i];
-      if (EX(i) > 0) axj += h[i];
-      if (EX(i) < 0) axj -= h[i];
-      if (EY(i) > 0) ayj += h[i];
-      if (EY(i) < 0) ayj -= h[i];
-    }
-    const float Jxj = P.c[j] * axj, Jyj = P.c[j] * ayj, dqj = s_m[j * GB + tid];
+    for (int i = 0; i < Q; ++i) h[i] = hv[j * Q + i];
+    const float drj = m.drho[j];
+    const float Jxj = m.Jx[j], Jyj = m.Jy[j], dqj = divq[j];
     const float rho = P.rref[j] + drj;
     // f-momentum of the species (Eq. moments_of_g) and its velocity, limited for trace
     // species (reading R15).
@@ -572,7 +462,7 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
     float a2j = P.a2[j], inv1a2j = P.inv1a2[j], omj = P.omega[j], omtj = P.omega[j] * P.t1t2[j];
     float wt1j = P.wt1[j], invtau2j = P.invtau2[j];
     if constexpr (LT) {
-      const float t1 = s_m[(NS + j) * GB + tid], t2 = s_m[(2 * NS + j) * GB + tid];
+      const float t1 = t1l[j], t2 = t2l[j];
       omj = 2.f / (1.f + 2.f * t1);
       wt1j = omj * t1;
       invtau2j = 1.f / t2;
@@ -580,8 +470,9 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
       a2j = 0.5f * invtau2j;
       inv1a2j = 1.f / (1.f + a2j);
     }
-    const float Jfx = (Jxj + a2j * rho * (ux + Ucx)) * inv1a2j;
-    const float Jfy = (Jyj + a2j * rho * (uy + Ucy)) * inv1a2j;
+    const float a2r = a2j * rho;
+    const float Jfx = fmaf(a2r, ux + Ucx, Jxj) * inv1a2j;
+    const float Jfy = fmaf(a2r, uy + Ucy, Jyj) * inv1a2j;
     float ujx = ux, ujy = uy;
     if (rho != 0.f) {
       const float ir = 1.f / rho;
@@ -619,9 +510,9 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
       const float qa = EX(i) == 0 ? q0 : q1;
       const float feq = fmaf(pe[a], ey.w[b], qa * ey.dw[b]);
       const float fst = fmaf(ps[a], sy.w[b], qa * sy.dw[b]);
-      float force = PSX(i) * gfx + PSY(i) * gfy;
+      float force = PSX(i) * gfx + PSY(i) * gfy;  // coefficients 0, +-1, +-4: no rounding choice
       if (i == 0) force -= gphi;
-      else if (i <= 4) force += 0.25f * gphi;
+      else if (i <= 4) force = fmaf(0.25f, gphi, force);
       // h' = h - w1 (h - f*) - w1 (tau1 / tau2)(f* - f^eq) + w1 tau1 (Psi + Phi); the two
       // small differences are formed first so that FP32 keeps their precision.
       hn[i] = fmaf(-om, h[i] - fst, fmaf(-omt, fst - feq, h[i] + force));
@@ -671,7 +562,7 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
 
 template <int NS, bool LT = false>
 size_t gas_smem_bytes() {
-  return sizeof(float) * ((NS * Q + (LT ? 3 : 1) * NS) * GB + (1 + NS) * GAS_MAP_SLOTS);
+  return sizeof(float) * (1 + NS) * GAS_MAP_SLOTS;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -825,8 +716,8 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
         for (int j = 0; j < NS; ++j) {
           float v = v1[j];
           if (!P.onlattice[j]) {
-            const float d1 = fmaf(sc.pA, vA[j], sc.pB * vB[j]) - sc.p1 * v1[j];
-            const float d2 = fmaf(sc.qA, vA[j], sc.qB * vB[j]) - sc.q1 * v1[j];
+            const float d1 = fmaf(-sc.p1, v1[j], fmaf(sc.pA, vA[j], sc.pB * vB[j]));
+            const float d2 = fmaf(-sc.q1, v1[j], fmaf(sc.qA, vA[j], sc.qB * vB[j]));
             v = fmaf(P.ha[j], d1, fmaf(P.ha2[j], d2, v1[j]));
           }
           if constexpr (DET) {  // arrival's departure from the shift; its energy, exactly
@@ -918,7 +809,7 @@ __device__ __forceinline__ void solid_node(const DevParams& P, const PT* __restr
       // other), so only small quantities are rounded.
       float dsc[NS];
 #pragma unroll
-      for (int j = 0; j < NS; ++j) dsc[j] = (Ah[j] - P.rref[j] * dBj[j] + mj[j]) * iBj[j];
+      for (int j = 0; j < NS; ++j) dsc[j] = (fmaf(-P.rref[j], dBj[j], Ah[j]) + mj[j]) * iBj[j];
       // Emissions towards the gas neighbours (the directions opposite to the arrivals).
 #pragma unroll 1
       for (int i = 1; i < Q; ++i) {
