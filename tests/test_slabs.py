@@ -1,0 +1,122 @@
+"""The slab decomposition of the D2Q9 path (x slabs, 4-column ghost strips exchanged by
+point-to-point send/recv every step, FP64 all-reduce of the totals and the residual),
+checked with the FP64 oracle as every rank's slab solver: gloo ranks on CPU, world
+sizes 2 and 4. The gathered moment fields must equal the undecomposed oracle's bit for
+bit; the all-reduced totals and residual equal it up to the order of the additions."""
+import os
+import pickle
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _problem(name):
+    from paper_1804_07588_gb300 import workloads as W
+    if name == "channel":  # inlet, outlet, catalytic FD walls, fixed-T faces
+        p = W.channel(nx=64, n_gas=12, wall=4)
+        p["init"] = W.random_fields(p, seed=71, du=0.005)
+        return p
+    if name == "periodic":  # periodic x and y over a catalytic slab
+        p = W.periodic_box(48, 16, solid_rows=4)
+        p["init"] = W.random_fields(p, seed=72)
+        return p
+    if name == "porous":  # digitised disks cut by the slab boundaries, paper coupling
+        p = W.porous_disks(nx=100, ny=60, porosity=0.75, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01, coupling=1)
+        p["init"] = W.random_fields(p, seed=73, du=0.005)
+        return p
+    raise KeyError(name)
+
+
+STEPS = 30
+
+
+def _rank_main(rank, world, port, name, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1804_07588_gb300 import slabs
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        p = _problem(name)
+        run = slabs.SlabRunner(p, oracle.Oracle, dist)
+        run.residual(10)
+        run.step(10)
+        r1 = run.residual(10)
+        run.step(STEPS - 10)
+        tot = run.totals()
+        m = run.gather_moments()
+        out.put((rank, pickle.dumps((m, tot, r1))))
+    finally:
+        dist.destroy_process_group()
+
+
+def _run(name, world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = {}
+    import queue
+    while len(res) < world:
+        try:
+            r, blob = q.get(timeout=5)
+            res[r] = pickle.loads(blob)
+        except queue.Empty:
+            dead = [pr.exitcode for pr in procs if pr.exitcode not in (None, 0)]
+            assert not dead, f"a rank failed: exit codes {dead}"
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    return res
+
+
+def test_partition_is_even_and_covers_the_lattice():
+    from paper_1804_07588_gb300 import slabs
+    parts = slabs.partition(50, 4)
+    assert parts[0][0] == 0 and parts[-1][1] == 50
+    assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))
+    assert max(b - a for a, b in parts) - min(b - a for a, b in parts) <= 1
+    with pytest.raises(ValueError):
+        slabs.partition(12, 4)  # slabs narrower than the ghost depth
+
+
+@pytest.mark.parametrize("name, world", [("channel", 2), ("channel", 4), ("periodic", 2), ("periodic", 4),
+                                         ("porous", 2), ("porous", 4)])
+def test_slabs_bitwise_equal_to_monolithic(name, world):
+    import oracle
+    res = _run(name, world)
+    m_slab, tot, r1 = res[0]
+    p = _problem(name)
+    o = oracle.Oracle(p)
+    o.residual(10)
+    o.step(10)
+    r1_mono = o.residual(10)
+    o.step(STEPS - 10)
+    m_mono = o.moments()
+    assert np.array_equal(m_slab, m_mono), np.abs(m_slab - m_mono).max()
+    b = o.balance()
+    for k in ("E_gas", "H_solid"):
+        assert abs(tot[k] - b[k]) <= 1e-12 * abs(b[k]), (k, tot[k], b[k])
+    for k in ("mass", "moles"):
+        np.testing.assert_allclose(tot[k], b[k], rtol=1e-12)
+    assert abs(r1 - r1_mono) <= 1e-10 * r1_mono, (r1, r1_mono)
+    # every rank reports the same all-reduced totals
+    for r in range(1, world):
+        assert res[r][0] is None
+        assert res[r][1]["E_gas"] == tot["E_gas"]
