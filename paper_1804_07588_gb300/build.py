@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlbm.so")
 SOURCES = ["fdlbm_kernels.cu", "fdlbm_local_tau.cu", "fdlbm_ledger_detail.cu", "fdlbm_store_bf16.cu",
            "fdlbm_store_fp16.cu", "fdlbm3d_kernels.cu", "fdlbm3d_ledger_detail.cu", "fdlbm3d_store_bf16.cu",
-           "fdlbm3d_store_fp16.cu", "fdlbm_api.cu"]
+           "fdlbm3d_store_fp16.cu", "fdlbm_api.cu", "net_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,6 +32,7 @@ def nvcc() -> str:
 def _inputs_mtime() -> float:
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(HERE, "..", "include", "fdlbm.h"))
+    files.append(os.path.join(HERE, "..", "include", "fdlbm_net.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 
