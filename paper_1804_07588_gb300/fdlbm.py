@@ -281,6 +281,8 @@ class Solver:
         self._M_lat = m / m.min()
         self._X_init = np.array([d["X_init"] for d in sp], np.float64)
         self._T_init = float(p["T_init_K"])
+        self._T_in = float(p["T_inlet_K"])
+        self._solid = np.asarray(p["mask"]).reshape(-1) > 0
 
     # -- life cycle ---------------------------------------------------------------
     def close(self):
@@ -370,14 +372,15 @@ class Solver:
         molar concentration, with the create-time defaults where a field is undefined
         (gas fields on solid nodes and the reverse)."""
         ns, D = self.ns, self.dim
-        m = self.moments_host().astype(np.float64)
+        m = self.moments_host(t_dev=True).astype(np.float64)  # temperatures as deviations
         rho, X = m[:ns], m[ns:2 * ns]
-        T, Ts = m[2 * ns + D], m[2 * ns + D + 1]
-        gas = T > 0
+        T, Ts = m[2 * ns + D] + self._T_in, m[2 * ns + D + 1] + self._T_in
+        gas = X.sum(axis=0) > 0
+        solid = self._solid
         C_lat = (rho / self._M_lat[:, None]).sum(axis=0)
         X = np.where(gas[None, :], X, self._X_init[:, None])
         return {"X": X, "u": np.where(gas[None, :], m[2 * ns:2 * ns + D], 0.0),
-                "T_K": np.where(gas, T, self._T_init), "Ts_K": np.where(Ts > 0, Ts, self._T_init),
+                "T_K": np.where(gas, T, self._T_init), "Ts_K": np.where(solid, Ts, self._T_init),
                 "C": np.where(gas, C_lat, 1.0)}
 
     def set_fields(self, init: dict):
