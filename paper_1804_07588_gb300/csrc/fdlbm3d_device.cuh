@@ -142,8 +142,8 @@ struct Ax {
   float wp, wm, w0, S;       // w(+1), w(-1), w(0), S = w(+1) + w(-1)
   float dwp, dwm, dw0, dS;   // deviations from the reference factors
 };
-__device__ __forceinline__ Ax axis3(float sqrtM, float M, float v, float T, float dT) {
-  const float s = sqrtM * v, m = M * v * v;
+__device__ __forceinline__ Ax axis3(float sqrtM, float sMlo, float M, float v, float T, float dT) {
+  const float s = fmaf(sqrtM, v, sMlo * v), m = M * v * v;
   Ax a;
   a.S = m + T;
   a.wp = 0.5f * (a.S + s);
@@ -158,39 +158,43 @@ __device__ __forceinline__ Ax axis3(float sqrtM, float M, float v, float T, floa
 
 // Deviation of one species' folded equilibrium from rref W(T_ref), for all 19
 // directions, density rho = rr + dr and per-axis factors A[3]:
-//   face:  (dr w_p(a) + rr dw_p(a)) w_q(b) + rr W(+-1) dw_q(b)
-//   axis:  (dr w_p(a) + rr dw_p(a)) G_p + rr W(+-1) dG_p,  G_p = w_q(0) w_r(0) - S_q S_r
-//   rest:  dr R + rr dR,  R = w_x(0) w_y(0) w_z(0) + S_x S_y S_z,
-// with the deviations dG, dR expanded so that no large term cancels.
+//   face:  P_p(a) W(+-1) + (P_p(a) + rr W(+-1)) dw_q(b)
+//   axis:  P_p(a) G0 + (P_p(a) + rr W(+-1)) dG_p,  G_p = w_q(0) w_r(0) - S_q S_r
+//   rest:  dr R0 + (rr + dr) dR,  R = w_x(0) w_y(0) w_z(0) + S_x S_y S_z,
+// with P_p(a) = rho w_p(a) - rr W(+-1) = dr W(+-1) + rho dw_p(a), G0 and R0 the rest values
+// and the deviations dG, dR expanded so that no large term cancels. Density deviations
+// multiply only rest factors: factors at the absolute temperature carry its rounding
+// (~1.5e-8, nearly the same on all nodes of a uniform region), which multiplied by dr
+// would act as a systematic energy source at every collision.
 __device__ __forceinline__ void feq_dev3(float dr, float rr, float Tr, const Ax (&A)[3], float (&f)[Q19]) {
   const float W0 = 1.f - Tr, Wpm = 0.5f * Tr;
-  float Pp[3], Pm[3], G[3], dG[3];
+  // G0 = W0^2 - Tr^2 = 1 - 2 Tr and R0 = W0^3 + Tr^3 = 1 - 3 Tr W0, exact in FP32 for the
+  // reference temperature on its 2^-12 grid
+  const float rho = rr + dr, G0 = 1.f - 2.f * Tr, R0 = 1.f - 3.f * (Tr * W0);
+  float Pp[3], Pm[3], dG[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    Pp[p] = fmaf(dr, A[p].wp, rr * A[p].dwp);
-    Pm[p] = fmaf(dr, A[p].wm, rr * A[p].dwm);
+    Pp[p] = fmaf(dr, Wpm, rho * A[p].dwp);
+    Pm[p] = fmaf(dr, Wpm, rho * A[p].dwm);
     const Ax& q = A[(p + 1) % 3];
     const Ax& r = A[(p + 2) % 3];
-    G[p] = q.w0 * r.w0 - q.S * r.S;
     dG[p] = (fmaf(q.dw0, r.w0, W0 * r.dw0)) - (fmaf(q.dS, r.S, Tr * r.dS));
   }
-  const float R = A[0].w0 * A[1].w0 * A[2].w0 + A[0].S * A[1].S * A[2].S;
   const float dR = fmaf(A[0].dw0, A[1].w0 * A[2].w0, W0 * fmaf(A[1].dw0, A[2].w0, W0 * A[2].dw0)) +
                    fmaf(A[0].dS, A[1].S * A[2].S, Tr * fmaf(A[1].dS, A[2].S, Tr * A[2].dS));
-  f[0] = fmaf(dr, R, rr * dR);
+  f[0] = fmaf(dr, R0, rho * dR);
 #pragma unroll
   for (int i = 1; i < Q19; ++i) {
     if (NNZ(i) == 1) {
       const int p = DX(i) ? 0 : (DY(i) ? 1 : 2);
       const float P_ = DC(i, p) > 0 ? Pp[p] : Pm[p];
-      f[i] = fmaf(P_, G[p], rr * Wpm * dG[p]);
+      f[i] = fmaf(P_, G0, (P_ + rr * Wpm) * dG[p]);
     } else {
       const int p = DX(i) ? 0 : 1;
       const int q = DZ(i) ? 2 : 1;
       const float P_ = DC(i, p) > 0 ? Pp[p] : Pm[p];
-      const float wq = DC(i, q) > 0 ? A[q].wp : A[q].wm;
       const float dwq = DC(i, q) > 0 ? A[q].dwp : A[q].dwm;
-      f[i] = fmaf(P_, wq, rr * Wpm * dwq);
+      f[i] = fmaf(P_, Wpm, (P_ + rr * Wpm) * dwq);
     }
   }
 }
@@ -414,8 +418,11 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
       bool big = false;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const float Jf = (P.c[j] * Jj[a] + P.a2[j] * rho * (u[a] + Uc[a])) * P.inv1a2[j];
-        uj[a] = Jf * ir;
+        // u + (J_j - rho_j u + a2 rho_j U^c) / ((1 + a2) rho_j): formed from the diffusion
+        // flux, so that no rounded constant multiplies rho_j u: the direct form leaves a
+        // momentum source ~1e-7 rho_j u per collision, a velocity error that builds up
+        const float Dj = fmaf(-rho, u[a], P.c[j] * Jj[a]);
+        uj[a] = fmaf(fmaf(P.a2[j] * rho, Uc[a], Dj) * P.inv1a2[j], ir, u[a]);
         big |= uj[a] * uj[a] > lim2;
       }
       if (big) {
@@ -427,8 +434,8 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
     Ax Ae[3], As[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      Ae[a] = axis3(sM, M, u[a], T, dT);
-      As[a] = axis3(sM, M, uj[a], T, dT);
+      Ae[a] = axis3(sM, P.sqrtM_lo[j], M, u[a], T, dT);
+      As[a] = axis3(sM, P.sqrtM_lo[j], M, uj[a], T, dT);
     }
     float feq[Q19], fst[Q19];
     feq_dev3(drj, rr, Tr, Ae, feq);
@@ -474,7 +481,7 @@ __device__ __forceinline__ void gas_node3(const DevParams& P, const PT* __restri
       const float rj = (P.rref[j] + dr[j]) * P.invM[j] / C * Cout * P.M[j];
       Ax Ae[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) Ae[a] = axis3(P.sqrtM[j], P.M[j], u[a], T, dT);
+      for (int a = 0; a < 3; ++a) Ae[a] = axis3(P.sqrtM[j], P.sqrtM_lo[j], P.M[j], u[a], T, dT);
       float f[Q19];
       feq_dev3(rj - P.rref[j], P.rref[j], Tr, Ae, f);
 #pragma unroll

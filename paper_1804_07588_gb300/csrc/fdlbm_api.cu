@@ -67,6 +67,7 @@ struct fdlbm_handle {
   std::vector<uint32_t> code;
   std::vector<double> X_init, X_inlet, inlet_u;
   double T0 = 0, T_init_lat = 0, T_inlet_lat = 0, Ts_init_lat = 0;
+  double T_st = 0;  // reference temperature of the stored deviations (a multiple of 2^-12)
   double heat0 = 0;           // -dH / (3 R T0) of reaction 0
   int eps_species = -1, eps_nu = 0;
   double E0 = 0, H0 = 0, mass0[MAX_NS] = {}, moles0[MAX_NS] = {};
@@ -188,11 +189,18 @@ void set_physics_params(fdlbm_handle* h, const fdlbm_species* species, int ns, c
   h->T_inlet_lat = Tref;
   h->T_init_lat = tr->T_init_K * tl;
   h->Ts_init_lat = tr->T_solid_init_K * tl;
-  P.Tref = (float)Tref;
+  // Populations are stored as deviations from the rest equilibrium at T_st, the inlet
+  // temperature rounded to a multiple of 2^-12: then the rest factors 1 - T_st, T_st / 2,
+  // 1 - 2 T_st and 1 - 3 T_st (1 - T_st) and the rest weights are exact FP32 numbers
+  // whose sums over the directions are exactly 1, so that the equilibria formed from
+  // them carry no constant rounding bias of mass, momentum or energy.
+  const double Tst = std::max(std::round(Tref * 4096.0), 1.0) / 4096.0;
+  h->T_st = Tst;
+  P.Tref = (float)Tst;
   P.p_out = (float)Tref;  // C_in T_in with C_in = 1
   P.u_inlet = (float)tr->u_inlet;
   P.Tin_lat = (float)Tref;
-  P.Tdev_off = (float)(double(P.Tref) - Tref);
+  P.Tdev_off = (float)(Tst - Tref);
   h->X_init.resize(ns);
   h->X_inlet.resize(ns);
   for (int j = 0; j < ns; ++j) {
@@ -203,6 +211,7 @@ void set_physics_params(fdlbm_handle* h, const fdlbm_species* species, int ns, c
     P.invM[j] = (float)(1.0 / M);
     P.sqrtM[j] = (float)std::sqrt(M);
     P.c[j] = (float)c;
+    P.sqrtM_lo[j] = (float)(1.0 / double(P.c[j]) - double(P.sqrtM[j]));
     P.c2[j] = (float)(1.0 / M);
     const double a = 1.0 - c;
     P.a[j] = (float)a;
@@ -252,7 +261,7 @@ void set_physics_params(fdlbm_handle* h, const fdlbm_species* species, int ns, c
   P.rhocp_s = (float)tr->rhocp_s;
   P.inv_rhocp_s = (float)(1.0 / tr->rhocp_s);
   P.kappa_f = (float)tr->kappa_f;
-  P.dTout = (float)(tr->T_outer_K * tl - Tref);
+  P.dTout = (float)(tr->T_outer_K * tl - Tst);
   P.nr = kin->n_react;
   for (int r = 0; r < kin->n_react; ++r) {
     for (int j = 0; j < ns; ++j) P.nu[r][j] = kin->nu[r][j];
@@ -635,7 +644,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   for (int f = 0; f < 4; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
   set_physics_params(h, species, ns, tr, kin, storage, 2);
   P.ledger_detail = (opts && opts->ledger_detail) ? 1 : 0;
-  const double Tref = h->T_inlet_lat;
+  const double Tref = h->T_st;
   for (int i = 0; i < Q; ++i) {
     const double wx = HEX[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
     const double wy = HEY[i] == 0 ? 1.0 - Tref : 0.5 * Tref;
@@ -1163,7 +1172,7 @@ fdlbm_status create3(const fdlbm_geometry* geom, const fdlbm_species* species, i
   for (int f = 0; f < 6; ++f) P.fixedT_face[f] = fb[f] == FDLBM_FACE_FIXED_T;
   set_physics_params(h, species, ns, tr, kin, storage, 3);
   P.ledger_detail = (opts && opts->ledger_detail) ? 1 : 0;
-  for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, h->T_inlet_lat);
+  for (int i = 0; i < Q19; ++i) P.W0_19[i] = (float)wrest3_h(i, h->T_st);
 
   // Device state.
   fdlbm_status st;

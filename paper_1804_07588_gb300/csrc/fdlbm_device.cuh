@@ -299,8 +299,8 @@ __device__ __forceinline__ void finish_moments(const DevParams& P, const Acc<NS>
 struct Axis {
   float w[3], dw[3];
 };
-__device__ __forceinline__ Axis axis_factors(float sqrtM, float M, float v, float T, float dT) {
-  const float s = sqrtM * v, m = M * v * v;
+__device__ __forceinline__ Axis axis_factors(float sqrtM, float sMlo, float M, float v, float T, float dT) {
+  const float s = fmaf(sqrtM, v, sMlo * v), m = M * v * v;
   Axis a;
   a.w[1] = 1.f - m - T;
   a.w[2] = 0.5f * (m + T + s);
@@ -470,14 +470,18 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
       a2j = 0.5f * invtau2j;
       inv1a2j = 1.f / (1.f + a2j);
     }
+    // Velocity of f*: u_j = (J_j + a2 rho_j (u + U^c)) / ((1 + a2) rho_j), formed as
+    // u + (D_j + a2 rho_j U^c) / ((1 + a2) rho_j) from the diffusion flux D_j = J_j - rho_j u.
+    // With the rounded constants a2, 1 / (1 + a2), omega, omega tau1 / tau2 the direct form
+    // leaves a momentum source (B - A) rho_j u per collision, B - A ~ 1e-7 (the two
+    // coefficients are equal in exact arithmetic), which builds up a velocity error
+    // proportional to u over the steps; in this form no constant multiplies rho_j u.
     const float a2r = a2j * rho;
-    const float Jfx = fmaf(a2r, ux + Ucx, Jxj) * inv1a2j;
-    const float Jfy = fmaf(a2r, uy + Ucy, Jyj) * inv1a2j;
     float ujx = ux, ujy = uy;
     if (rho != 0.f) {
       const float ir = 1.f / rho;
-      ujx = Jfx * ir;
-      ujy = Jfy * ir;
+      ujx = fmaf(fmaf(a2r, Ucx, fmaf(-rho, ux, Jxj)) * inv1a2j, ir, ux);
+      ujy = fmaf(fmaf(a2r, Ucy, fmaf(-rho, uy, Jyj)) * inv1a2j, ir, uy);
       const float lim2 = fmaxf(1.f - T, 0.f) * P.invM[j];
       if (ujx * ujx > lim2 || ujy * ujy > lim2) {  // rare: trace species driven through zero
         const float lim = sqrtf(lim2);
@@ -485,16 +489,21 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
         ujy = fminf(fmaxf(ujy, -lim), lim);
       }
     }
-    const float M = P.M[j], sM = P.sqrtM[j], dr = drj, rr = P.rref[j];
-    const Axis ex = axis_factors(sM, M, ux, T, dT), ey = axis_factors(sM, M, uy, T, dT);
-    const Axis sx = axis_factors(sM, M, ujx, T, dT), sy = axis_factors(sM, M, ujy, T, dT);
-    // f(a, b) = (drho wx(a) + rref dwx(a)) wy(b) + rref w0(a) dwy(b): the deviation of
-    // rho wx wy from rref w0x w0y.
+    const float M = P.M[j], sM = P.sqrtM[j], sl = P.sqrtM_lo[j], dr = drj, rr = P.rref[j];
+    const Axis ex = axis_factors(sM, sl, M, ux, T, dT), ey = axis_factors(sM, sl, M, uy, T, dT);
+    const Axis sx = axis_factors(sM, sl, M, ujx, T, dT), sy = axis_factors(sM, sl, M, ujy, T, dT);
+    // The deviation of rho wx(a) wy(b) from rref w0(a) w0(b), with p(a) = rho wx(a) -
+    // rref w0(a) = drho w0(a) + rho dwx(a):  f(a, b) = p(a) w0(b) + (p(a) + rref w0(a)) dwy(b).
+    // Only the rest factors w0 and the deviations dw (formed from T - T_ref) appear: the
+    // factors w at the absolute temperature carry its rounding (~1.5e-8, nearly the same
+    // on all nodes of a uniform region), which multiplied by drho would act as a
+    // systematic energy source at every collision.
+    const float w0e[3] = {0.5f * P.Tref, 1.f - P.Tref, 0.5f * P.Tref};
     float pe[3], ps[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      pe[e] = fmaf(dr, ex.w[e], rr * ex.dw[e]);
-      ps[e] = fmaf(dr, sx.w[e], rr * sx.dw[e]);
+      pe[e] = fmaf(dr, w0e[e], rho * ex.dw[e]);
+      ps[e] = fmaf(dr, w0e[e], rho * sx.dw[e]);
     }
     const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;  // rref w0(0), rref w0(+-1)
     const float om = omj, omt = omtj;
@@ -508,8 +517,8 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
     for (int i = 0; i < Q; ++i) {
       const int a = EX(i) + 1, b = EY(i) + 1;
       const float qa = EX(i) == 0 ? q0 : q1;
-      const float feq = fmaf(pe[a], ey.w[b], qa * ey.dw[b]);
-      const float fst = fmaf(ps[a], sy.w[b], qa * sy.dw[b]);
+      const float feq = fmaf(pe[a], w0e[b], (pe[a] + qa) * ey.dw[b]);
+      const float fst = fmaf(ps[a], w0e[b], (ps[a] + qa) * sy.dw[b]);
       float force = PSX(i) * gfx + PSY(i) * gfy;  // coefficients 0, +-1, +-4: no rounding choice
       if (i == 0) force -= gphi;
       else if (i <= 4) force = fmaf(0.25f, gphi, force);
@@ -547,13 +556,15 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
     for (int j = 0; j < NS; ++j) {
       const float rj = (P.rref[j] + m.drho[j]) * P.invM[j] / m.C * Cout * P.M[j];
       const float dr = rj - P.rref[j], rr = P.rref[j];
-      const Axis ex = axis_factors(P.sqrtM[j], P.M[j], ux, T, dT), ey = axis_factors(P.sqrtM[j], P.M[j], uy, T, dT);
+      const Axis ex = axis_factors(P.sqrtM[j], P.sqrtM_lo[j], P.M[j], ux, T, dT),
+                 ey = axis_factors(P.sqrtM[j], P.sqrtM_lo[j], P.M[j], uy, T, dT);
       const float q0 = rr * (1.f - P.Tref), q1 = rr * 0.5f * P.Tref;
+      const float w0e[3] = {0.5f * P.Tref, 1.f - P.Tref, 0.5f * P.Tref};
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int a = EX(i) + 1, b = EY(i) + 1;
-        const float pa = fmaf(dr, ex.w[a], rr * ex.dw[a]);
-        const float v = fmaf(pa, ey.w[b], (EX(i) == 0 ? q0 : q1) * ey.dw[b]);
+        const float pa = fmaf(dr, w0e[a], rj * ex.dw[a]);
+        const float v = fmaf(pa, w0e[b], (pa + (EX(i) == 0 ? q0 : q1)) * ey.dw[b]);
         pop_store_ghosts(dst + (long long)(j * Q + i) * P.plane, k + 1, go, v, P.hs[j], seed, NS * Q + j * Q + i);
       }
     }

@@ -48,6 +48,11 @@ struct DevParams {
   int fixedT_face[6];   // x-, x+, y-, y+, z-, z+
   // species
   float M[MAX_NS], invM[MAX_NS], sqrtM[MAX_NS], c[MAX_NS], c2[MAX_NS];
+  // sqrtM + sqrtM_lo is the reciprocal of the stored c to ~1e-14: velocities enter the
+  // equilibria as v (sqrtM + sqrtM_lo), so that the equilibrium's momentum, measured with
+  // c, is rho v without the constant bias c sqrtM - 1 (~1e-8) that would otherwise scale
+  // the momentum at every collision.
+  float sqrtM_lo[MAX_NS];
   float a[MAX_NS];      // 1 - c_j
   float ha[MAX_NS], ha2[MAX_NS];  // (1 - c_j) / 2 and (1 - c_j)^2 / 2 (interpolation)
   int onlattice[MAX_NS];
@@ -73,7 +78,7 @@ struct DevParams {
   // steady-state residual references
   float Xin[MAX_NS];
   float Tin_lat;
-  float Tdev_off;       // float(T_ref) - T_inlet (lattice): the float reference's own rounding
+  float Tdev_off;       // T_ref - T_inlet (lattice): T_ref is T_inlet rounded to a multiple of 2^-12
   // D3Q19 lattice (dim 3): node (x, y, z) at (x + xoff) + (y + yoff) pitch + (z + zoff) slab
   int dim;              // 2 (D2Q9) or 3 (D3Q19)
   int nz, zoff, periodic_z;

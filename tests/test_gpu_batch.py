@@ -1,6 +1,7 @@
 """Batched stepping through the C ABI (fdlbm_batch_*): members of different sizes,
 geometries and parameters advanced in one launch per step give the same bits as each
-member stepped on its own (same kernels, same per-block ledger slots)."""
+member stepped on its own (same kernels, same per-block ledger slots), and a member
+matches the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -94,3 +95,23 @@ def test_batch_rejects_incompatible_members():
         fdlbm.Batch([s, s])
     with pytest.raises(fdlbm.FdlbmError):
         fdlbm.Batch([fdlbm.Solver(p), fdlbm.Solver(p, storage="bf16")])
+
+
+def test_batch_member_matches_the_oracle():
+    """Every member of a batch after 300 batched steps against the FP64 oracle of the same
+    problem (the parity bar of the solver stepped alone)."""
+    import oracle
+    from parity import assert_parity
+    fdlbm = _fdlbm()
+    probs = _problems()
+    members = [fdlbm.Solver(p) for p in probs]
+    b = fdlbm.Batch(members)
+    b.step(300)
+    for s in members:
+        s.sync()
+    b.close()
+    for p, s in zip(probs, members):
+        o = oracle.Oracle(p)
+        o.step(300)
+        assert_parity(s, o, what="batch member")
+        s.close()

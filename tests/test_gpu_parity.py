@@ -87,6 +87,27 @@ def test_parity_config0_1000_steps():
     print("config0 errors", errs)
 
 
+def _bed_crop(w, h):
+    """The top-left w x h crop of the 1024x512 bed (same disk packing), outlet columns
+    opened, periodic in y."""
+    full = W.config1()
+    mask = full["mask"].reshape(512, 1024)[:h, :w].copy()
+    mask[:, w - 2:] = W.GAS
+    return W._base(2, w, h, 1, mask, [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC], u_inlet=full["u_inlet"],
+                   inlet_profile=W.PLUG)
+
+
+def test_parity_bed_crop_1000_steps():
+    """The 128x128 crop of the disk bed (catalytic disks of radius 6-12, digitised
+    corners, inlet, outlet) from random fields, 1000 steps: every field within 1e-5."""
+    p = _bed_crop(128, 128)
+    p["init"] = W.random_fields(p, seed=29, du=0.005)
+    s, o = run_both(p, 1000, chunks=4)
+    errs = assert_parity(s, o, what="bed crop 1000 steps")
+    print("bed crop errors", errs)
+    s.close()
+
+
 def test_parity_config1_full_size_few_steps():
     """The full 1024x512 porous bed, in the launch configuration the benchmark times,
     from random fields: 4 steps, every node of every field."""

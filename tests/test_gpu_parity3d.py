@@ -147,6 +147,16 @@ def test_parity3_config2_crop():
     s.close()
 
 
+def test_parity3_sphere_crop_1000_steps():
+    """A 40x20x20 corner crop of the sphere packing (catalytic spheres with FD heat,
+    inlet, outlet, periodic y and z) from random fields, 1000 steps."""
+    p = W.crop3(W.config2(), 40, 20, 20)
+    p["init"] = W.random_fields(p, seed=62, du=0.005)
+    s, o = run_both3(p, 1000)
+    check(s, o, what="sphere crop 1000 steps")
+    s.close()
+
+
 def test_parity3_full_bed_sampled():
     """The full 256x128x128 bed (the benchmark's workload and launch configuration) from
     seeded random fields, 4 steps, compared on the nodes of the 64x48x48 corner crop
