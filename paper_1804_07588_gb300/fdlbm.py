@@ -428,6 +428,42 @@ class Batch:
     def __len__(self):
         return load().fdlbm_batch_size(self._b)
 
+    def run_to_steady(self, tol: float = 1e-6, every: int = 500, max_steps: int = 200_000) -> list:
+        """Advance the batch until every member's steady-state residual (``Solver.residual``,
+        the largest field change per step relative to the field) is below tol: every
+        `every` steps the residual of each member still in the batch is read, and members
+        below tol, or unstable, are removed so that the remaining launches cover only the
+        others. Stops after max_steps. Returns, per member in the original order, {steps,
+        residual, converged, unstable}."""
+        members = list(self.solvers)
+        out = {id(s): {"steps": 0, "residual": float("inf"), "converged": False, "unstable": False}
+               for s in members}
+        for s in members:
+            s.residual()  # snapshot the moments the first change is measured against
+        steps = 0
+        active = list(members)
+        while active and steps < max_steps:
+            n = min(every, max_steps - steps)
+            self.step(n)
+            steps += n
+            for s in list(active):
+                rec = out[id(s)]
+                rec["steps"] = steps
+                try:
+                    r = s.residual()
+                except FdlbmError:
+                    r = float("nan")
+                rec["residual"] = r
+                if not np.isfinite(r):
+                    rec["unstable"] = True
+                elif r < tol:
+                    rec["converged"] = True
+                else:
+                    continue
+                self.remove(s)
+                active.remove(s)
+        return [out[id(s)] for s in members]
+
     def close(self):
         b = getattr(self, "_b", None)
         if b is not None and b.value:

@@ -115,3 +115,30 @@ def test_batch_member_matches_the_oracle():
         o.step(300)
         assert_parity(s, o, what="batch member")
         s.close()
+
+
+def test_batch_runs_members_to_steady_and_removes_them():
+    """Six small beds of uneven size and inlet velocity run to residual 1e-5 in one batch:
+    a member below the tolerance leaves the batch at the check where it got there and is
+    not advanced further (its step count stays there), the others go on; at least four of
+    the six get there within 100,000 steps."""
+    fdlbm = _fdlbm()
+    probs = W.batch_instances(n=6, seed=77, nx_range=(96, 160), ny_range=(48, 64), porosity=(0.5, 0.7),
+                              u_inlet=(0.02, 0.03))
+    solvers = [fdlbm.Solver(p) for p in probs]
+    b = fdlbm.Batch(solvers)
+    res = b.run_to_steady(tol=1e-5, every=1000, max_steps=100_000)
+    remaining = len(b)
+    b.close()
+    conv = [r for r in res if r["converged"]]
+    assert len(conv) >= 4, res
+    assert remaining == len(res) - len(conv) - sum(r["unstable"] for r in res)
+    for s, r in zip(solvers, res):
+        assert not r["unstable"]
+        assert s.info()["steps"] == r["steps"]
+        if r["converged"]:
+            assert r["residual"] < 1e-5
+        else:
+            assert r["steps"] == 100_000
+        s.close()
+    assert len({r["steps"] for r in conv}) > 1  # members leave at different times

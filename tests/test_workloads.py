@@ -5,6 +5,7 @@ ranges of the batched instances. Host logic only."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_1804_07588_gb300 import workloads as W
 
@@ -67,20 +68,35 @@ def test_percolation_check_detects_a_blocked_bed():
 
 
 def test_batch_instance_ranges():
-    """64 instances: nx, ny multiples of 8 in [256, 1024] x [128, 256], porosity in
-    [0.6, 0.7], inlet 0.005-0.03, inlet temperature 450-600 K (also T0 and the initial
-    temperatures); every instance its own seed."""
+    """Instances: nx, ny multiples of 8 in [256, 1024] x [128, 256], porosity in [0.4,
+    0.7], inlet 0.005-0.03, inlet temperature 450-600 K (also T0 and the initial
+    temperatures); every instance its own seed, its gas connecting inlet and outlet."""
     inst = W.batch_instances(n=8)
     assert len(inst) == 8
+    pors = []
     for p in inst:
         assert p["nx"] % 8 == 0 and 256 <= p["nx"] <= 1024
         assert p["ny"] % 8 == 0 and 128 <= p["ny"] <= 256
         por = 1.0 - (p["mask"] > 0).mean()
-        assert 0.6 - 2e-3 <= por <= 0.7 + 2e-3
+        pors.append(por)
+        assert 0.4 - 2e-3 <= por <= 0.7 + 2e-3
+        assert W._percolates((np.asarray(p["mask"]).reshape(1, p["ny"], p["nx"]) == 0))
         assert 0.005 <= p["u_inlet"] <= 0.03
         assert 450.0 <= p["T_inlet_K"] <= 600.0
         assert p["T0_K"] == p["T_inlet_K"] == p["T_init_K"] == p["T_solid_init_K"]
     assert len({p["mask"].tobytes() for p in inst}) == len(inst)
+    assert min(pors) < 0.55  # below what separated disks reach
+
+
+def test_boolean_disks_reach_low_porosity():
+    """Overlapping disks reach porosity 0.4 (digitised, within one disk's area), keep the
+    inlet and outlet columns free, and a packing whose gas is cut is rejected."""
+    mask, disks = W.disk_mask_boolean(256, 128, 0.4, 6.0, 12.0, 27)
+    por = (mask == W.GAS).mean()
+    assert 0.4 - math.pi * 144 / (256 * 128) <= por <= 0.4 + 1e-12
+    assert (mask[:, :17] == W.GAS).all() and (mask[:, -17:] == W.GAS).all()
+    with pytest.raises((ValueError, RuntimeError)):
+        W.disk_mask_boolean(128, 64, 0.05, 6.0, 12.0, 3)
 
 
 def test_species_and_kinetics_tables():
