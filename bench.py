@@ -340,7 +340,7 @@ def measure(fdlbm, p, storage, steps, warmup, dev, flush, Q):
     of its step launches: algorithmic bytes (2 Q populations per species-node) over the
     CUDA-event time of the step's kernels."""
     import torch
-    s = fdlbm.Solver(p, device=dev, storage=storage)
+    s = fdlbm.Solver(p, device=dev, storage=storage, band_rows="auto" if p["dim"] == 2 else 0)
     info = s.info()
     ns, n_gas = info["ns"], info["n_gas"]
     s.step(warmup)
@@ -526,7 +526,7 @@ def run_fdlbm(args, rank, world, local_rank):
     else:
         p = workloads.config1()
     Q = 19 if three_d else 9
-    s = fdlbm.Solver(p, device=dev, storage=args.storage)
+    s = fdlbm.Solver(p, device=dev, storage=args.storage, band_rows="auto" if not three_d else 0)
     info = s.info()
     ns = info["ns"]
     n_gas = info["n_gas"]
@@ -569,7 +569,7 @@ def run_fdlbm(args, rank, world, local_rank):
         import numpy as np
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        s2 = fdlbm.Solver(p, device=dev, storage=args.storage)
+        s2 = fdlbm.Solver(p, device=dev, storage=args.storage, band_rows="auto" if not three_d else 0)
         s2.step(args.steps)
         m = s2.moments_host()
         s2.sync()
@@ -640,6 +640,9 @@ def run_fdlbm(args, rank, world, local_rank):
                                            "rounding"}[args.storage],
                        "species": ns, "gas_nodes": n_gas, "wall_nodes": info["n_wall"],
                        "solid_nodes": info["n_solid"], "l2": "flushed (256 MB write) before every timed step",
+                       **({} if three_d else {"block_order": {"band_rows": s.band_rows, "tile_entries": s.tile_entries,
+                                                              "wall_order": s.wall_order,
+                                                              "from": "autotuner table (tuning_gb300.json)"}}),
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak,

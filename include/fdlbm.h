@@ -174,6 +174,12 @@ typedef struct {
                               concave corners and one- or two-node gaps; the paper
                               restricts its walls to planar and convex corner nodes
                               (Sec. 4.2, Sec. 4.3). 0: accept them, with the fallbacks */
+  int tile_entries;        /* D2Q9: at most this many gas nodes (interior and halo ring) per
+                              gas tile, which is also the step kernel's block size: a
+                              multiple of 32 in [64, 256]; 0: 256. EINVAL otherwise */
+  int wall_order;          /* D2Q9 block order: 0 each band's wall and solid blocks right
+                              after its gas tiles (their neighbours' populations still in
+                              L2); 1 all wall and solid blocks after all gas tiles */
 } fdlbm_options;
 
 /* Counts and derived constants of a handle. */

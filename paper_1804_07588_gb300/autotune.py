@@ -1,12 +1,15 @@
-"""Autotuner for the step kernel's block order.
+"""Autotuner for the D2Q9 step kernel's block order.
 
-The one launch of a time step runs, per band of rows, the gas blocks of the band and then
-its wall blocks (so that the wall blocks find their neighbours' populations in L2); the
-band height (`band_rows`) is the tunable. `sweep` times candidate heights on
-representative porous beds on the current GPU and writes a JSON table keyed by lattice
-size, porosity, species count and storage; `lookup` returns the height of the nearest
-table entry for a problem (8 when there is no table). Solvers created with
-band_rows="auto" use it.
+The one launch of a time step runs gas tiles (a band of rows x a column range, with the
+one-node halo ring the energy correction needs) and wall and solid blocks. Three
+tunables shape it: the band height (`band_rows`, also the tiles' height), the gas nodes
+per tile (`tile_entries`, also the block size: smaller tiles mean more blocks per SM and
+more halo work) and the block order (`wall_order`: each band's wall blocks right after its
+gas tiles, or all wall blocks last). `sweep` times every combination of the candidate
+values on representative porous beds on the current GPU and writes a JSON table keyed by
+lattice size, porosity, species count and storage; `lookup` returns the best combination
+of the nearest table entry for a problem (the defaults when there is no table). Solvers
+created with band_rows="auto" use it.
 
 Run the sweep on the target GPU:  python -m paper_1804_07588_gb300.autotune --out FILE
 """
@@ -20,8 +23,10 @@ import os
 import numpy as np
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
-CANDIDATES = (4, 8, 16, 32, 64)
-DEFAULT_BAND = 8
+BANDS = (8, 16, 32)
+TILE_ENTRIES = (128, 192, 256)
+WALL_ORDERS = (0, 1)
+DEFAULT = (16, 256, 0)  # band_rows, tile_entries, wall_order
 
 
 def _porosity(p: dict) -> float:
@@ -33,11 +38,13 @@ def _key(p: dict, storage: str) -> dict:
             "ns": len(p["species"]), "storage": storage}
 
 
-def measure(p: dict, storage: str, band_rows: int, steps: int = 100, repeats: int = 3, device: int = 0) -> float:
+def measure(p: dict, storage: str, band_rows: int, tile_entries: int = 0, wall_order: int = 0, steps: int = 100,
+            repeats: int = 3, device: int = 0) -> float:
     """Microseconds per step of the step kernel (CUDA events on the solver's stream; the
     best of `repeats` runs of `steps` steps after 10 warm-up steps)."""
     from . import fdlbm
-    s = fdlbm.Solver(p, device=device, storage=storage, band_rows=band_rows)
+    s = fdlbm.Solver(p, device=device, storage=storage, band_rows=band_rows, tile_entries=tile_entries,
+                     wall_order=wall_order)
     s.step(10)
     s.sync()
     best = math.inf
@@ -52,12 +59,33 @@ def measure(p: dict, storage: str, band_rows: int, steps: int = 100, repeats: in
     return best
 
 
-def tune(p: dict, storage: str = "fp32", candidates=CANDIDATES, steps: int = 100, device: int = 0) -> dict:
-    times = {int(b): measure(p, storage, b, steps=steps, device=device) for b in candidates}
+def tune(p: dict, storage: str = "fp32", bands=BANDS, tiles=TILE_ENTRIES, orders=WALL_ORDERS, steps: int = 100,
+         device: int = 0) -> dict:
+    """Step time of every (band_rows, tile_entries, wall_order) combination; the entry
+    holds the fastest and all timings."""
+    times = {}
+    for b in bands:
+        for t in tiles:
+            for o in orders:
+                times[f"{b},{t},{o}"] = measure(p, storage, b, t, o, steps=steps, device=device)
     best = min(times, key=times.get)
+    b, t, o = (int(v) for v in best.split(","))
     entry = _key(p, storage)
-    entry.update({"band_rows": best, "us_per_step": times})
+    entry.update({"band_rows": b, "tile_entries": t, "wall_order": o, "us_per_step": times,
+                  "us_default": times.get(f"{DEFAULT[0]},{DEFAULT[1]},{DEFAULT[2]}")})
     return entry
+
+
+def _boolean_bed(nx: int, ny: int, por: float, seed: int) -> dict:
+    from . import workloads as W
+    while True:
+        try:
+            mask, _ = W.disk_mask_boolean(nx, ny, por, 6.0, 12.0, seed)
+            break
+        except ValueError:
+            seed += 1
+    return W._base(2, nx, ny, 1, mask, [W.INLET, W.OUTLET, W.PERIODIC, W.PERIODIC], u_inlet=0.01,
+                   inlet_profile=W.PLUG)
 
 
 def representative_problems():
@@ -65,8 +93,9 @@ def representative_problems():
     from . import workloads
     out = []
     for (nx, ny) in ((256, 128), (512, 192), (512, 256), (1024, 256), (1024, 512)):
-        for por in (0.6, 0.7):
-            out.append(workloads.porous_disks(nx=nx, ny=ny, porosity=por, seed=5000 + nx + ny))
+        for por in (0.45, 0.7):
+            out.append(workloads.porous_disks(nx=nx, ny=ny, porosity=por, seed=5000 + nx + ny) if por >= 0.6 else
+                       _boolean_bed(nx, ny, por, 5000 + nx + ny))
     return out
 
 
@@ -82,25 +111,27 @@ def sweep(out: str, storages=("fp32",), steps: int = 100, device: int = 0) -> li
     return entries
 
 
-def lookup(p: dict, storage: str = "fp32", table: str | None = None) -> int:
-    """band_rows of the nearest entry (log lattice size, porosity) with the same species
-    count and storage; DEFAULT_BAND without a matching table entry."""
+def lookup(p: dict, storage: str = "fp32", table: str | None = None) -> tuple:
+    """(band_rows, tile_entries, wall_order) of the nearest entry (log lattice size,
+    porosity) with the same species count and storage; DEFAULT without a matching table
+    entry."""
     path = table or TABLE
     try:
         with open(path) as f:
             entries = json.load(f)["entries"]
     except (OSError, ValueError, KeyError):
-        return DEFAULT_BAND
+        return DEFAULT
     k = _key(p, storage)
     cands = [e for e in entries if e["ns"] == k["ns"] and e["storage"] == storage] or \
             [e for e in entries if e["storage"] == storage]
     if not cands:
-        return DEFAULT_BAND
+        return DEFAULT
 
     def dist(e):
         return (abs(math.log(e["nx"] * e["ny"]) - math.log(k["nx"] * k["ny"])) +
                 4.0 * abs(e["porosity"] - k["porosity"]))
-    return int(min(cands, key=dist)["band_rows"])
+    e = min(cands, key=dist)
+    return int(e["band_rows"]), int(e.get("tile_entries", DEFAULT[1])), int(e.get("wall_order", DEFAULT[2]))
 
 
 def main():

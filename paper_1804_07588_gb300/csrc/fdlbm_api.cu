@@ -362,6 +362,12 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   }
   if (opts && opts->ledger_detail && (storage != FDLBM_STORAGE_FP32 || tr->local_tau))
     return fail(FDLBM_EINVAL, "exact accounts need FP32 storage and constant relaxation times");
+  if (opts && (opts->tile_entries != 0 && (opts->tile_entries % 32 != 0 || opts->tile_entries < 64 ||
+                                           opts->tile_entries > STEP_BLOCK)))
+    return fail(FDLBM_EINVAL, "tile_entries must be 0 or a multiple of 32 in [64, %d] (got %d)", STEP_BLOCK,
+                opts->tile_entries);
+  if (opts && opts->wall_order != 0 && opts->wall_order != 1)
+    return fail(FDLBM_EINVAL, "wall_order must be 0 or 1 (got %d)", opts->wall_order);
   {
     // Mole fractions: each in [0, 1], summing to 1 (initial and inlet composition).
     double sx0 = 0.0, sx1 = 0.0;
@@ -558,6 +564,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
   std::vector<uint16_t> gas_slot;
   {
     const int band = std::min(64, (opts && opts->band_rows > 0) ? opts->band_rows : 16);
+    const int cap = (opts && opts->tile_entries > 0) ? opts->tile_entries : STEP_BLOCK;
+    const bool walls_last = opts && opts->wall_order == 1;
+    P.block_threads = cap;
     auto is_gas = [&](int x, int y) { return G.cls_at(x, y) == GAS; };
     std::vector<int> wall_row(ny + 1, 0);
     for (int y = 0, w = 0; y <= ny; ++y) {
@@ -566,7 +575,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       for (int x = 0; x < nx; ++x) w += G.cls[x + nx * y] == WALL;
     }
     auto chunks = [&](int first, int last) {
-      for (int s0 = first; s0 < last; s0 += STEP_BLOCK) blocks.push_back(make_int4(1, s0, std::min(STEP_BLOCK, last - s0), 0));
+      for (int s0 = first; s0 < last; s0 += cap) blocks.push_back(make_int4(1, s0, std::min(cap, last - s0), 0));
     };
     auto push_entry = [&](int x, int y, int aux, int slot) {
       const int wx = ((x % nx) + nx) % nx, wy = ((y % ny) + ny) % ny;
@@ -594,7 +603,7 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
         int x1 = x0 + 1, inner = col_int[x0] + col_tb[x0];
         while (x1 < nx) {
           const int more = inner + col_int[x1] + col_tb[x1];
-          if (left + more + side(x1 + 1, x1) > STEP_BLOCK) break;
+          if (left + more + side(x1 + 1, x1) > cap) break;
           if (phi && (x1 + 1 - x0 + 2) * (H + 2) > GAS_MAP_SLOTS) break;
           inner = more;
           ++x1;
@@ -629,8 +638,9 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
         }
         x0 = x1;
       }
-      chunks(wall_row[y0], wall_row[y1]);
+      if (!walls_last) chunks(wall_row[y0], wall_row[y1]);
     }
+    if (walls_last) chunks(0, (int)walls.size());
     chunks((int)walls.size(), (int)solid_list.size());
   }
   P.n_gas = h->counts[GAS];

@@ -1141,7 +1141,7 @@ cudaError_t step_launch(const DevParams& P, const DevState& S, int src, cudaStre
   }
   const int dstb = 1 - src;
   const bool paper = MODE == 0 && P.coupling == FDLBM_COUPLING_PAPER;
-  step_kernel<PT, NS, PHI, LT, DET, MODE><<<P.n_blocks, GB, smem, st>>>(
+  step_kernel<PT, NS, PHI, LT, DET, MODE><<<P.n_blocks, P.block_threads, smem, st>>>(
       P, (const PT*)S.h[src], (PT*)S.h[dstb], S.code, S.gas_list, S.gas_slot, S.solid_list, S.blocks,
       MODE == 1 ? S.mom : nullptr, S.Ts[src], S.Ts[dstb], paper ? S.Tgas + (long long)src * P.n : nullptr,
       paper ? S.Tgas + (long long)dstb * P.n : nullptr, S.ledger, S.flags, S.rw, step, S.wall_u);

@@ -44,6 +44,7 @@ struct DevParams {
   int n_solid_list, n_wall_list;  // solid-list length, number of wall nodes
   int n_gas;            // gas-node list length
   int n_blocks;         // blocks of the fused step kernel
+  int block_threads;    // its block size (the gas-tile entry cap)
   int energy_correction, coupling;
   int fixedT_face[6];   // x-, x+, y-, y+, z-, z+
   // species

@@ -70,7 +70,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Options(C.Structure):
     _fields_ = [("storage", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("band_rows", C.c_int),
-                ("ledger_detail", C.c_int), ("strict_geometry", C.c_int)]
+                ("ledger_detail", C.c_int), ("strict_geometry", C.c_int), ("tile_entries", C.c_int),
+                ("wall_order", C.c_int)]
 
 
 class Info(C.Structure):
@@ -215,17 +216,20 @@ def create_args(p: dict, keep: list):
 class Solver:
     """One coupled FD-LBM problem on one GPU, built from a problem dict (see
     ``paper_1804_07588_gb300.workloads``). storage: "fp32", "bf16" or "fp16" population
-    storage (FP32 arithmetic in every case). band_rows: rows per band of the step
-    kernel's block order and height of the D2Q9 gas tiles (0: 16; "auto": the
-    autotuner's table). ledger_detail: every step also keeps the exact energy accounts of
-    ``balance()`` (FP32 storage, constant relaxation times). strict_geometry: reject
-    geometries whose pulls need the linear or no-interpolation fallbacks (concave corners,
-    narrow gaps) with FDLBM_EGEOM."""
+    storage (FP32 arithmetic in every case). The D2Q9 step kernel's block order:
+    band_rows, rows per band and height of the gas tiles (0: 16); tile_entries, gas
+    nodes per tile and block size (0: 256; a multiple of 32 in [64, 256]); wall_order, 0
+    wall blocks after each band's gas tiles, 1 after all of them. band_rows="auto" takes
+    all three from the autotuner's table. ledger_detail: every step also keeps the exact
+    energy accounts of ``balance()`` (FP32 storage, constant relaxation times).
+    strict_geometry: reject geometries whose pulls need the linear or no-interpolation
+    fallbacks (concave corners, narrow gaps) with FDLBM_EGEOM."""
 
     STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
 
     def __init__(self, p: dict, device: int = 0, stream=None, storage: str = "fp32", band_rows: int = 0,
-                 ledger_detail: bool = False, strict_geometry: bool = False):
+                 ledger_detail: bool = False, strict_geometry: bool = False, tile_entries: int = 0,
+                 wall_order: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("fdlbm.Solver needs a CUDA device (no CPU fallback)")
@@ -262,10 +266,13 @@ class Solver:
         self.storage = storage
         if band_rows == "auto":
             from . import autotune
-            band_rows = autotune.lookup(p, storage)
+            band_rows, tile_entries, wall_order = autotune.lookup(p, storage)
         self.band_rows = int(band_rows)
+        self.tile_entries = int(tile_entries)
+        self.wall_order = int(wall_order)
         opts = Options(self.STORAGE[storage], device, C.c_void_p(self.stream.cuda_stream), self._alloc_cb,
-                       self._free_cb, None, self.band_rows, int(bool(ledger_detail)), int(bool(strict_geometry)))
+                       self._free_cb, None, self.band_rows, int(bool(ledger_detail)), int(bool(strict_geometry)),
+                       self.tile_entries, self.wall_order)
         h = C.c_void_p()
         _check(L.fdlbm_create(C.byref(g), spec, ns, C.byref(tr), C.byref(kin), C.byref(fields),
                               C.byref(opts), C.byref(h)))

@@ -142,3 +142,36 @@ def test_batch_runs_members_to_steady_and_removes_them():
             assert r["steps"] == 100_000
         s.close()
     assert len({r["steps"] for r in conv}) > 1  # members leave at different times
+
+
+@pytest.mark.parametrize("band, tile, order", [(8, 128, 0), (32, 192, 1), (5, 64, 1)])
+def test_block_order_gives_the_same_bits(band, tile, order):
+    """The step kernel's block order (band height, gas nodes per tile, wall blocks per
+    band or last) changes which block does a node's work, not the node's arithmetic:
+    populations and moments are bit-identical to the default order's; the FP64 ledger
+    sums its per-block slots in another grouping, so it agrees to rounding."""
+    fdlbm = _fdlbm()
+    p = W.porous_disks(nx=192, ny=96, porosity=0.65, seed=41)
+    p["init"] = W.random_fields(p, seed=9, du=0.005)
+    a = fdlbm.Solver(p)
+    b = fdlbm.Solver(p, band_rows=band, tile_entries=tile, wall_order=order)
+    for s in (a, b):
+        s.step(150)
+        s.sync()
+    assert np.array_equal(a.populations().view(np.uint32), b.populations().view(np.uint32))
+    assert np.array_equal(a.moments_host().view(np.uint32), b.moments_host().view(np.uint32))
+    la, lb = a.balance(), b.balance()
+    fin = {k: v for k, v in la.items() if isinstance(v, float) and np.isfinite(v)}  # kept accounts only
+    scale = max(abs(v) for v in fin.values())
+    for k, v in fin.items():
+        assert abs(v - lb[k]) <= 1e-12 * scale, k
+    a.close()
+    b.close()
+
+
+def test_block_order_options_are_validated():
+    fdlbm = _fdlbm()
+    p = W.periodic_box(32, 16)
+    for kw in ({"tile_entries": 100}, {"tile_entries": 32}, {"tile_entries": 512}, {"wall_order": 2}):
+        with pytest.raises(fdlbm.FdlbmError):
+            fdlbm.Solver(p, **kw)
