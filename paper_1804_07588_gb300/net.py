@@ -316,3 +316,40 @@ def up2_only(h, fine_shape):
     out = torch.empty((N, D, H, W, cu), dtype=torch.bfloat16, device=h.device)
     _chk(lib().fdlbm_net_up2cat(_p(h), cu, None, 0, N, D, H, W, _p(out), _stream()))
     return out
+
+
+def _profile_main():
+    """Training iterations of the warm start's U-Net on a random batch (a fixed workload for
+    timing and profiling the network kernels): python -m paper_1804_07588_gb300.net
+    [--batch N] [--iters K]; prints the mean time per iteration."""
+    import argparse
+    import time
+
+    import numpy as np
+    import torch
+
+    from . import warmstart as WS
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=5)
+    args = ap.parse_args()
+    nx, ny, nz = WS.SHAPE
+    rng = np.random.default_rng(0)
+    x = torch.tensor(rng.normal(size=(args.batch, nz, ny, nx, 16)), dtype=torch.float32, device="cuda")
+    x = x.to(torch.bfloat16)
+    t = torch.tensor(rng.normal(size=(args.batch, nz, ny, nx, WS.N_OUT)), dtype=torch.float32, device="cuda")
+    model = WS.new_model(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.iters):
+        y = model.forward(x)
+        loss, gy = mse(y, t)
+        model.adam_step(model.backward(gy), lr=1e-3)
+    check()
+    torch.cuda.synchronize()
+    print(f"{(time.perf_counter() - t0) / args.iters * 1e3:.2f} ms per training iteration "
+          f"(batch {args.batch}, {nx}x{ny}x{nz})")
+
+
+if __name__ == "__main__":
+    _profile_main()
