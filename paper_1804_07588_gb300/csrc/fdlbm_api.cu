@@ -574,6 +574,25 @@ fdlbm_status fdlbm_create(const fdlbm_geometry* geom, const fdlbm_species* speci
       if (y == ny) break;
       for (int x = 0; x < nx; ++x) w += G.cls[x + nx * y] == WALL;
     }
+    // The wall nodes of a band, sorted by their set of arrival directions (stable, so by
+    // position within a set): the lanes of a warp then share their arrival and emission
+    // directions, and a warp steps through the union of its lanes' directions (on the
+    // 1024x512 bed with bands of 8 rows: 3.6 directions on average instead of 8.0 in
+    // row-major order; 2.6 per node).
+    {
+      auto arrivals = [&](int32_t k) {
+        uint32_t m = 0;
+        for (int i = 1; i < Q; ++i)
+          if (stencil_of(h->code[k], i) != ST_NOT_ARRIVAL) m |= 1u << i;
+        return m;
+      };
+      for (int y0 = 0; y0 < ny; y0 += band) {
+        const int y1 = std::min(ny, y0 + band);
+        std::stable_sort(walls.begin() + wall_row[y0], walls.begin() + wall_row[y1],
+                         [&](int32_t a, int32_t b) { return arrivals(a) < arrivals(b); });
+      }
+      std::copy(walls.begin(), walls.end(), solid_list.begin());
+    }
     auto chunks = [&](int first, int last) {
       for (int s0 = first; s0 < last; s0 += cap) blocks.push_back(make_int4(1, s0, std::min(cap, last - s0), 0));
     };

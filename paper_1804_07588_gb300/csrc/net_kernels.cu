@@ -135,6 +135,9 @@ struct FwdArgs {
   int seg_c[2];      // channels of each source (multiples of 8)
   int cout;          // output channels, a multiple of 16 (<= 128)
   int tmem_cols;
+  int a_stage, b_stage;  // bytes of one pipeline stage of the input tile and of the weights,
+                         // sized for the largest channel chunk of this call
+  int stages;            // halo kernel: stages in the ring (1 or 2)
   const float* bias;  // [cout] or null
   int relu;           // apply ReLU
   const __nv_bfloat16* mask;  // ReLU-backward mask (NDHWC, cout channels) or null
@@ -165,12 +168,12 @@ __device__ __forceinline__ void chunk_of(const FwdArgs& a, int q, int& src, int&
   src = 0, c0 = 0, cc = 0;
 }
 
-__global__ void __launch_bounds__(128, 1) conv3_fwd_kernel(const __grid_constant__ CUtensorMap tx0,
+__global__ void __launch_bounds__(128, 4) conv3_fwd_kernel(const __grid_constant__ CUtensorMap tx0,
                                                            const __grid_constant__ CUtensorMap tx1,
                                                            const __grid_constant__ CUtensorMap tw, FwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_STAGE_BYTES;
+  uint8_t* sB = smem + STAGES * a.a_stage;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tslot;
   __shared__ int fail, n_issued, n_used;
@@ -216,9 +219,9 @@ __global__ void __launch_bounds__(128, 1) conv3_fwd_kernel(const __grid_constant
         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
         const CUtensorMap* mx = src == 0 ? &tx0 : &tx1;
         for (int g = 0; g < ng; ++g) {
-          tma_load5(sA + s * A_STAGE_BYTES + g * (TILE_M * 16), mx, c0 + 8 * g, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, n,
+          tma_load5(sA + s * a.a_stage + g * (TILE_M * 16), mx, c0 + 8 * g, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1, n,
                     &full[s]);
-          tma_load3(sB + s * B_STAGE_BYTES + g * (a.cout * 16), &tw, woff + 8 * g, tap, 0, &full[s]);
+          tma_load3(sB + s * a.b_stage + g * (a.cout * 16), &tw, woff + 8 * g, tap, 0, &full[s]);
         }
         n_issued = it + 1;
       }
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(128, 1) conv3_fwd_kernel(const __grid_constant
         const int q = it % nq;
         int src, c0, cc, woff;
         chunk_of(a, q, src, c0, cc, woff);
-        const uint32_t abase = smem_u32(sA + s * A_STAGE_BYTES), bbase = smem_u32(sB + s * B_STAGE_BYTES);
+        const uint32_t abase = smem_u32(sA + s * a.a_stage), bbase = smem_u32(sB + s * a.b_stage);
         for (int k = 0; k < cc / 16; ++k) {
           const uint64_t da = umma_desc(abase + k * 2 * (TILE_M * 16), TILE_M * 16, 128);
           const uint64_t db = umma_desc(bbase + k * 2 * (a.cout * 16), a.cout * 16, 128);
@@ -282,6 +285,141 @@ __global__ void __launch_bounds__(128, 1) conv3_fwd_kernel(const __grid_constant
   if (warp == 0) tmem_free(tmem, a.tmem_cols);
 }
 
+// conv3_fwd_halo_kernel: the same convolution for volumes whose H is a multiple of 16,
+// with the input staged once per channel chunk instead of once per tap. Output tile: 8
+// voxels along x times 16 along y (one z plane), M = 128 rows, row group g = y offset, row
+// r within it = x offset. For each chunk of 16 input channels TMA loads the tile's input
+// box with its one-voxel halo, 10 x 18 x 3 voxels, as two 8-channel slabs laid out
+// [z][y][x][8 channels] (one 16-byte row per voxel), and the weights of all 27 taps of the
+// chunk; the A operand of tap (dz, dy, dx) is the same slab read from the offset of voxel
+// (dx, dy, dz): its 8-row groups (consecutive x) are 128 contiguous bytes, 160 bytes apart
+// along y (SBO), the second slab at the slab stride (LBO). So one load of the halo feeds 27
+// MMAs. Stages: a ring of `stages` chunks (1 or 2).
+constexpr int HX = 8, HY = 16;               // halo-kernel output tile (x, y)
+constexpr int HALO_ROWS = (HX + 2) * (HY + 2) * 3;  // 540 voxels of the halo box
+constexpr int HALO_SLAB = (HALO_ROWS * 16 + 127) / 128 * 128;  // bytes per 8-channel slab, 128-B aligned
+
+__global__ void __launch_bounds__(128, 4) conv3_fwd_halo_kernel(const __grid_constant__ CUtensorMap tx0,
+                                                                const __grid_constant__ CUtensorMap tx1,
+                                                                const __grid_constant__ CUtensorMap tw, FwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  // stage s: A slabs at smem + s * a.a_stage, B (27 taps x cout rows per slab) after the A
+  // stages at + s * a.b_stage
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + a.stages * a.a_stage;
+  __shared__ __align__(8) uint64_t full[2], empty[2], done;
+  __shared__ uint32_t tslot;
+  __shared__ int fail, n_issued, n_used;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tiles_x = a.W / HX, tiles_y = a.H / HY;
+  int t = blockIdx.x;
+  const int txi = t % tiles_x;
+  t /= tiles_x;
+  const int tyi = t % tiles_y;
+  t /= tiles_y;
+  const int z0 = t % a.D;
+  const int n = t / a.D;
+  const int x0 = txi * HX, y0 = tyi * HY;
+  // chunks of 16 channels over the sources
+  int nq = 0;
+  for (int s2 = 0; s2 < a.nseg; ++s2) nq += a.seg_c[s2] / 16;
+  const int ST = a.stages;
+  if (tid == 0) {
+    for (int s2 = 0; s2 < ST; ++s2) {
+      mbar_init(&full[s2], 1);
+      mbar_init(&empty[s2], 1);
+    }
+    mbar_init(&done, 1);
+    fail = 0;
+    n_issued = n_used = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) tmem_alloc(&tslot, a.tmem_cols);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const uint32_t bslab = 27u * (uint32_t)a.cout * 16u;  // bytes of one weight slab (all taps)
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      for (int it = 0; it < nq; ++it) {
+        const int s2 = it % ST;
+        if (!mbar_wait(&empty[s2], ((it / ST) & 1) ^ 1)) { fail = 1; break; }
+        // chunk it: source and first channel, weight column offset
+        int q = it, src = 0, c0 = 0, woff = 0;
+        for (int g = 0; g < a.nseg; ++g) {
+          const int ng = a.seg_c[g] / 16;
+          if (q < ng) { src = g; c0 = 16 * q; woff += c0; break; }
+          q -= ng;
+          woff += a.seg_c[g];
+        }
+        mbar_expect_tx(&full[s2], 2u * (uint32_t)(HALO_ROWS * 16) + 2u * bslab);
+        const CUtensorMap* mx = src == 0 ? &tx0 : &tx1;
+        for (int g = 0; g < 2; ++g) {
+          tma_load5(sA + s2 * a.a_stage + g * HALO_SLAB, mx, c0 + 8 * g, x0 - 1, y0 - 1, z0 - 1, n, &full[s2]);
+          tma_load3(sB + s2 * a.b_stage + g * bslab, &tw, woff + 8 * g, 0, 0, &full[s2]);
+        }
+        n_issued = it + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer: 27 taps per chunk
+      const uint32_t idesc = umma_idesc(128, a.cout, 0, 0);
+      for (int it = 0; it < nq; ++it) {
+        const int s2 = it % ST;
+        if (!mbar_wait(&full[s2], (it / ST) & 1)) { fail = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t abase = smem_u32(sA + s2 * a.a_stage), bbase = smem_u32(sB + s2 * a.b_stage);
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint32_t aoff = (uint32_t)(((dz * (HY + 2) + dy) * (HX + 2) + dx) * 16);
+          const uint64_t da = umma_desc(abase + aoff, HALO_SLAB, (HX + 2) * 16);
+          const uint64_t db = umma_desc(bbase + (uint32_t)tap * (uint32_t)a.cout * 16u, bslab, 128);
+          umma(tmem, da, db, idesc, (it > 0 || tap > 0) ? 1u : 0u);
+        }
+        umma_commit(&empty[s2]);
+        n_used = it + 1;
+      }
+      umma_commit(&done);
+    }
+    __syncwarp();
+  }
+  // Epilogue: warp w reads accumulator lanes 32w..32w+31; row r = (y offset) * 8 + x offset.
+  bool ok = mbar_wait(&done, 0) && !fail;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int r = tid;
+    const int x = x0 + r % HX, y = y0 + r / HX;
+    const long long v = (((long long)n * a.D + z0) * a.H + y) * a.W + x;
+    __nv_bfloat16* out = a.y + v * a.cout;
+    const __nv_bfloat16* mk = a.mask ? a.mask + v * a.cout : nullptr;
+    for (int c = 0; c < a.cout; c += 16) {
+      float f[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, f);
+      __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float val = f[i] + (a.bias ? a.bias[c + i] : 0.f);
+        if (a.relu) val = fmaxf(val, 0.f);
+        if (mk && !(__bfloat162float(mk[c + i]) > 0.f)) val = 0.f;
+        o[i] = __float2bfloat16_rn(val);
+      }
+      reinterpret_cast<uint4*>(out + c)[0] = reinterpret_cast<const uint4*>(o)[0];
+      reinterpret_cast<uint4*>(out + c)[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+  } else if (tid == 0) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0)
+    for (int it = n_used; it < n_issued; ++it) mbar_wait(&full[it % ST], (it / ST) & 1);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, a.tmem_cols);
+}
+
 struct WgradArgs {
   int D, H, W, N;
   int nseg;
@@ -289,17 +427,19 @@ struct WgradArgs {
   int cin;           // total input channels (row length of dW)
   int cout;          // gradient channels (<= 128; padded to M = 128)
   int tiles_per_cta;
+  int stages;        // pipeline stages (<= STAGES)
+  int b_stage;       // bytes of one input-tile stage (the channel chunk's slabs)
   float* gw;         // [cout][27][cin], accumulated
   int* err;
 };
 
 // grid: x = tap (27) x chunk, y = split over voxel tiles
-__global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_constant__ CUtensorMap tx0,
+__global__ void __launch_bounds__(128, 3) conv3_wgrad_kernel(const __grid_constant__ CUtensorMap tx0,
                                                              const __grid_constant__ CUtensorMap tx1,
                                                              const __grid_constant__ CUtensorMap tg, WgradArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                             // gradient tile: 16 channel groups x 128 voxels x 16 B
-  uint8_t* sB = smem + STAGES * (16 * TILE_M * 16);  // input tile: up to 8 channel groups
+  uint8_t* sB = smem + a.stages * (16 * TILE_M * 16);  // input tile: the chunk's channel groups
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tslot;
   __shared__ int fail, n_issued, n_used;
@@ -332,10 +472,11 @@ __global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_consta
   const int nstage = max(0, t_last - t_first);
   const int gA = (a.cout + 7) / 8, gB = cc / 8;
   // the gradient operand is padded to 128 rows with zeros that no load overwrites
-  for (int i = tid; i < STAGES * 16 * TILE_M * 16 / 16; i += blockDim.x) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < a.stages * 16 * TILE_M * 16 / 16; i += blockDim.x) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
   asm volatile("fence.proxy.async.shared::cta;");
+  const int ST = a.stages;
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -353,8 +494,8 @@ __global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_consta
   if (warp == 0) {
     if (lane == 0) {
       for (int it = 0; it < nstage; ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(&empty[s], ((it / STAGES) & 1) ^ 1)) { fail = 1; break; }
+        const int s = it % ST;
+        if (!mbar_wait(&empty[s], ((it / ST) & 1) ^ 1)) { fail = 1; break; }
         int tt = t_first + it;
         const int txi = tt % tiles_x;
         tt /= tiles_x;
@@ -367,7 +508,7 @@ __global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_consta
         for (int g = 0; g < gA; ++g)
           tma_load5(sA + s * (16 * TILE_M * 16) + g * (TILE_M * 16), &tg, 8 * g, x0, y0, z0, n, &full[s]);
         for (int g = 0; g < gB; ++g)
-          tma_load5(sB + s * A_STAGE_BYTES + g * (TILE_M * 16), mx, c0 + 8 * g, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1,
+          tma_load5(sB + s * a.b_stage + g * (TILE_M * 16), mx, c0 + 8 * g, x0 + dx - 1, y0 + dy - 1, z0 + dz - 1,
                     n, &full[s]);
         n_issued = it + 1;
       }
@@ -377,10 +518,10 @@ __global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_consta
     if (lane == 0) {
       const uint32_t idesc = umma_idesc(TILE_M, cc, 1, 1);
       for (int it = 0; it < nstage; ++it) {
-        const int s = it % STAGES;
-        if (!mbar_wait(&full[s], (it / STAGES) & 1)) { fail = 1; break; }
+        const int s = it % ST;
+        if (!mbar_wait(&full[s], (it / ST) & 1)) { fail = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t abase = smem_u32(sA + s * (16 * TILE_M * 16)), bbase = smem_u32(sB + s * A_STAGE_BYTES);
+        const uint32_t abase = smem_u32(sA + s * (16 * TILE_M * 16)), bbase = smem_u32(sB + s * a.b_stage);
         // K = voxels: 8 MMAs of 16 voxels; an 8-voxel group is 128 B within a channel slab
         for (int k = 0; k < TILE_M / 16; ++k) {
           const uint64_t da = umma_desc(abase + k * 256, 128, TILE_M * 16);
@@ -414,7 +555,7 @@ __global__ void __launch_bounds__(128, 1) conv3_wgrad_kernel(const __grid_consta
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (tid == 0)
-    for (int it = n_used; it < n_issued; ++it) mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+    for (int it = n_used; it < n_issued; ++it) mbar_wait(&full[it % ST], (it / ST) & 1);
   __syncthreads();
   if (warp == 0) tmem_free(tmem, 64);
 }
@@ -696,6 +837,30 @@ bool wt_map(CUtensorMap* m, const void* base, int cin, int cout) {
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The halo kernel's maps: the activation box with its one-voxel halo {8, HX + 2, HY + 2,
+// 3, 1}, and the weights of all taps of 8 input channels, {cin, cout, 27} with box {8,
+// cout, 27}, so that they land tap-major ([tap][o][8 channels]).
+bool act_map_halo(CUtensorMap* m, const void* base, int c, int N, int D, int H, int W) {
+  const cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {c * es, (cuuint64_t)W * c * es, (cuuint64_t)H * W * c * es,
+                                 (cuuint64_t)D * H * W * c * es};
+  const cuuint32_t box[5] = {8, HX + 2, HY + 2, 3, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+bool wt_map_taps(CUtensorMap* m, const void* base, int cin, int cout) {
+  const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 27};
+  const cuuint64_t strides[2] = {(cuuint64_t)27 * cin * 2, (cuuint64_t)cin * 2};
+  const cuuint32_t box[3] = {8, (cuuint32_t)cout, 27};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Per-device error flag of the network kernels (a few bytes, allocated on first use).
@@ -754,10 +919,18 @@ fdlbm_status fdlbm_conv3_fwd(const void* x0, int c0, const void* x1, int c1, int
   if (!aligned16(x0) || (x1 && !aligned16(x1)) || !aligned16(wt) || !aligned16(y))
     return net_fail(FDLBM_EINVAL, "conv3_fwd: tensors must be 16-byte aligned");
   if (!encode_fn()) return net_fail(FDLBM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  // the halo kernel for volumes with H a multiple of 16 whose stages fit shared memory
+  const int halo_a = 2 * HALO_SLAB, halo_b = 2 * 27 * cout * 16;
+  const int halo_chunks = c0 / 16 + c1 / 16;  // 16-channel chunks: one stage each in the ring
+  const int halo_stages = (halo_chunks > 1 && 2 * (halo_a + halo_b) <= 200 * 1024) ? 2 : 1;
+  const bool halo = H % HY == 0 && W % HX == 0 && halo_stages * (halo_a + halo_b) <= 220 * 1024;
   CUtensorMap m0, m1, mw;
-  if (!act_map(&m0, x0, c0, N, D, H, W) || !act_map(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) ||
-      !wt_map(&mw, wt, c0 + c1, cout))
-    return net_fail(FDLBM_EINVAL, "conv3_fwd: tensor map encoding failed");
+  const bool maps = halo ? (act_map_halo(&m0, x0, c0, N, D, H, W) &&
+                            act_map_halo(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) &&
+                            wt_map_taps(&mw, wt, c0 + c1, cout))
+                         : (act_map(&m0, x0, c0, N, D, H, W) &&
+                            act_map(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) && wt_map(&mw, wt, c0 + c1, cout));
+  if (!maps) return net_fail(FDLBM_EINVAL, "conv3_fwd: tensor map encoding failed");
   FwdArgs a{};
   a.D = D, a.H = H, a.W = W;
   a.nseg = c1 > 0 ? 2 : 1;
@@ -769,12 +942,32 @@ fdlbm_status fdlbm_conv3_fwd(const void* x0, int c0, const void* x1, int c1, int
   a.y = static_cast<__nv_bfloat16*>(y);
   a.err = err_flag();
   if (!a.err) return net_fail(FDLBM_ECUDA, "conv3_fwd: error flag");
-  const int smem = STAGES * (A_STAGE_BYTES + B_STAGE_BYTES);
+  // stages sized for the largest channel chunk (<= 64 channels), so that small layers
+  // leave shared memory for several CTAs per SM
+  const int cmax = std::min(64, std::max(c0, c1));
+  a.a_stage = (cmax / 8) * TILE_M * 16;
+  a.b_stage = (cmax / 8) * cout * 16;
+  // Several CTAs share an SM; padding the shared memory keeps their tensor-memory columns
+  // within the SM's 512 (228 KB of shared memory per SM: at most 512 / tmem_cols CTAs), so
+  // that tcgen05.alloc never has to wait for another CTA's columns.
+  const int per_sm = 512 / a.tmem_cols;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(conv3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(conv3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         STAGES * (A_STAGE_BYTES + B_STAGE_BYTES));
+    cudaFuncSetAttribute(conv3_fwd_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr = true;
   }
+  if (halo) {
+    a.a_stage = halo_a;
+    a.b_stage = halo_b;
+    a.stages = halo_stages;
+    const int smem = std::max(halo_stages * (halo_a + halo_b), 233472 / (per_sm + 1) + 1024);
+    const unsigned grid = (unsigned)N * D * (H / HY) * (W / HX);
+    conv3_fwd_halo_kernel<<<grid, 128, smem, (cudaStream_t)stream>>>(m0, m1, mw, a);
+    return check_launch("conv3_fwd");
+  }
+  const int smem = std::max(STAGES * (a.a_stage + a.b_stage), 233472 / (per_sm + 1) + 1024);
   const unsigned grid = (unsigned)N * (D / BZ) * (H / BY) * (W / BX);
   conv3_fwd_kernel<<<grid, 128, smem, (cudaStream_t)stream>>>(m0, m1, mw, a);
   return check_launch("conv3_fwd");
@@ -819,10 +1012,16 @@ fdlbm_status fdlbm_conv3_wgrad(const void* x0, int c0, const void* x1, int c1, i
   int splits = std::max(1, std::min(tiles, (152 * 4) / (27 * nq) + 1));
   a.tiles_per_cta = (tiles + splits - 1) / splits;
   splits = (tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
-  const int smem = STAGES * (16 * TILE_M * 16 + A_STAGE_BYTES);
+  // two stages, the input stage sized to the channel chunk: 72-96 KB, two or three CTAs per
+  // SM (64 tensor-memory columns each)
+  const int cmax = std::min(64, std::max(c0, c1));
+  a.stages = 2;
+  a.b_stage = (cmax / 8) * TILE_M * 16;
+  const int smem = a.stages * (16 * TILE_M * 16 + a.b_stage);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(conv3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(conv3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         STAGES * (16 * TILE_M * 16 + A_STAGE_BYTES));
     attr = true;
   }
   conv3_wgrad_kernel<<<dim3(27 * nq, splits), 128, smem, st>>>(m0, m1, mg, a);

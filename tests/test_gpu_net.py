@@ -62,12 +62,17 @@ def rel_max(a, b):
 SHAPE = (2, 8, 8, 16)  # N, D, H, W
 
 
+# H = 16: the halo-staged kernel (output tiles 8 x 16 x 1); H = 8: the per-tap kernel
+SHAPE_HALO = (1, 4, 16, 16)
+
+
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE_HALO])
 @pytest.mark.parametrize("c0, c1, cout", [(16, 0, 16), (16, 0, 32), (64, 0, 64), (32, 16, 16), (64, 32, 128),
-                                          (64, 64, 64), (16, 0, 48)])
-def test_conv3_forward(c0, c1, cout):
+                                          (64, 64, 64), (16, 0, 48), (32, 64, 96)])
+def test_conv3_forward(c0, c1, cout, shape):
     net = _net()
     rng = np.random.default_rng(c0 * 7 + c1 + cout)
-    N, D, H, W = SHAPE
+    N, D, H, W = shape
     x = bf16_round(rng.normal(size=(N, D, H, W, c0 + c1)))
     w = bf16_round(rng.normal(size=(cout, c0 + c1, 3, 3, 3)) / np.sqrt(27 * (c0 + c1)))
     b = rng.normal(size=cout) * 0.1
@@ -88,13 +93,14 @@ def test_conv3_forward(c0, c1, cout):
     assert rel_max(y2.float().cpu().numpy(), ref2) <= 1e-2
 
 
-@pytest.mark.parametrize("cin, cout", [(16, 16), (48, 16), (32, 64), (128, 64)])
-def test_conv3_data_gradient(cin, cout):
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE_HALO])
+@pytest.mark.parametrize("cin, cout", [(16, 16), (48, 16), (32, 64), (128, 64), (96, 32)])
+def test_conv3_data_gradient(cin, cout, shape):
     """The input gradient (the forward kernel with flipped, transposed weights) against
     the oracle's adjoint."""
     net = _net()
     rng = np.random.default_rng(cin + 3 * cout)
-    N, D, H, W = SHAPE
+    N, D, H, W = shape
     x = rng.normal(size=(N, D, H, W, cin))
     w = bf16_round(rng.normal(size=(cout, cin, 3, 3, 3)) / np.sqrt(27 * cin))
     gy = bf16_round(rng.normal(size=(N, D, H, W, cout)))
