@@ -560,6 +560,130 @@ __global__ void __launch_bounds__(128, 3) conv3_wgrad_kernel(const __grid_consta
   if (warp == 0) tmem_free(tmem, 64);
 }
 
+// conv3_wgrad_halo_kernel: the weight gradient for volumes with H a multiple of 16 and a
+// 16-channel input chunk per CTA, all 27 taps at once. The accumulators of the taps sit
+// side by side in tensor memory (tap t: columns 16 t .. 16 t + 15, 432 of 512). Per voxel
+// tile (8 x 16 x 1, voxel k = 8 y + x) TMA loads the output gradient (MN-major A: gradient
+// channels padded to 128 rows with zeros, 8-voxel K groups 128 B apart) and the input with
+// its one-voxel halo (the forward halo kernel's layout); the B operand of tap (dz, dy, dx) is
+// the halo read from voxel (dx, dy, dz): an 8-voxel K group is one halo row of 8
+// consecutive x (128 contiguous bytes), the next K group 160 bytes on (LBO), the next 8
+// channels a slab further (SBO). 27 taps x 8 MMAs per tile; the partial sums of the CTA's
+// tiles are added into dW with FP32 atomics.
+__global__ void __launch_bounds__(128, 1) conv3_wgrad_halo_kernel(const __grid_constant__ CUtensorMap tx0,
+                                                                  const __grid_constant__ CUtensorMap tx1,
+                                                                  const __grid_constant__ CUtensorMap tg, WgradArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int A_ST = 16 * TILE_M * 16;          // gradient tile: 16 slabs x 128 voxels x 16 B
+  constexpr int B_ST = 2 * HALO_SLAB;             // input halo: 2 slabs
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + 2 * A_ST;
+  __shared__ __align__(8) uint64_t full[2], empty[2], done;
+  __shared__ uint32_t tslot;
+  __shared__ int fail, n_issued, n_used;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the CTA's 16-channel chunk
+  int q = blockIdx.x, src = 0, c0 = 0, woff = 0;
+  for (int g = 0; g < a.nseg; ++g) {
+    const int ng = a.seg_c[g] / 16;
+    if (q < ng) { src = g; c0 = 16 * q; woff += c0; break; }
+    q -= ng;
+    woff += a.seg_c[g];
+  }
+  const int tiles_x = a.W / HX, tiles_y = a.H / HY;
+  const int total_tiles = tiles_x * tiles_y * a.D * a.N;
+  const int t_first = blockIdx.y * a.tiles_per_cta;
+  const int t_last = min(total_tiles, t_first + a.tiles_per_cta);
+  const int nstage = max(0, t_last - t_first);
+  const int gA = (a.cout + 7) / 8;
+  for (int i = tid; i < 2 * A_ST / 16; i += blockDim.x) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
+  asm volatile("fence.proxy.async.shared::cta;");
+  if (tid == 0) {
+    for (int s2 = 0; s2 < 2; ++s2) {
+      mbar_init(&full[s2], 1);
+      mbar_init(&empty[s2], 1);
+    }
+    mbar_init(&done, 1);
+    fail = 0;
+    n_issued = n_used = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) tmem_alloc(&tslot, 512);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const CUtensorMap* mx = src == 0 ? &tx0 : &tx1;
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int it = 0; it < nstage; ++it) {
+        const int s2 = it & 1;
+        if (!mbar_wait(&empty[s2], ((it >> 1) & 1) ^ 1)) { fail = 1; break; }
+        int tt = t_first + it;
+        const int txi = tt % tiles_x;
+        tt /= tiles_x;
+        const int tyi = tt % tiles_y;
+        tt /= tiles_y;
+        const int z0 = tt % a.D;
+        const int n = tt / a.D;
+        const int x0 = txi * HX, y0 = tyi * HY;
+        mbar_expect_tx(&full[s2], (uint32_t)(gA * TILE_M * 16 + 2 * HALO_ROWS * 16));
+        for (int g = 0; g < gA; ++g)
+          tma_load5(sA + s2 * A_ST + g * (TILE_M * 16), &tg, 8 * g, x0, y0, z0, n, &full[s2]);
+        for (int g = 0; g < 2; ++g)
+          tma_load5(sB + s2 * B_ST + g * HALO_SLAB, mx, c0 + 8 * g, x0 - 1, y0 - 1, z0 - 1, n, &full[s2]);
+        n_issued = it + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc(TILE_M, 16, 1, 1);
+      for (int it = 0; it < nstage; ++it) {
+        const int s2 = it & 1;
+        if (!mbar_wait(&full[s2], (it >> 1) & 1)) { fail = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t abase = smem_u32(sA + s2 * A_ST), bbase = smem_u32(sB + s2 * B_ST);
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint32_t boff = (uint32_t)(((dz * (HY + 2) + dy) * (HX + 2) + dx) * 16);
+          for (int k = 0; k < TILE_M / 16; ++k) {  // K = 16 voxels = two tile rows
+            const uint64_t da = umma_desc(abase + k * 256, 128, TILE_M * 16);
+            const uint64_t db = umma_desc(bbase + boff + k * 2 * (HX + 2) * 16, (HX + 2) * 16, HALO_SLAB);
+            umma(tmem + (uint32_t)(16 * tap), da, db, idesc, (it > 0 || k > 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(&empty[s2]);
+        n_used = it + 1;
+      }
+      umma_commit(&done);
+    }
+    __syncwarp();
+  }
+  bool ok = mbar_wait(&done, 0) && !fail;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok && nstage > 0) {
+    const int o = tid;  // accumulator row = gradient channel
+    for (int tap = 0; tap < 27; ++tap) {
+      float f[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * tap), f);
+      if (o < a.cout) {
+        float* dst = a.gw + ((long long)o * 27 + tap) * a.cin + woff;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) atomicAdd(dst + i, f[i]);
+      }
+    }
+  } else if (!ok && tid == 0) {
+    atomicExch(a.err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0)
+    for (int it = n_used; it < n_issued; ++it) mbar_wait(&full[it & 1], (it >> 1) & 1);
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, 512);
+}
+
 // ---- small layers (CUDA cores) ---------------------------------------------------------
 
 // y[v][o] (flipped transpose for the data gradient): W'[c][tap][o] = W[o][26 - tap][c]
@@ -851,6 +975,18 @@ bool act_map_halo(CUtensorMap* m, const void* base, int c, int N, int D, int H, 
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+// The halo weight-gradient kernel's output-gradient tile, box {8, HX, HY, 1, 1}.
+bool act_map_tile(CUtensorMap* m, const void* base, int c, int N, int D, int H, int W) {
+  const cuuint64_t dims[5] = {(cuuint64_t)c, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)N};
+  const cuuint64_t es = 2;
+  const cuuint64_t strides[4] = {c * es, (cuuint64_t)W * c * es, (cuuint64_t)H * W * c * es,
+                                 (cuuint64_t)D * H * W * c * es};
+  const cuuint32_t box[5] = {8, HX, HY, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 bool wt_map_taps(CUtensorMap* m, const void* base, int cin, int cout) {
   const cuuint64_t dims[3] = {(cuuint64_t)cin, (cuuint64_t)cout, 27};
   const cuuint64_t strides[2] = {(cuuint64_t)27 * cin * 2, (cuuint64_t)cin * 2};
@@ -990,15 +1126,52 @@ fdlbm_status fdlbm_conv3_wgrad(const void* x0, int c0, const void* x1, int c1, i
   if (!aligned16(x0) || (x1 && !aligned16(x1)) || !aligned16(gy))
     return net_fail(FDLBM_EINVAL, "conv3_wgrad: tensors must be 16-byte aligned");
   if (!encode_fn()) return net_fail(FDLBM_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  // the halo kernel (all taps per 16-channel chunk) for volumes with H a multiple of 16
+  const bool halo = H % HY == 0 && W % HX == 0;
   CUtensorMap m0, m1, mg;
-  if (!act_map(&m0, x0, c0, N, D, H, W) || !act_map(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) ||
-      !act_map(&mg, gy, cout, N, D, H, W))
-    return net_fail(FDLBM_EINVAL, "conv3_wgrad: tensor map encoding failed");
+  const bool maps = halo ? (act_map_halo(&m0, x0, c0, N, D, H, W) &&
+                            act_map_halo(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) &&
+                            act_map_tile(&mg, gy, cout, N, D, H, W))
+                         : (act_map(&m0, x0, c0, N, D, H, W) &&
+                            act_map(&m1, c1 > 0 ? x1 : x0, c1 > 0 ? c1 : c0, N, D, H, W) &&
+                            act_map(&mg, gy, cout, N, D, H, W));
+  if (!maps) return net_fail(FDLBM_EINVAL, "conv3_wgrad: tensor map encoding failed");
   cudaStream_t st = (cudaStream_t)stream;
   const int cin = c0 + c1;
   if (cudaMemsetAsync(gw, 0, sizeof(float) * (size_t)cout * 27 * cin, st) != cudaSuccess)
     return check_launch("conv3_wgrad memset");
   WgradArgs a{};
+  if (halo) {
+    a.D = D, a.H = H, a.W = W, a.N = N;
+    a.nseg = c1 > 0 ? 2 : 1;
+    a.seg_c[0] = c0, a.seg_c[1] = c1;
+    a.cin = cin, a.cout = cout;
+    a.gw = gw;
+    a.err = err_flag();
+    if (!a.err) return net_fail(FDLBM_ECUDA, "conv3_wgrad: error flag");
+    const int tiles = N * D * (H / HY) * (W / HX);
+    const int nq = c0 / 16 + c1 / 16;
+    // one CTA per SM (it holds all 512 tensor-memory columns): about one wave
+    int splits = std::max(1, std::min(tiles, 152 / nq));
+    a.tiles_per_cta = (tiles + splits - 1) / splits;
+    splits = (tiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
+    // two stages of 32 KB + 17 KB, padded so that no second CTA (and tcgen05.alloc of
+    // another 512 columns) shares the SM
+    const int smem = std::max(2 * (16 * TILE_M * 16 + 2 * HALO_SLAB), 120 * 1024);
+    static bool hattr = false;
+    if (!hattr) {
+      cudaFuncSetAttribute(conv3_wgrad_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      hattr = true;
+    }
+    conv3_wgrad_halo_kernel<<<dim3(nq, splits), 128, smem, st>>>(m0, m1, mg, a);
+    fdlbm_status s = check_launch("conv3_wgrad");
+    if (s != FDLBM_OK || !gb) return s;
+    if (cudaMemsetAsync(gb, 0, sizeof(float) * cout, st) != cudaSuccess) return check_launch("bias grad memset");
+    const long long nvox = (long long)N * D * H * W;
+    bias_grad_kernel<<<std::max(1, std::min(1024, (int)(nvox / 64))), (256 / cout) * cout, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(gy), cout, nvox, gb);
+    return check_launch("bias grad");
+  }
   a.D = D, a.H = H, a.W = W, a.N = N;
   a.nseg = c1 > 0 ? 2 : 1;
   a.seg_c[0] = c0, a.seg_c[1] = c1;

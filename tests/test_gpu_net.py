@@ -110,12 +110,13 @@ def test_conv3_data_gradient(cin, cout, shape):
     assert rel_max(gx.float().cpu().numpy(), ref) <= 1e-2
 
 
+@pytest.mark.parametrize("shape", [SHAPE, SHAPE_HALO])
 @pytest.mark.parametrize("c0, c1, cout", [(16, 0, 16), (16, 0, 32), (64, 0, 64), (32, 16, 16), (64, 64, 64),
-                                          (32, 0, 128)])
-def test_conv3_weight_gradient(c0, c1, cout):
+                                          (32, 0, 128), (48, 0, 8)])
+def test_conv3_weight_gradient(c0, c1, cout, shape):
     net = _net()
     rng = np.random.default_rng(100 + c0 + c1 + cout)
-    N, D, H, W = SHAPE
+    N, D, H, W = shape
     x = bf16_round(rng.normal(size=(N, D, H, W, c0 + c1)))
     gy = bf16_round(rng.normal(size=(N, D, H, W, cout)))
     w = np.zeros((cout, c0 + c1, 3, 3, 3))
