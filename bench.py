@@ -93,6 +93,17 @@ def kernel_source_hash(three_d=False):
     return h.hexdigest()[:16]
 
 
+def variant_traffic(name, three_d):
+    """DRAM bytes per step of a bench variant from the committed ncu table, or None when the
+    kernel source changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "variant_traffic.json")) as f:
+            e = json.load(f)["variants"][name]
+    except Exception:
+        return None
+    return e["dram_bytes_per_step"] if e.get("kernel_source_sha") == kernel_source_hash(three_d) else None
+
+
 def ncu_traffic(three_d=False):
     """DRAM bytes per step-kernel launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
@@ -615,6 +626,7 @@ def run_fdlbm(args, rank, world, local_rank):
                 if q is None:
                     q = workloads.config2()
                 variants[name] = measure(fdlbm, q, storage, k, w, dev, flush, Qv)
+                variants[name]["roofline"]["traffic"] = variant_traffic(name, Qv == 19)
             except Exception as e:
                 variants[name] = {"error": str(e)[:200]}
 
