@@ -1052,15 +1052,16 @@ cudaError_t step3_launch(const DevParams& P, const DevState& S, int src, bool mo
   const PT* hs = static_cast<const PT*>(S.h[src]);
   cudaError_t e;
   const int gas_grid = (P.n_gas + G3 - 1) / G3;
+  // The field pass and the moments pass keep no pulled values (they return before any use
+  // of shared memory): launched without dynamic shared memory, they run at the occupancy
+  // their registers allow (32 warps per SM) instead of the step kernel's 16.
   if (PHI && P.n_gas > 0) {
-    if ((e = opt_in_smem3(gas_pass_kernel3<PT, NS, PHI, 2>, smem, configured[2])) != cudaSuccess) return e;
-    gas_pass_kernel3<PT, NS, PHI, 2><<<gas_grid, G3, smem, st>>>(P, hs, S.code64, S.gas_list, nullptr, S.F[0], nullptr);
+    gas_pass_kernel3<PT, NS, PHI, 2><<<gas_grid, G3, 0, st>>>(P, hs, S.code64, S.gas_list, nullptr, S.F[0], nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (moments_only) {
     if (P.n_gas <= 0) return cudaSuccess;
-    if ((e = opt_in_smem3(gas_pass_kernel3<PT, NS, PHI, 1>, smem, configured[1])) != cudaSuccess) return e;
-    gas_pass_kernel3<PT, NS, PHI, 1><<<gas_grid, G3, smem, st>>>(P, hs, S.code64, S.gas_list, S.F[0], nullptr, S.mom);
+    gas_pass_kernel3<PT, NS, PHI, 1><<<gas_grid, G3, 0, st>>>(P, hs, S.code64, S.gas_list, S.F[0], nullptr, S.mom);
     return cudaGetLastError();
   }
   if (P.n_blocks <= 0) return cudaSuccess;
