@@ -125,6 +125,11 @@ __device__ __forceinline__ void pop_store_ghosts(PT* p, int k, const Ghost& g, f
   pop_put_ghosts(p, k, g, pop_round<PT>(v, sc, sizeof(PT) == 4 ? 0U : pop_random(seed, q)));
 }
 
+// Species whose pulled values a gas-tile thread keeps in shared memory rather than registers
+// (the last two; NS <= 2: the last one).
+template <int NS>
+constexpr int NSC_OF = NS >= 3 ? 2 : 1;
+
 // Running species moments of pulled deviations.
 template <int NS>
 struct Acc {
@@ -184,13 +189,15 @@ __constant__ int2 c_st_m[8] = {{0, 0}, {-2, 0}, {0, 1}, {-2, -3}, {0, 0}, {-2, -
 template <class PT, int NS, int I, bool DET>
 __device__ __forceinline__ void pull_dir(const DevParams& P, const PT* __restrict__ src,
                                          const uint32_t* __restrict__ code, int k, uint32_t cw, Acc<NS>& a,
-                                         float (&hv)[NS * Q], const float (&ecoef)[3], Acct* ac) {
+                                         float (&hv)[NS * Q], float* __restrict__ scol, const float (&ecoef)[3],
+                                         Acct* ac) {
   constexpr int e2 = EX(I) * EX(I) + EY(I) * EY(I);
   if (I == 0) {
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
       const float v = pop_ld(src + ((j * Q) * (int)P.plane + k), P.hsi[j]);
-      hv[j * Q] = v;
+      if (j >= NS - NSC_OF<NS>) scol[(j - (NS - NSC_OF<NS>)) * Q * GB] = v;
+      else hv[j * Q] = v;
       a.dr[j] += v;
       a.e[j] = fmaf(ecoef[0], v, a.e[j]);
     }
@@ -240,7 +247,8 @@ __device__ __forceinline__ void pull_dir(const DevParams& P, const PT* __restric
         else ac->qout -= own;
       }
     }
-    hv[j * Q + I] = v;
+    if (j >= NS - NSC_OF<NS>) scol[((j - (NS - NSC_OF<NS>)) * Q + I) * GB] = v;
+    else hv[j * Q + I] = v;
     a.dr[j] += v;
     if (EX(I) > 0) a.ax[j] += v;
     if (EX(I) < 0) a.ax[j] -= v;
@@ -255,19 +263,19 @@ __device__ __forceinline__ void pull_dir(const DevParams& P, const PT* __restric
 template <class PT, int NS, bool DET>
 __device__ __forceinline__ void pull_node(const DevParams& P, const PT* __restrict__ src,
                                           const uint32_t* __restrict__ code, int k, uint32_t cw, Acc<NS>& a,
-                                          float (&hv)[NS * Q], Acct* ac) {
+                                          float (&hv)[NS * Q], float* __restrict__ scol, Acct* ac) {
   const float ecoef[3] = {-2.f * P.Tref, 1.f - 2.f * P.Tref, 2.f - 2.f * P.Tref};
 #pragma unroll
   for (int j = 0; j < NS; ++j) a.dr[j] = a.ax[j] = a.ay[j] = a.e[j] = 0.f;
-  pull_dir<PT, NS, 0, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 1, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 2, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 3, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 4, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 5, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 6, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 7, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
-  pull_dir<PT, NS, 8, DET>(P, src, code, k, cw, a, hv, ecoef, ac);
+  pull_dir<PT, NS, 0, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 1, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 2, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 3, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 4, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 5, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 6, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 7, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
+  pull_dir<PT, NS, 8, DET>(P, src, code, k, cw, a, hv, scol, ecoef, ac);
 }
 
 // Mixture moments from the species accumulators (Eq. moments_of_g, Eq. moments_of_f):
@@ -357,6 +365,9 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
   Mom<NS> m;
   float t1l[NS], t2l[NS];
   float hv[NS * Q];  // the pulled populations, in registers until the collision
+  // ... except those of the last NSC_OF<NS> species, in the thread's column of shared memory
+  // (stride GB): fewer live registers leave less to spill within 80 registers
+  float* s_col = smem + (1 + NS) * GAS_MAP_SLOTS + tid;
   if (tid < n_tot) {
     const int2 g = __ldg(gas_list + d.y + tid);
     k = g.x;
@@ -364,7 +375,7 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
     if (PHI) slot = __ldg(gas_slot + d.y + tid);
     cw = __ldg(code + k);
     Acct halo_acct{0.0, 0.0, 0.0, 0.0};  // halo entries are counted by their own tile
-    pull_node<PT, NS, DET>(P, src, code, k, cw, acc, hv, tid < n_int ? ac : &halo_acct);
+    pull_node<PT, NS, DET>(P, src, code, k, cw, acc, hv, s_col, tid < n_int ? ac : &halo_acct);
     finish_moments<NS>(P, acc, m);
     // Local relaxation times: tau1_j = mu_j / (C T sum_k X_k phi_jk), tau2_j = rho_j D_j /
     // (X_j C T) = M_j (1 - Y_j) / (T sum_{k != j} X_k / D_jk), T the g-temperature.
@@ -456,7 +467,8 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
   for (int j = 0; j < NS; ++j) {
     float h[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = hv[j * Q + i];
+    for (int i = 0; i < Q; ++i)
+      h[i] = j >= NS - NSC_OF<NS> ? s_col[((j - (NS - NSC_OF<NS>)) * Q + i) * GB] : hv[j * Q + i];
     const float drj = m.drho[j];
     const float Jxj = m.Jx[j], Jyj = m.Jy[j], dqj = divq[j];
     const float rho = P.rref[j] + drj;
@@ -577,7 +589,7 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
 
 template <int NS, bool LT = false>
 size_t gas_smem_bytes() {
-  return sizeof(float) * (1 + NS) * GAS_MAP_SLOTS;
+  return sizeof(float) * ((1 + NS) * GAS_MAP_SLOTS + NSC_OF<NS> * Q * GB);  // moment map + the shared species' column
 }
 
 // ---------------------------------------------------------------------------------------
