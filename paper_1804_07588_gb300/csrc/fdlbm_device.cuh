@@ -17,10 +17,9 @@ namespace fdlbm {
 namespace {
 
 constexpr int GB = 256;  // gas kernel block size (threads = gas nodes)
-// Resident blocks of the step kernel per SM: 3 caps it at 80 registers (the pulled values
-// of a node partly spill to local memory, ~150 B per thread) and runs 24 warps per SM; on
-// the 1024x512 bed it is 7% faster than 2 blocks at 128 registers without spills, while 4
-// blocks (64 registers) spill too much to gain.
+// Resident blocks of the step kernel per SM: 3 caps it at 80 registers (with part of the
+// pulled values in shared memory, see NSC_OF) and runs 24 warps per SM: on the 1024x512 bed
+// 10% faster than 2 blocks at 128 registers; 4 blocks (64 registers) spill and lose.
 #ifndef GAS_MIN_BLOCKS
 #define GAS_MIN_BLOCKS 3
 #endif
@@ -126,9 +125,11 @@ __device__ __forceinline__ void pop_store_ghosts(PT* p, int k, const Ghost& g, f
 }
 
 // Species whose pulled values a gas-tile thread keeps in shared memory rather than registers
-// (the last two; NS <= 2: the last one).
+// (the last three, or all of them for NS <= 3): with the other pulled values and the
+// collision's temporaries the kernel then fits 80 registers without spills (three blocks per
+// SM; 43 KB of shared memory per block for 5 species).
 template <int NS>
-constexpr int NSC_OF = NS >= 3 ? 2 : 1;
+constexpr int NSC_OF = NS > 3 ? 3 : NS;
 
 // Running species moments of pulled deviations.
 template <int NS>
@@ -366,7 +367,7 @@ __device__ __forceinline__ void gas_tile(const DevParams& P, const PT* __restric
   float t1l[NS], t2l[NS];
   float hv[NS * Q];  // the pulled populations, in registers until the collision
   // ... except those of the last NSC_OF<NS> species, in the thread's column of shared memory
-  // (stride GB): fewer live registers leave less to spill within 80 registers
+  // (stride GB)
   float* s_col = smem + (1 + NS) * GAS_MAP_SLOTS + tid;
   if (tid < n_tot) {
     const int2 g = __ldg(gas_list + d.y + tid);
