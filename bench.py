@@ -233,20 +233,24 @@ def run_to_steady(fdlbm, p, init=None, tol=1e-6, every=500, max_steps=400_000, d
     to reach the steady-state residual tol, checked every `every` steps."""
     import torch
     s = fdlbm.Solver(p, device=device, storage=storage)
-    if init is not None:
-        s.set_fields(init)
-    s.residual()
-    torch.cuda.synchronize(device)
-    t0 = time.perf_counter()
-    steps, r = 0, float("inf")
-    while steps < max_steps:
-        s.step(every)
-        steps += every
-        r = s.residual()
-        if r < tol:
-            break
-    s.sync()
-    el = time.perf_counter() - t0
+    try:
+        if init is not None:
+            s.set_fields(init)
+        s.residual()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        steps, r = 0, float("inf")
+        while steps < max_steps:
+            s.step(every)
+            steps += every
+            r = s.residual()
+            if r < tol:
+                break
+        s.sync()
+        el = time.perf_counter() - t0
+    except BaseException:
+        s.close()                       # the caller never sees this solver
+        raise
     return s, {"steps": steps, "seconds": el, "residual": r, "converged": r < tol}
 
 
@@ -258,8 +262,10 @@ def time_to_steady(fdlbm, workloads, device=0):
     p = workloads.config0()
     near = workloads.config0(u_inlet=0.018)
     s_near, _ = run_to_steady(fdlbm, near, device=device)
-    warm_init = s_near.restart_fields()
-    s_near.close()
+    try:
+        warm_init = s_near.restart_fields()
+    finally:
+        s_near.close()
     s, cold = run_to_steady(fdlbm, p, device=device)
     s.close()
     s, warm = run_to_steady(fdlbm, p, init=warm_init, device=device)
@@ -286,24 +292,26 @@ def precision_handoff(fdlbm, p, storage, device=0, tol=1e-6, every=500, stall_ch
     solver that runs to tol. Steps and wall time of both phases and in total."""
     import torch
     s = fdlbm.Solver(p, device=device, storage=storage)
-    s.residual()
-    torch.cuda.synchronize(device)
-    t0 = time.perf_counter()
-    steps, best, since = 0, float("inf"), 0
-    while steps < max_steps:
-        s.step(every)
-        steps += every
-        r = s.residual()
-        if r < tol:
-            break
-        if r < best:
-            best, since = r, 0
-        else:
-            since += 1
-            if since >= stall_checks:
+    try:
+        s.residual()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        steps, best, since = 0, float("inf"), 0
+        while steps < max_steps:
+            s.step(every)
+            steps += every
+            r = s.residual()
+            if r < tol:
                 break
-    init = s.restart_fields()
-    s.close()
+            if r < best:
+                best, since = r, 0
+            else:
+                since += 1
+                if since >= stall_checks:
+                    break
+        init = s.restart_fields()
+    finally:
+        s.close()
     t16 = time.perf_counter() - t0
     s32, rest = run_to_steady(fdlbm, p, init=init, tol=tol, device=device)
     s32.close()

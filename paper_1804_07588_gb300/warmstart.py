@@ -110,10 +110,14 @@ def solve(p: dict, init=None, tol=1e-6, every=250, max_steps=200_000, device=0):
 
     from . import fdlbm
     s = fdlbm.Solver(p, device=device)
-    if init is not None:
-        s.set_fields(init)
-    s.residual()
-    torch.cuda.synchronize(device)
+    try:
+        if init is not None:
+            s.set_fields(init)
+        s.residual()
+        torch.cuda.synchronize(device)
+    except BaseException:
+        s.close()                       # the caller never sees this solver
+        raise
     t0 = time.perf_counter()
     steps, r, diverged = 0, float("inf"), False
     try:
@@ -129,6 +133,9 @@ def solve(p: dict, init=None, tol=1e-6, every=250, max_steps=200_000, device=0):
         s.sync()
     except fdlbm.FdlbmError:
         diverged = True
+    except BaseException:
+        s.close()
+        raise
     el = time.perf_counter() - t0
     return s, {"steps": steps, "seconds": el, "residual": r, "converged": (r < tol) and not diverged,
                "diverged": diverged}
@@ -139,8 +146,10 @@ def generate(problems, tol=1e-6, every=250, max_steps=200_000, device=0) -> list
     data = []
     for p in problems:
         s, st = solve(p, None, tol, every, max_steps, device)
-        m = s.moments_host(t_dev=True).astype(np.float64)
-        s.close()
+        try:
+            m = s.moments_host(t_dev=True).astype(np.float64)
+        finally:
+            s.close()
         data.append({"x": network_input(p), "y": target_fields(p, m), "stats": st})
     return data
 
