@@ -313,6 +313,84 @@ def test_trace_species_diffusion3(species):
     assert abs(D0 / D_th - 1.0) < 0.01, (D1, D2, D0, D_th)
 
 
+_PLANES = {"xy": (0, 1), "xz": (0, 2), "yz": (1, 2)}
+
+
+def _diagonal_mode3(plane, sgn, n, steps, u0=0.0, species="CO2"):
+    """A trace-species mode cos(2 pi (a + sgn b) / n) on an n x n periodic plane of the
+    box (a, b the plane's two axes, the third axis one node deep), optionally carried by
+    a uniform flow u0 (1, sgn) along its wave vector. Returns the projections of the
+    species' mole-fraction deviation on cos and sin of the phase after each entry of
+    `steps` (cumulative), the wave number |k| and the problem."""
+    shape = [1, 1, 1]
+    a, b = _PLANES[plane]
+    shape[a] = shape[b] = n
+    nx, ny, nz = shape
+    p = W.periodic_box3(nx, ny, nz, reactions=[], energy_correction=0)
+    j = W.SPECIES_ORDER.index(species)
+    xyz = [g.ravel() for g in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")[::-1]]
+    ph = 2 * np.pi * (xyz[a] + sgn * xyz[b]) / n
+    N = nx * ny * nz
+    X0 = np.array([s["X_init"] for s in p["species"]])
+    X0[j] = 1e-3
+    X = np.repeat(X0[:, None], N, 1)
+    X[j] *= 1.0 + 0.01 * np.cos(ph)
+    X[4] = 1.0 - X[:4].sum(0)
+    u = np.zeros((3, N))
+    u[a], u[b] = u0, sgn * u0
+    p["init"] = {"X": X, "u": u}
+    o = oracle.Oracle3(p)
+    out, done = [], 0
+    for t in steps:
+        o.step(t - done)
+        done = t
+        f = o.moments()[5 + j] - X0[j]
+        out.append((2.0 * (f * np.cos(ph)).mean(), 2.0 * (f * np.sin(ph)).mean()))
+    return out, 2 * np.pi * math.sqrt(2.0) / n, p
+
+
+def _diagonal_D3(plane, sgn, n, t0, t1):
+    (a0, _), (a1, _) = _diagonal_mode3(plane, sgn, n, (t0, t1))[0]
+    k = 2 * np.pi * math.sqrt(2.0) / n
+    return -math.log(a1 / a0) / (k * k * (t1 - t0))
+
+
+def test_trace_species_diffusion3_along_face_diagonals():
+    """The interpolated pulls of the 12 face-diagonal links: a heavy trace species' mode
+    along a face diagonal diffuses with D = tau2 T / M_j like an axis mode (D3Q19 is
+    isotropic to second order; k -> 0 from two wavelengths, 1%), and the modes along
+    (1, 1) and (1, -1) of all three planes decay at the same rate (the lattice's
+    reflection and axis-permutation symmetries; a (1, -1) mode is the one that sees a
+    wrong pull position of the links perpendicular to a (1, 1) mode)."""
+    D1 = _diagonal_D3("xy", 1, 24, 15, 130)
+    D2 = _diagonal_D3("xy", 1, 48, 60, 520)
+    D0 = (4.0 * D2 - D1) / 3.0
+    p = W.periodic_box3(4, 4, 4, reactions=[])
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    j = W.SPECIES_ORDER.index("CO2")
+    D_th = p["species"][j]["tau2"] * (1.0 / 3.0) / (M[j] / M.min())
+    assert abs(D0 / D_th - 1.0) < 0.01, (D1, D2, D0, D_th)
+    for plane, sgn in (("xy", -1), ("xz", 1), ("xz", -1), ("yz", 1), ("yz", -1)):
+        assert math.isclose(_diagonal_D3(plane, sgn, 24, 15, 130), D1, rel_tol=1e-9), (plane, sgn)
+
+
+def test_trace_species_advection3_along_face_diagonals():
+    """A heavy trace species' mode carried by a uniform flow along a face diagonal moves
+    with the flow: its phase advances by |k| |u| per step (k -> 0 from two wavelengths,
+    0.5%; the interpolation's dispersion is O(k^2)). The sign of every pull offset enters
+    here, and again all six diagonal modes of the three planes agree."""
+    u0 = 0.01
+    ph = {}
+    for n, t in ((24, 100), (48, 400)):
+        ((A, B),), k, _ = _diagonal_mode3("xy", 1, n, (t,), u0=u0)
+        ph[n] = math.atan2(B, A) / (k * math.sqrt(2.0) * u0 * t)
+    r0 = (4.0 * ph[48] - ph[24]) / 3.0
+    assert abs(r0 - 1.0) < 0.005, (ph, r0)
+    for plane, sgn in (("xy", -1), ("xz", 1), ("xz", -1), ("yz", 1), ("yz", -1)):
+        ((A, B),), k, _ = _diagonal_mode3(plane, sgn, 24, (100,), u0=u0)
+        assert math.isclose(math.atan2(B, A) / (k * math.sqrt(2.0) * u0 * 100), ph[24], rel_tol=1e-9), (plane, sgn)
+
+
 @pytest.mark.parametrize("ec,pr,pr_eff", [(1, 1.0, 1.0), (1, 0.7, 0.7), (0, 1.0, 2.5)])
 def test_entropy_mode3_thermal_diffusivity(ec, pr, pr_eff):
     """Isobaric temperature mode of an equal-mass gas on D3Q19 decays with
