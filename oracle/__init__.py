@@ -149,6 +149,8 @@ def lib():
         L.ora3_counts.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
         L.ora3_classes.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
         L.ora3_velocity.argtypes = [C.c_int, C.POINTER(C.c_int)]
+        L.ora3_interp.argtypes = [C.c_int] + [C.c_double] * 6
+        L.ora3_interp.restype = C.c_double
         L.ora3_equilibrium.argtypes = [C.c_double] * 6 + [dp]
         L.ora3_psi.argtypes = [C.c_double, dp, dp, dp]
         L.ora3_phi.argtypes = [C.c_double, dp]
@@ -493,6 +495,10 @@ class Oracle3:
         out = np.zeros(self.n, np.int32)
         lib().ora3_classes(self._h, out.ctypes.data_as(C.POINTER(C.c_int)))
         return out
+
+
+def interp3(code, c, s3, s2, s1, s0, sp) -> float:
+    return lib().ora3_interp(code, c, s3, s2, s1, s0, sp)
 
 
 def velocities3() -> np.ndarray:

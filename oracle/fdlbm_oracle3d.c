@@ -191,6 +191,10 @@ static double eps_w(const ora3_state* s, int j, int i) {
  * Equilibria, correction coefficients, collision
  * ---------------------------------------------------------------------------------- */
 
+double ora3_interp(int code, double c, double s3, double s2, double s1, double s0, double sp) {
+  return interp(code, c, s3, s2, s1, s0, sp);
+}
+
 void ora3_velocity(int i, int* out3) {
   out3[0] = EX[i];
   out3[1] = EY[i];

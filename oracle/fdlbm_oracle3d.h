@@ -80,6 +80,9 @@ void ora3_classes(const ora3_state* s, int* out);
 /* Point functions for the pins. Velocity set: index i has components
  * ora3_velocity(i, out3) (rest, 6 axis links, 12 face diagonals). */
 void ora3_velocity(int i, int* out3);
+/* One link's interpolated pull (the 3D oracle's own copy of the Sec. 4.2 stencils): code
+ * as for the D2Q9 oracle (0 none, 1 central, 2 forward, 3 backward, 4/5 linear). */
+double ora3_interp(int code, double c, double s3, double s2, double s1, double s0, double sp);
 void ora3_equilibrium(double rho, double ux, double uy, double uz, double M, double T, double* f19);
 void ora3_psi(double c, double* px, double* py, double* pz);
 void ora3_phi(double c, double* phi);

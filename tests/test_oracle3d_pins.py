@@ -623,3 +623,29 @@ def test_single_species_wall_density_closed_form():
     k = idx(c0, c0, c0)
     A = sum(g0[0, i, idx(c0 - E[i, 0], c0 - E[i, 1], c0 - E[i, 2])] for i in range(1, 19))
     assert abs(g1[0, 1:, k].sum() - A) <= 1e-14 * A
+
+
+def test_reactive_wall3_delivers_c_squared_of_its_production():
+    """The D3Q19 form of the closed-form delivery of a flat reactive wall: a uniform gas at
+    rest and in equilibrium over a catalytic slab (periodic box, wall normal +z). The
+    walls' step-1 reaction production goes out on the five links with e_z = +1; in step 2
+    the first gas node along each such link takes it with the forward stencil's weight
+    c (1 + c) / 2, the second with the central stencil's -(1 - c) c / 2, so the gas
+    inventory of species j grows by exactly c_j^2 times the production. A wrong stencil
+    choice near the wall, a wrong coefficient or a lost share of a diagonal emission link
+    breaks the identity."""
+    p = W.periodic_box3(8, 6, 12, solid_layers=4)
+    o = oracle.Oracle3(p)
+    gas = o.classes() == 0
+    ns = len(p["species"])
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    c2 = M.min() / M
+    o.step(1)
+    g1 = o.moments()[:ns][:, gas].sum(axis=1)
+    r1 = o.accounts()["M_rxn"].copy()
+    o.step(1)
+    g2 = o.moments()[:ns][:, gas].sum(axis=1)
+    assert np.all(np.abs(r1[:4]) > 0) and r1[4] == 0  # CO and H2O consumed, CO2 and H2 made, N2 inert
+    # the difference of two inventories of ~10^3 carries their FP64 rounding, ~1e-12
+    np.testing.assert_allclose(g2 - g1, c2 * r1, rtol=1e-9, atol=1e-14 * g1.max())
+    assert abs((g2 - g1)[3] - r1[3]) <= 1e-9 * abs(r1[3])  # H2 (c = 1) in full

@@ -78,11 +78,15 @@ def test_psi_phi_moments(M):
 
 
 CENTRAL, FORWARD, BACKWARD, LIN_S0, LIN_S2, NONE = 1, 2, 3, 4, 5, 0
+# The D2Q9 and the D3Q19 oracle each carry their own copy of the stencils.
+INTERPS = pytest.mark.parametrize("interp", [oracle.interp, oracle.interp3],
+                                  ids=["d2q9", "d3q19"])
 
 
+@INTERPS
 @pytest.mark.parametrize("code", [CENTRAL, FORWARD, BACKWARD])
 @pytest.mark.parametrize("c", [0.214, 0.268, 0.335, 0.6, 1.0])
-def test_interp_exact_on_quadratics(code, c):
+def test_interp_exact_on_quadratics(code, c, interp):
     """Eqs. interpol_bulk / interpol_away / interpol_towards are second order: streaming a
     quadratic profile by c and interpolating back on-lattice is exact. Off-lattice
     point positions relative to the target node: s1 at c - 1, s2 at c - 2, s3 at c - 3,
@@ -94,28 +98,30 @@ def test_interp_exact_on_quadratics(code, c):
         def prof(s):
             return a0 + a1 * s + a2 * s * s
 
-        v = oracle.interp(code, c, prof(c - 3), prof(c - 2), prof(c - 1), prof(c), prof(c + 1))
+        v = interp(code, c, prof(c - 3), prof(c - 2), prof(c - 1), prof(c), prof(c + 1))
         assert np.isclose(v, prof(0.0), rtol=1e-12, atol=1e-12)
 
 
+@INTERPS
 @pytest.mark.parametrize("code", [LIN_S0, LIN_S2])
-def test_interp_linear_fallbacks_exact_on_lines(code):
+def test_interp_linear_fallbacks_exact_on_lines(code, interp):
     rng = np.random.default_rng(8)
     for c in (0.2, 0.5, 0.9):
         a0, a1 = rng.normal(size=2)
         prof = lambda s: a0 + a1 * s  # noqa: E731
-        v = oracle.interp(code, c, prof(c - 3), prof(c - 2), prof(c - 1), prof(c), prof(c + 1))
+        v = interp(code, c, prof(c - 3), prof(c - 2), prof(c - 1), prof(c), prof(c + 1))
         assert np.isclose(v, prof(0.0), rtol=1e-12, atol=1e-12)
 
 
-def test_interp_limits():
+@INTERPS
+def test_interp_limits(interp):
     """c_j = 1 is a pure lattice shift (the lightest species, Fig. D2Q9); c_j -> 0 in the
     bulk leaves the node's own population in place."""
     rng = np.random.default_rng(9)
     s3, s2, s1, s0, sp = rng.normal(size=5)
     for code in (NONE, CENTRAL, FORWARD, BACKWARD, LIN_S0, LIN_S2):
-        assert oracle.interp(code, 1.0, s3, s2, s1, s0, sp) == s1
-    assert np.isclose(oracle.interp(CENTRAL, 0.0, s3, s2, s1, s0, sp), s0, rtol=1e-14)
+        assert interp(code, 1.0, s3, s2, s1, s0, sp) == s1
+    assert np.isclose(interp(CENTRAL, 0.0, s3, s2, s1, s0, sp), s0, rtol=1e-14)
 
 
 def _random_node(ns, rng):
