@@ -272,6 +272,26 @@ def test_fixed_t_solid_eigenmode3():
     np.testing.assert_allclose(got, A * lam ** 30 * np.sin(np.pi * (z + 1) / (nz + 1)), rtol=1e-11)
 
 
+def test_fixed_t_solid_product_eigenmode3():
+    """All three axes of the 7-point difference: in a solid block with fixed-T faces all
+    round (three different side lengths) the product of the axis eigenmodes decays by
+    1 - 4 alpha sum_a sin^2(pi / (2 (n_a + 1))) per step; a wrong weight or neighbour on
+    any axis changes the rate."""
+    nx, ny, nz = 9, 11, 13
+    mask = np.full((nz, ny, nx), W.INERT, np.uint8)
+    p = W._base(3, nx, ny, nz, mask, [W.FIXED_T] * 6, reactions=[])
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mode = (np.sin(np.pi * (x + 1) / (nx + 1)) * np.sin(np.pi * (y + 1) / (ny + 1))
+            * np.sin(np.pi * (z + 1) / (nz + 1)))
+    A = 6.0
+    p["init"] = {"Ts_K": (p["T_outer_K"] + A * mode).ravel()}
+    o = oracle.Oracle3(p)
+    o.step(30)
+    lam = 1.0 - 4.0 * p["alpha_s"] * sum(math.sin(math.pi / (2 * (m + 1))) ** 2 for m in (nx, ny, nz))
+    got = o.moments()[-1].reshape(nz, ny, nx) - p["T_outer_K"]
+    np.testing.assert_allclose(got, A * lam ** 30 * mode, rtol=1e-11, atol=1e-13)
+
+
 # ---------------------------------------------------------------------------------------
 # Transport against analytic decay rates
 # ---------------------------------------------------------------------------------------

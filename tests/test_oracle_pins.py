@@ -338,6 +338,27 @@ def test_fixed_t_solid_eigenmode():
     assert n == o.n
 
 
+def test_fixed_t_solid_product_eigenmode():
+    """Both axes of the 5-point difference: in a solid block with fixed-T faces all round
+    (unequal sides), sin(pi (x + 1) / (nx + 1)) sin(pi (y + 1) / (ny + 1)) decays by
+    1 - 4 alpha (sin^2(pi / (2 (nx + 1))) + sin^2(pi / (2 (ny + 1)))) per step; a wrong
+    weight or neighbour on either axis changes the rate."""
+    nx, ny = 11, 15
+    mask = np.full((ny, nx), W.INERT, np.uint8)
+    p = W._base(2, nx, ny, 1, mask, [W.FIXED_T] * 4, reactions=[])
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    mode = np.sin(np.pi * (x + 1) / (nx + 1)) * np.sin(np.pi * (y + 1) / (ny + 1))
+    A = 7.0
+    p["init"] = {"Ts_K": (p["T_outer_K"] + A * mode).ravel()}
+    o = oracle.Oracle(p)
+    nsteps = 40
+    o.step(nsteps)
+    al = p["alpha_s"]
+    lam = 1.0 - 4.0 * al * (math.sin(math.pi / (2 * (nx + 1))) ** 2 + math.sin(math.pi / (2 * (ny + 1))) ** 2)
+    got = o.moments()[-1].reshape(ny, nx) - p["T_outer_K"]
+    np.testing.assert_allclose(got, A * lam ** nsteps * mode, rtol=1e-11, atol=1e-13)
+
+
 # ---------------------------------------------------------------------------------------
 # Transport against analytic solutions (Sec. 4.4 benchmarks)
 # ---------------------------------------------------------------------------------------
