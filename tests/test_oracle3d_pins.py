@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from outlet_check import outlet_condition_errors
 from paper_1804_07588_gb300 import workloads as W
 
 E = None
@@ -669,3 +670,22 @@ def test_reactive_wall3_delivers_c_squared_of_its_production():
     # the difference of two inventories of ~10^3 carries their FP64 rounding, ~1e-12
     np.testing.assert_allclose(g2 - g1, c2 * r1, rtol=1e-9, atol=1e-14 * g1.max())
     assert abs((g2 - g1)[3] - r1[3]) <= 1e-9 * abs(r1[3])  # H2 (c = 1) in full
+
+
+def test_outlet3_holds_inlet_pressure_with_upstream_state():
+    """Reading R13 on D3Q19: every outlet node holds the equilibrium at the inlet
+    pressure p = C_in T_in with the composition, velocity and temperature of its upstream
+    gas node. Checked where the channel's hotter walls have warmed the gas (the outlet's
+    upstream temperature differs from T_in, so holding C instead of p would fail)."""
+    nx, ng, wall, nz = 24, 10, 2, 2
+    ny = ng + 2 * wall
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, :wall, :] = W.INERT
+    mask[:, wall + ng:, :] = W.INERT
+    p = W._base(3, nx, ny, nz, mask, [W.INLET, W.OUTLET, W.FIXED_T, W.FIXED_T, W.PERIODIC, W.PERIODIC],
+                u_inlet=0.02, inlet_profile=W.PLUG, reactions=[], T_solid_init_K=540.0, T_outer_K=540.0)
+    o = oracle.Oracle3(p)
+    o.step(200)
+    r = outlet_condition_errors(p, o, _vel())
+    assert len(r) == ny * nz - 2 * wall * nz and r[:, 3].min() > p["T_inlet_K"] + 2.0
+    assert r[:, 0].max() < 1e-12 and r[:, 1].max() < 1e-13 and r[:, 2].max() < 1e-14

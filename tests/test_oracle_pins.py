@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from outlet_check import outlet_condition_errors
 from paper_1804_07588_gb300 import workloads as W
 
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
@@ -846,3 +847,16 @@ def test_reactive_wall_delivers_c_squared_of_its_production():
     # the on-lattice species (H2, c = 1) is delivered in full, the heavy ones only c^2 of it
     assert abs((g2 - g1)[3] - r1[3]) <= 1e-9 * abs(r1[3])
     assert abs((g2 - g1)[2]) < 0.05 * abs(r1[2])
+
+
+def test_outlet_holds_inlet_pressure_with_upstream_state():
+    """Reading R13: every outlet node holds the equilibrium at the inlet pressure
+    p = C_in T_in with the composition, velocity and temperature of its upstream gas node.
+    Checked where the channel's hotter walls have warmed the gas (the outlet's upstream
+    temperature differs from T_in, so holding C instead of p would fail)."""
+    p = W.channel(nx=32, n_gas=10, wall=3, reactions=[], T_solid_init_K=540.0, T_outer_K=540.0)
+    o = oracle.Oracle(p)
+    o.step(200)
+    r = outlet_condition_errors(p, o, np.stack([EX, EY], 1))
+    assert len(r) == 10 and r[:, 3].min() > p["T_inlet_K"] + 2.0
+    assert r[:, 0].max() < 1e-12 and r[:, 1].max() < 1e-13 and r[:, 2].max() < 1e-14
