@@ -860,3 +860,35 @@ def test_outlet_holds_inlet_pressure_with_upstream_state():
     r = outlet_condition_errors(p, o, np.stack([EX, EY], 1))
     assert len(r) == 10 and r[:, 3].min() > p["T_inlet_K"] + 2.0
     assert r[:, 0].max() < 1e-12 and r[:, 1].max() < 1e-13 and r[:, 2].max() < 1e-14
+
+
+@pytest.mark.parametrize("n_gas", [9, 10])
+def test_parabolic_inlet_profile(n_gas):
+    """Reading R13's parabolic inlet: the velocity the inlet nodes hold (from their
+    stored populations) lies on the quadratic that vanishes on the two wall nodes
+    bounding the inlet run and peaks at u_inlet mid-way between them, along x only, with
+    the inlet composition."""
+    wall = 3
+    p = W.channel(nx=16, n_gas=n_gas, wall=wall, reactions=[])
+    o = oracle.Oracle(p)
+    o.step(3)
+    ns = o.ns
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    c = np.sqrt(1.0 / M)
+    g = o.populations()
+    inlet = np.where(o.classes() == 1)[0]
+    assert len(inlet) == n_gas
+    y = inlet // 16 - wall                        # 0 .. n_gas - 1; walls at -1 and n_gas
+    rho = np.array([g[:, :, k].sum(1) for k in inlet])        # [node][species]
+    J = np.array([sum(c[j] * np.array([(EX * g[j, :, k]).sum(), (EY * g[j, :, k]).sum()]) for j in range(ns))
+                  for k in inlet])
+    u = J / rho.sum(1)[:, None]
+    yc = (n_gas - 1) / 2.0
+    half = (n_gas + 1) / 2.0                      # centre to bounding wall node
+    ref = p["u_inlet"] * (1.0 - ((y - yc) / half) ** 2)
+    np.testing.assert_allclose(u[:, 0], ref, rtol=1e-13, atol=1e-16)
+    assert np.abs(u[:, 1]).max() < 1e-16
+    X = rho / M / (rho / M).sum(1)[:, None]
+    X_in = np.array([s["X_inlet"] for s in p["species"]])
+    np.testing.assert_allclose(X, np.repeat(X_in[None], n_gas, 0), rtol=1e-13, atol=1e-18)
