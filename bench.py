@@ -93,6 +93,12 @@ def kernel_source_hash(three_d=False):
     return h.hexdigest()[:16]
 
 
+def traffic_record_holds(rec, sha):
+    """A traffic record holds for the source it was captured on and for the later sources
+    it lists under also_valid_for, each with the reason the measured kernels are unchanged."""
+    return rec.get("kernel_source_sha") == sha or any(v.get("sha") == sha for v in rec.get("also_valid_for", []))
+
+
 def variant_traffic(name, three_d):
     """DRAM bytes per step of a bench variant from the committed ncu table, or None when the
     kernel source changed since the counters were taken."""
@@ -101,7 +107,7 @@ def variant_traffic(name, three_d):
             e = json.load(f)["variants"][name]
     except Exception:
         return None
-    return e["dram_bytes_per_step"] if e.get("kernel_source_sha") == kernel_source_hash(three_d) else None
+    return e["dram_bytes_per_step"] if traffic_record_holds(e, kernel_source_hash(three_d)) else None
 
 
 def ncu_traffic(three_d=False):
@@ -114,7 +120,7 @@ def ncu_traffic(three_d=False):
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_source_sha") != kernel_source_hash(three_d):
+    if not traffic_record_holds(d, kernel_source_hash(three_d)):
         return None
     return d.get("dram_bytes_per_launch")
 

@@ -67,3 +67,11 @@ def test_reference_arm_other_ranks_do_nothing(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_record_holds_for_its_source_and_listed_equivalents():
+    import bench
+    rec = {"kernel_source_sha": "aaaa", "also_valid_for": [{"sha": "bbbb", "why": "unchanged kernels"}]}
+    assert bench.traffic_record_holds(rec, "aaaa") and bench.traffic_record_holds(rec, "bbbb")
+    assert not bench.traffic_record_holds(rec, "cccc")
+    assert not bench.traffic_record_holds({"kernel_source_sha": "aaaa"}, "bbbb")
