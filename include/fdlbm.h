@@ -303,10 +303,10 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out);
  *
  * The first call on a device looks up the scratch address on that device; make that
  * first call before any stream capture on the device. The scratch is shared by all
- * handles on a device, so calls that overlap in time (from several host threads, or on
- * several streams whose work is not ordered) race on it and may return wrong totals:
- * serialise them. Errors: EINVAL (NULL arguments, out_len too small, lattice over the
- * limit), ECUDA. */
+ * handles on a device: a process-wide lock, held from the start of a call until its
+ * read-back has completed, makes calls from several host threads, handles or streams
+ * take it one after another (a call waits for any other in progress). Errors: EINVAL
+ * (NULL arguments, out_len too small, lattice over the limit), ECUDA. */
 #define FDLBM_STATIC_SCRATCH_BYTES 262144
 fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len);
 

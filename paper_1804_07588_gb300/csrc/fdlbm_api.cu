@@ -1465,7 +1465,9 @@ fdlbm_status fdlbm_residual(fdlbm_handle* h, double* out) {
 }
 
 // Address of the static totals scratch, looked up once per device (with that device
-// current) and kept for the life of the process.
+// current) and kept for the life of the process. g_static_mu is held from the lookup
+// until the call's read-back has completed: calls from several host threads, handles or
+// streams then take the scratch one after another instead of racing on it.
 namespace {
 constexpr int STATIC_MAX_DEVICES = 64;
 std::mutex g_static_mu;
@@ -1487,16 +1489,13 @@ fdlbm_status fdlbm_totals_static(fdlbm_handle* h, double* out, int out_len) {
     return fail(FDLBM_EINVAL, "device %d outside the %d devices the static scratch serves", h->device,
                 STATIC_MAX_DEVICES);
   DeviceGuard guard(h->device);
-  double* scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_scratch[h->device]) {
-      double* p = nullptr;
-      CK(totals_static_scratch(&p), "static totals scratch address");
-      g_static_scratch[h->device] = p;
-    }
-    scratch = g_static_scratch[h->device];
+  std::lock_guard<std::mutex> lock(g_static_mu);  // until the stream sync below
+  if (!g_static_scratch[h->device]) {
+    double* p = nullptr;
+    CK(totals_static_scratch(&p), "static totals scratch address");
+    g_static_scratch[h->device] = p;
   }
+  double* const scratch = g_static_scratch[h->device];
   fdlbm_status st = ensure_moments(h);
   if (st != FDLBM_OK) return st;
   CK(launch_totals_static(h->P, h->S, h->cur, scratch, h->stream), "static totals launch");
