@@ -142,6 +142,8 @@ def lib():
         L.ora3_nfields.argtypes = [C.c_void_p]
         L.ora3_moments.argtypes = [C.c_void_p, dp]
         L.ora3_populations.argtypes = [C.c_void_p, dp]
+        L.ora3_get_state.argtypes = [C.c_void_p, dp, dp, dp]
+        L.ora3_set_state.argtypes = [C.c_void_p, dp, dp, dp]
         L.ora3_balance.argtypes = [C.c_void_p, dp]
         L.ora3_accounts.argtypes = [C.c_void_p, dp]
         L.ora3_residual.argtypes = [C.c_void_p, C.c_int]
@@ -458,6 +460,21 @@ class Oracle3:
         out = np.zeros((self.ns, Q3, self.n))
         lib().ora3_populations(self._h, _dptr(out))
         return out
+
+    def get_state(self):
+        """(g [ns][19][n], Ts [n], T [n]) of the current time level (lattice units)."""
+        g = np.empty((self.ns, Q3, self.n))
+        Ts = np.empty(self.n)
+        T = np.empty(self.n)
+        lib().ora3_get_state(self._h, _dptr(g), _dptr(Ts), _dptr(T))
+        return g, Ts, T
+
+    def set_state(self, g, Ts, T):
+        g = np.ascontiguousarray(g, np.float64)
+        Ts = np.ascontiguousarray(Ts, np.float64)
+        T = np.ascontiguousarray(T, np.float64)
+        assert g.size == self.ns * Q3 * self.n and Ts.size == self.n and T.size == self.n
+        lib().ora3_set_state(self._h, _dptr(g), _dptr(Ts), _dptr(T))
 
     def accounts(self) -> dict:
         """Exact accounts of the D3Q19 scheme (the layout of Oracle.accounts)."""

@@ -851,6 +851,20 @@ void ora3_populations(const ora3_state* s, double* out) {
   memcpy(out, s->g, sizeof(double) * (size_t)s->ns * Q * s->n);
 }
 
+/* The state the next step reads: stored populations, solid temperature and the gas
+ * mixture temperature of the last step (read by the paper's coupling law). */
+void ora3_get_state(const ora3_state* s, double* g, double* Ts, double* T) {
+  if (g) memcpy(g, s->g, sizeof(double) * (size_t)s->ns * Q * s->n);
+  if (Ts) memcpy(Ts, s->Ts, sizeof(double) * (size_t)s->n);
+  if (T) memcpy(T, s->T, sizeof(double) * (size_t)s->n);
+}
+
+void ora3_set_state(ora3_state* s, const double* g, const double* Ts, const double* T) {
+  if (g) memcpy(s->g, g, sizeof(double) * (size_t)s->ns * Q * s->n);
+  if (Ts) memcpy(s->Ts, Ts, sizeof(double) * (size_t)s->n);
+  if (T) memcpy(s->T, T, sizeof(double) * (size_t)s->n);
+}
+
 /* Gas energy sum (D/2) C T + rho u^2 / 2 plus the in-transit wall emissions; solid
  * enthalpy; species mass and moles (as in the D2Q9 oracle). */
 static void ledger_totals(const ora3_state* s, double* E, double* H, double* mass, double* moles) {

@@ -70,6 +70,10 @@ int ora3_step(ora3_state* s, int nsteps);
 int ora3_nfields(const ora3_state* s);                 /* 2*ns + 5 */
 void ora3_moments(const ora3_state* s, double* out);   /* rho_j, X_j, ux, uy, uz, T_K (gas), Ts_K (solid) */
 void ora3_populations(const ora3_state* s, double* out); /* [ns][19][n] */
+/* State the next step reads (g [ns][19][n], T_s [n], gas T [n], lattice units); the
+ * slab decomposition's exchange reads and overwrites its ghost strips through these. */
+void ora3_get_state(const ora3_state* s, double* g, double* Ts, double* T);
+void ora3_set_state(ora3_state* s, const double* g, const double* Ts, const double* T);
 void ora3_balance(const ora3_state* s, double* out);
 /* Exact accounts (energy, then per-species mass; layout ORA3_A_*). */
 void ora3_accounts(const ora3_state* s, double* out);

@@ -1,8 +1,8 @@
-"""The slab decomposition of the D2Q9 path (x slabs, 4-column ghost strips exchanged by
-point-to-point send/recv every step, FP64 all-reduce of the totals and the residual),
-checked with the FP64 oracle as every rank's slab solver: gloo ranks on CPU, world
-sizes 2 and 4. The gathered moment fields must equal the undecomposed oracle's bit for
-bit; the all-reduced totals and residual equal it up to the order of the additions."""
+"""The slab decomposition of the D2Q9 and D3Q19 paths (x slabs, 4-column ghost strips
+exchanged by point-to-point send/recv every step, FP64 all-reduce of the totals and the
+residual), checked with the FP64 oracles as every rank's slab solver: gloo ranks on CPU,
+world sizes 2 and 4. The gathered moment fields must equal the undecomposed oracle's bit
+for bit; the all-reduced totals and residual equal it up to the order of the additions."""
 import os
 import pickle
 import socket
@@ -34,25 +34,47 @@ def _problem(name):
         p = W.porous_disks(nx=100, ny=60, porosity=0.75, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01, coupling=1)
         p["init"] = W.random_fields(p, seed=73, du=0.005)
         return p
+    if name == "channel3":  # D3Q19: inlet, outlet, catalytic FD walls in y, periodic z
+        nx, ng, wall, nz = 40, 8, 3, 6
+        mask = np.zeros((nz, ng + 2 * wall, nx), np.uint8)
+        mask[:, :wall, :] = W.CATALYTIC
+        mask[:, wall + ng:, :] = W.CATALYTIC
+        p = W._base(3, nx, ng + 2 * wall, nz, mask,
+                    [W.INLET, W.OUTLET, W.FIXED_T, W.FIXED_T, W.PERIODIC, W.PERIODIC],
+                    u_inlet=0.02, inlet_profile=W.PLUG)
+        p["init"] = W.random_fields(p, seed=74, du=0.005)
+        return p
+    if name == "periodic3":  # D3Q19, periodic in all three axes over a catalytic slab
+        p = W.periodic_box3(24, 8, 6, solid_layers=2)
+        p["init"] = W.random_fields(p, seed=75)
+        return p
+    if name == "spheres3":  # crop of the sphere packing (cut by every slab boundary)
+        p = W.config2_crop(nx=32, ny=16, nz=16)
+        p["init"] = W.random_fields(p, seed=76, du=0.005)
+        return p
     raise KeyError(name)
+
+
+def _solver_class(p):
+    import oracle
+    return oracle.Oracle3 if p["dim"] == 3 else oracle.Oracle
 
 
 STEPS = 30
 
 
-def _rank_main(rank, world, port, name, out):
+def _rank_main(rank, world, port, name, out, halo=None):
     import sys
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
 
-    import oracle
     from paper_1804_07588_gb300 import slabs
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         p = _problem(name)
-        run = slabs.SlabRunner(p, oracle.Oracle, dist)
+        run = slabs.SlabRunner(p, _solver_class(p), dist, halo=slabs.HALO if halo is None else halo)
         run.residual(10)
         run.step(10)
         r1 = run.residual(10)
@@ -64,11 +86,11 @@ def _rank_main(rank, world, port, name, out):
         dist.destroy_process_group()
 
 
-def _run(name, world):
+def _run(name, world, halo=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, name, q, halo)) for r in range(world)]
     for pr in procs:
         pr.start()
     res = {}
@@ -92,18 +114,19 @@ def test_partition_is_even_and_covers_the_lattice():
     assert parts[0][0] == 0 and parts[-1][1] == 50
     assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))
     assert max(b - a for a, b in parts) - min(b - a for a, b in parts) <= 1
+    assert slabs.HALO == 3
     with pytest.raises(ValueError):
-        slabs.partition(12, 4)  # slabs narrower than the ghost depth
+        slabs.partition(11, 4)  # slabs narrower than the ghost depth
 
 
 @pytest.mark.parametrize("name, world", [("channel", 2), ("channel", 4), ("periodic", 2), ("periodic", 4),
-                                         ("porous", 2), ("porous", 4)])
+                                         ("porous", 2), ("porous", 4), ("channel3", 2), ("periodic3", 4),
+                                         ("spheres3", 2), ("spheres3", 4)])
 def test_slabs_bitwise_equal_to_monolithic(name, world):
-    import oracle
     res = _run(name, world)
     m_slab, tot, r1 = res[0]
     p = _problem(name)
-    o = oracle.Oracle(p)
+    o = _solver_class(p)(p)
     o.residual(10)
     o.step(10)
     r1_mono = o.residual(10)
@@ -120,3 +143,15 @@ def test_slabs_bitwise_equal_to_monolithic(name, world):
     for r in range(1, world):
         assert res[r][0] is None
         assert res[r][1]["E_gas"] == tot["E_gas"]
+
+
+@pytest.mark.parametrize("name", ["porous", "channel3"])
+def test_one_column_less_of_ghosts_breaks_the_decomposition(name):
+    """The ghost depth is the reach of one step and no more than needed: with HALO - 1
+    columns the gathered fields differ from the undecomposed run."""
+    from paper_1804_07588_gb300 import slabs
+    m_slab = _run(name, 2, halo=slabs.HALO - 1)[0][0]
+    p = _problem(name)
+    o = _solver_class(p)(p)
+    o.step(STEPS)
+    assert not np.array_equal(m_slab, o.moments())
