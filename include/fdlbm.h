@@ -267,7 +267,12 @@ fdlbm_status fdlbm_moments(fdlbm_handle* h, float* dst, int dst_on_device);
 fdlbm_status fdlbm_moments_ex(fdlbm_handle* h, unsigned flags, float* dst, int dst_on_device);
 
 /* Stored populations g* (post-collision on gas, inlet and outlet nodes, emissions on
- * wall nodes), [ns][Q][n] float32 (Q = 9 or 19; absolute values, not deviations). */
+ * wall nodes), [ns][Q][n] float32 (Q = 9 or 19; absolute values, not deviations).
+ * Direction i moves along e_i (species j by c_j e_i per step, Sec. 4.2):
+ *   D2Q9:  (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1);
+ *   D3Q19: (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1) (1,1,0) (-1,-1,0)
+ *          (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1)
+ *          (0,1,-1) (0,-1,1). */
 fdlbm_status fdlbm_populations(fdlbm_handle* h, float* dst, int dst_on_device);
 
 /* FP64 ledger (synchronous). */

@@ -88,3 +88,28 @@ def test_binding_structs_match_header_layout(tmp_path):
         cls = getattr(fdlbm, pyname)
         got = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
         assert got == int(value), f"{pyname}.{what}: ctypes {got}, C {value}"
+
+
+def test_header_direction_order_is_the_oracles():
+    """The velocity order include/fdlbm.h gives for fdlbm_populations is the one the FP64
+    oracles use (the GPU population parity tests compare the two index by index)."""
+    import re
+
+    import numpy as np
+
+    import oracle
+    h = open(os.path.join(ROOT, "include", "fdlbm.h")).read()
+    blk = h[h.index("Direction i moves along e_i"):h.index("fdlbm_status fdlbm_populations")]
+    two, three = blk.split("D3Q19")
+    d2 = np.array([[int(a), int(b)] for a, b in re.findall(r"\((-?\d),(-?\d)\)", two)])
+    d3 = np.array([[int(a), int(b), int(c)] for a, b, c in re.findall(r"\((-?\d),(-?\d),(-?\d)\)", three)])
+    assert d2.shape == (9, 2) and d3.shape == (19, 3)
+    np.testing.assert_array_equal(d3, oracle.velocities3())
+    # D2Q9: the odd part f(u) - f(-u) of the oracle's equilibrium for u along one axis has
+    # the sign of e_i's component on that axis (zero where it is zero)
+    for axis in range(2):
+        u = [0.0, 0.0]
+        u[axis] = 0.01
+        odd = (oracle.equilibrium(1.0, u[0], u[1], 1.0, 1.0 / 3.0)
+               - oracle.equilibrium(1.0, -u[0], -u[1], 1.0, 1.0 / 3.0))
+        np.testing.assert_array_equal(np.sign(odd).astype(int), d2[:, axis])
