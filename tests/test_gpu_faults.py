@@ -3,7 +3,6 @@ iteration cap (non-converged wall nodes are counted in the ledger, as the oracle
 them), initial fields outside the equilibrium's range, and the strict geometry mode that
 rejects the concave corners and narrow gaps the paper excludes (FDLBM_EGEOM). No case
 faults the device: every failure is a status returned by the host or a count."""
-import numpy as np
 import pytest
 
 import oracle

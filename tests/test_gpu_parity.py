@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1804_07588_gb300 import workloads as W
-from parity import TOL, assert_parity, field_errors, run_both
+from parity import assert_parity, run_both
 
 pytestmark = pytest.mark.gpu
 

@@ -5,7 +5,6 @@ D3Q19 oracle on the 64x32x32 crop of the 256x128x128 sphere packing, 200 steps.
 The paper fixes no precision: the bounds are the stated ones, about three times the
 errors measured on GB300 per field (field-normalised; velocity components share the
 maximum speed as their scale). FP32 storage is held to the parity bar 1e-5."""
-import numpy as np
 import pytest
 
 import oracle
