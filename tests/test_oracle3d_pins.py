@@ -412,14 +412,18 @@ def test_trace_species_advection3_along_face_diagonals():
         assert math.isclose(math.atan2(B, A) / (k * math.sqrt(2.0) * u0 * 100), ph[24], rel_tol=1e-9), (plane, sgn)
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
 @pytest.mark.parametrize("ec,pr,pr_eff", [(1, 1.0, 1.0), (1, 0.7, 0.7), (0, 1.0, 2.5)])
-def test_entropy_mode3_thermal_diffusivity(ec, pr, pr_eff):
+def test_entropy_mode3_thermal_diffusivity(ec, pr, pr_eff, axis):
     """Isobaric temperature mode of an equal-mass gas on D3Q19 decays with
     alpha = tau1 T / Pr. Without the energy correction the folded product form carries
     (D - 1) / (D + 2) = 2/5 of the kinetic heat flux, i.e. Pr = 5/2 (the 3D counterpart
-    of the paper's Pr = 4 for D2Q9). 2% tolerance."""
+    of the paper's Pr = 4 for D2Q9). 2% tolerance. The mode runs along each axis in turn:
+    the correction's divergence has a term per axis."""
     nx, tau = 48, 0.25
-    p = _unit_mass(W.periodic_box3(nx, 1, 1, reactions=[], Pr=pr, energy_correction=ec), tau=tau)
+    shape = [1, 1, 1]
+    shape[axis] = nx
+    p = _unit_mass(W.periodic_box3(*shape, reactions=[], Pr=pr, energy_correction=ec), tau=tau)
     x = np.arange(nx)
     T = p["T_init_K"] * (1.0 + 0.002 * np.cos(2 * np.pi * x / nx))
     X0 = np.array([s["X_init"] for s in p["species"]])
