@@ -369,8 +369,9 @@ def _mode_amplitude(f, nx):
     return 2.0 * (f * np.cos(2 * np.pi * x / nx)).mean()
 
 
-def _trace_decay_rate(species, nx, t0, t1):
-    p = W.periodic_box(nx, 1, reactions=[], energy_correction=0)
+def _trace_decay_rate(species, nx, t0, t1, axis=0):
+    shape = (nx, 1) if axis == 0 else (1, nx)    # the node index is the coordinate along axis
+    p = W.periodic_box(*shape, reactions=[], energy_correction=0)
     j = W.SPECIES_ORDER.index(species)
     X0 = np.array([s["X_init"] for s in p["species"]])
     X0[j] = 1e-3
@@ -388,16 +389,17 @@ def _trace_decay_rate(species, nx, t0, t1):
     return -math.log(a1 / a0) / (k * k * (t1 - t0)), p, j
 
 
+@pytest.mark.parametrize("axis", [0, 1])
 @pytest.mark.parametrize("species", ["CO2", "H2O"])
-def test_trace_species_diffusion_mode(species):
+def test_trace_species_diffusion_mode(species, axis):
     """A small sinusoidal mole-fraction perturbation of a heavy trace species in the
     inlet mixture decays as exp(-D k^2 t) with D = tau2 T / M_j (mass diffusivity of
     Eq. tau2_approx_text at X_j p = C_j T), streamed off-lattice with the quadratic
     interpolation. The interpolation adds a k^4 damping (second-order scheme), so D is
     measured at two wavelengths (48 and 96 nodes) and extrapolated to k -> 0; 1%
-    tolerance."""
-    D1, p, j = _trace_decay_rate(species, 48, 100, 900)
-    D2, _, _ = _trace_decay_rate(species, 96, 400, 3600)
+    tolerance. Along x and along y: each axis has its own links."""
+    D1, p, j = _trace_decay_rate(species, 48, 100, 900, axis)
+    D2, _, _ = _trace_decay_rate(species, 96, 400, 3600, axis)
     D0 = (4.0 * D2 - D1) / 3.0
     M = np.array([s["M_gmol"] for s in p["species"]])
     M = M / M.min()
