@@ -565,6 +565,36 @@ def test_local_tau_shear_viscosity_wilke():
     assert abs(nu0 / (mu_mix / rho) - 1.0) < 0.01, (nu1, nu2, nu0, mu_mix / rho)
 
 
+def _binary_interdiffusion(nx, t0, t1, x_co2):
+    jc, jh = W.SPECIES_ORDER.index("CO2"), W.SPECIES_ORDER.index("H2")
+    p = W.local_transport(W.periodic_box(nx, 1, reactions=[], energy_correction=0))
+    x = np.arange(nx)
+    X = np.full((len(p["species"]), nx), 1e-9)     # the other three species (nearly) empty
+    X[jc] = x_co2 * (1.0 + 0.01 * np.cos(2 * np.pi * x / nx))
+    X[jh] = 1.0 - X[jc] - 3e-9
+    p["init"] = {"X": X}
+    o = oracle.Oracle(p)
+    o.step(t0)
+    a0 = _mode_amplitude(o.moments()[5 + jc], nx)
+    o.step(t1 - t0)
+    a1 = _mode_amplitude(o.moments()[5 + jc], nx)
+    k = 2 * np.pi / nx
+    return -math.log(a1 / a0) / (k * k * (t1 - t0)), p["species"][jc]["D"][jh]
+
+
+@pytest.mark.parametrize("x_co2", [0.1, 0.5, 0.9])
+def test_local_tau_binary_interdiffusion_is_D12(x_co2):
+    """Fick's law for a binary mixture: in H2/CO2 (the other species empty) a small
+    composition wave decays with the binary diffusivity D_12 at any composition. The
+    mixture-averaged coefficient of Eq. D_j_text (with its 1 - Y_j), the relaxation time
+    of Eq. tau2_approx_text and the momentum closure U^c give that together; k -> 0 from
+    two wavelengths, 1%. (With 1 - X_j in place of 1 - Y_j the 10% mixture goes unstable.)"""
+    D1, D12 = _binary_interdiffusion(48, 100, 900, x_co2)
+    D2, _ = _binary_interdiffusion(96, 400, 3600, x_co2)
+    D0 = (4.0 * D2 - D1) / 3.0
+    assert np.isfinite(D0) and abs(D0 / D12 - 1.0) < 0.01, (D1, D2, D0, D12)
+
+
 def test_local_tau_conserves_periodic():
     """Locally updated relaxation times keep species mass and mixture momentum (U^c with
     the node's tau2) in a periodic box from random fields."""
