@@ -693,3 +693,19 @@ def test_outlet3_holds_inlet_pressure_with_upstream_state():
     r = outlet_condition_errors(p, o, _vel())
     assert len(r) == ny * nz - 2 * wall * nz and r[:, 3].min() > p["T_inlet_K"] + 2.0
     assert r[:, 0].max() < 1e-12 and r[:, 1].max() < 1e-13 and r[:, 2].max() < 1e-14
+
+
+def test_paper_coupling3_one_step_by_hand():
+    """Eq. wall_temperature on D3Q19: a one-layer FD slab in a periodic box (gas above and
+    below every slab node, no gradient along the slab); from a uniform gas at T_g and
+    solid at T_s0 the first step moves the solid by exactly
+    2 kappa_f (T_g - T_s0) / (rho c_p)_s."""
+    p = W.periodic_box3(6, 6, 6, solid_layers=1, reactions=[], coupling=1)
+    n = p["nx"] * p["ny"] * p["nz"]
+    p["init"] = {"T_K": np.full(n, 520.0), "Ts_K": np.full(n, 500.0)}
+    o = oracle.Oracle3(p)
+    wall = o.classes() == 3
+    assert wall.sum() == p["nx"] * p["ny"]
+    o.step(1)
+    dT = o.moments()[-1][wall] - 500.0
+    np.testing.assert_allclose(dT, 2.0 * p["kappa_f"] * (520.0 - 500.0) / p["rhocp_s"], rtol=1e-9)

@@ -924,3 +924,20 @@ def test_parabolic_inlet_profile(n_gas):
     X = rho / M / (rho / M).sum(1)[:, None]
     X_in = np.array([s["X_inlet"] for s in p["species"]])
     np.testing.assert_allclose(X, np.repeat(X_in[None], n_gas, 0), rtol=1e-13, atol=1e-18)
+
+
+def test_paper_coupling_one_step_by_hand():
+    """Eq. wall_temperature (the paper's coupling law): a one-row FD slab in a periodic
+    box, every slab node a wall with gas on both sides and no temperature gradient along
+    the slab. From a uniform gas at T_g and solid at T_s0 the first step moves the solid
+    by exactly 2 kappa_f (T_g - T_s0) / (rho c_p)_s (the gas temperature of the previous
+    time level on the two gas neighbours)."""
+    p = W.periodic_box(8, 8, solid_rows=1, reactions=[], coupling=1)
+    n = p["nx"] * p["ny"]
+    p["init"] = {"T_K": np.full(n, 520.0), "Ts_K": np.full(n, 500.0)}
+    o = oracle.Oracle(p)
+    wall = o.classes() == 3
+    assert wall.sum() == p["nx"]
+    o.step(1)
+    dT = o.moments()[-1][wall] - 500.0
+    np.testing.assert_allclose(dT, 2.0 * p["kappa_f"] * (520.0 - 500.0) / p["rhocp_s"], rtol=1e-9)
