@@ -709,3 +709,23 @@ def test_paper_coupling3_one_step_by_hand():
     o.step(1)
     dT = o.moments()[-1][wall] - 500.0
     np.testing.assert_allclose(dT, 2.0 * p["kappa_f"] * (520.0 - 500.0) / p["rhocp_s"], rtol=1e-9)
+
+
+def test_residual3_closed_form_on_a_decaying_eigenmode():
+    """Reading R16's residual on D3Q19: a solid block with fixed-T faces at T_inlet
+    carrying the product eigenmode of the 7-point FD step decays as lam^t, so the
+    residual over K steps is (lam^-K - 1) / K; +inf on the first call."""
+    nx, ny, nz = 9, 11, 13
+    mask = np.full((nz, ny, nx), W.INERT, np.uint8)
+    p = W._base(3, nx, ny, nz, mask, [W.FIXED_T] * 6, reactions=[])
+    assert p["T_outer_K"] == p["T_inlet_K"]
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    mode = (np.sin(np.pi * (x + 1) / (nx + 1)) * np.sin(np.pi * (y + 1) / (ny + 1))
+            * np.sin(np.pi * (z + 1) / (nz + 1)))
+    p["init"] = {"Ts_K": (p["T_outer_K"] + 6.0 * mode).ravel()}
+    o = oracle.Oracle3(p)
+    lam = 1.0 - 4.0 * p["alpha_s"] * sum(math.sin(math.pi / (2 * (m + 1))) ** 2 for m in (nx, ny, nz))
+    assert o.residual(0) == float("inf")
+    for K in (10, 25):
+        o.step(K)
+        assert math.isclose(o.residual(K), (lam ** -K - 1.0) / K, rel_tol=1e-11)

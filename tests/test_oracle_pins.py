@@ -941,3 +941,24 @@ def test_paper_coupling_one_step_by_hand():
     o.step(1)
     dT = o.moments()[-1][wall] - 500.0
     np.testing.assert_allclose(dT, 2.0 * p["kappa_f"] * (520.0 - 500.0) / p["rhocp_s"], rtol=1e-9)
+
+
+def test_residual_closed_form_on_a_decaying_eigenmode():
+    """Reading R16's residual, max over fields of ||F(t) - F(t - K)|| / (K ||F(t) - F_ref||),
+    on a solid block with fixed-T faces at T_inlet carrying the product eigenmode of the
+    FD step: T_s - T_inlet = A lam^t mode, so the residual is (lam^-K - 1) / K at any t
+    (no gas field contributes). Also +inf on the first call."""
+    nx, ny = 11, 15
+    mask = np.full((ny, nx), W.INERT, np.uint8)
+    p = W._base(2, nx, ny, 1, mask, [W.FIXED_T] * 4, reactions=[])
+    assert p["T_outer_K"] == p["T_inlet_K"]
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    mode = np.sin(np.pi * (x + 1) / (nx + 1)) * np.sin(np.pi * (y + 1) / (ny + 1))
+    p["init"] = {"Ts_K": (p["T_outer_K"] + 7.0 * mode).ravel()}
+    o = oracle.Oracle(p)
+    lam = 1.0 - 4.0 * p["alpha_s"] * (math.sin(math.pi / (2 * (nx + 1))) ** 2
+                                      + math.sin(math.pi / (2 * (ny + 1))) ** 2)
+    assert o.residual(0) == float("inf")
+    for K in (10, 25):
+        o.step(K)
+        assert math.isclose(o.residual(K), (lam ** -K - 1.0) / K, rel_tol=1e-11)
