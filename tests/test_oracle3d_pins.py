@@ -729,3 +729,40 @@ def test_residual3_closed_form_on_a_decaying_eigenmode():
     for K in (10, 25):
         o.step(K)
         assert math.isclose(o.residual(K), (lam ** -K - 1.0) / K, rel_tol=1e-11)
+
+
+def test_inlet3_holds_the_inlet_equilibrium():
+    """Sec. 6's inlet on D3Q19 (plug profile): every inlet node holds, from its stored
+    populations, u = (u_inlet, 0, 0), the inlet composition, C = 1 and T_inlet, here in
+    a channel whose gas starts 10 K below the inlet temperature; T from the moments,
+    T = (E - |J|^2 / rho) / (D C), D = 3."""
+    nx, ng, wall, nz = 12, 6, 2, 4
+    ny = ng + 2 * wall
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, :wall, :] = W.INERT
+    mask[:, wall + ng:, :] = W.INERT
+    p = W._base(3, nx, ny, nz, mask, [W.INLET, W.OUTLET, W.FIXED_T, W.FIXED_T, W.PERIODIC, W.PERIODIC],
+                u_inlet=0.02, inlet_profile=W.PLUG, reactions=[], T_init_K=490.0)
+    assert p["T_inlet_K"] == 500.0
+    o = oracle.Oracle3(p)
+    o.step(3)
+    ns = len(p["species"])
+    M = np.array([s["M_gmol"] for s in p["species"]])
+    M = M / M.min()
+    c = np.sqrt(1.0 / M)
+    e = _vel().astype(float)
+    e2 = (e * e).sum(1)
+    g = o.populations()
+    inlet = np.where(o.classes() == 1)[0]
+    assert len(inlet) == ng * nz
+    rho = np.array([g[:, :, k].sum(1) for k in inlet])
+    J = np.array([sum(c[j] * (e.T @ g[j, :, k]) for j in range(ns)) for k in inlet])
+    E = np.array([sum(c[j] ** 2 * (e2 * g[j, :, k]).sum() for j in range(ns)) for k in inlet])
+    C = (rho / M).sum(1)
+    u = J / rho.sum(1)[:, None]
+    T_K = (E - (J ** 2).sum(1) / rho.sum(1)) / (3.0 * C) * 3.0 * p["T0_K"]
+    X_in = np.array([s["X_inlet"] for s in p["species"]])
+    np.testing.assert_allclose(u, np.repeat([[p["u_inlet"], 0.0, 0.0]], len(inlet), 0), rtol=1e-13, atol=1e-16)
+    np.testing.assert_allclose(rho / M / C[:, None], np.repeat(X_in[None], len(inlet), 0), rtol=1e-13, atol=1e-18)
+    np.testing.assert_allclose(C, 1.0, rtol=1e-13)
+    np.testing.assert_allclose(T_K, p["T_inlet_K"], rtol=1e-12)

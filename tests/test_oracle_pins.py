@@ -899,9 +899,11 @@ def test_parabolic_inlet_profile(n_gas):
     """Reading R13's parabolic inlet: the velocity the inlet nodes hold (from their
     stored populations) lies on the quadratic that vanishes on the two wall nodes
     bounding the inlet run and peaks at u_inlet mid-way between them, along x only, with
-    the inlet composition."""
+    the inlet composition, temperature and C = 1 (Sec. 6: the inlet equilibrium), here
+    in a channel whose gas starts 10 K below the inlet temperature."""
     wall = 3
-    p = W.channel(nx=16, n_gas=n_gas, wall=wall, reactions=[])
+    p = W.channel(nx=16, n_gas=n_gas, wall=wall, reactions=[], T_init_K=490.0)
+    assert p["T_inlet_K"] == 500.0
     o = oracle.Oracle(p)
     o.step(3)
     ns = o.ns
@@ -924,6 +926,12 @@ def test_parabolic_inlet_profile(n_gas):
     X = rho / M / (rho / M).sum(1)[:, None]
     X_in = np.array([s["X_inlet"] for s in p["species"]])
     np.testing.assert_allclose(X, np.repeat(X_in[None], n_gas, 0), rtol=1e-13, atol=1e-18)
+    # C and T from the populations' moments: T = (E - |J|^2 / rho) / (D C), D = 2
+    C = (rho / M).sum(1)
+    E = np.array([sum(c[j] ** 2 * ((EX ** 2 + EY ** 2) * g[j, :, k]).sum() for j in range(ns)) for k in inlet])
+    T_K = (E - (J ** 2).sum(1) / rho.sum(1)) / (2.0 * C) * 3.0 * p["T0_K"]
+    np.testing.assert_allclose(C, 1.0, rtol=1e-13)
+    np.testing.assert_allclose(T_K, p["T_inlet_K"], rtol=1e-12)
 
 
 def test_paper_coupling_one_step_by_hand():
