@@ -34,6 +34,10 @@ def _problem(name):
         p = W.porous_disks(nx=100, ny=60, porosity=0.75, rmin=3.0, rmax=7.0, seed=7, u_inlet=0.01, coupling=1)
         p["init"] = W.random_fields(p, seed=73, du=0.005)
         return p
+    if name == "local_tau":  # relaxation times from each node's own moments (Wilke, mixture-averaged D)
+        p = W.local_transport(W.channel(nx=64, n_gas=12, wall=4))
+        p["init"] = W.random_fields(p, seed=77, du=0.005)
+        return p
     if name == "channel3":  # D3Q19: inlet, outlet, catalytic FD walls in y, periodic z
         nx, ng, wall, nz = 40, 8, 3, 6
         mask = np.zeros((nz, ng + 2 * wall, nx), np.uint8)
@@ -120,7 +124,8 @@ def test_partition_is_even_and_covers_the_lattice():
 
 
 @pytest.mark.parametrize("name, world", [("channel", 2), ("channel", 4), ("periodic", 2), ("periodic", 4),
-                                         ("porous", 2), ("porous", 4), ("channel3", 2), ("periodic3", 4),
+                                         ("porous", 2), ("porous", 4), ("local_tau", 2), ("channel3", 2),
+                                         ("periodic3", 4),
                                          ("spheres3", 2), ("spheres3", 4)])
 def test_slabs_bitwise_equal_to_monolithic(name, world):
     res = _run(name, world)
