@@ -75,3 +75,48 @@ def test_traffic_record_holds_for_its_source_and_listed_equivalents():
     assert bench.traffic_record_holds(rec, "aaaa") and bench.traffic_record_holds(rec, "bbbb")
     assert not bench.traffic_record_holds(rec, "cccc")
     assert not bench.traffic_record_holds({"kernel_source_sha": "aaaa"}, "bbbb")
+
+
+def test_steady_runs_close_their_solver_when_a_step_raises(monkeypatch):
+    """bench.run_to_steady and bench.precision_handoff close the solver they created
+    when a step raises, and let the error through (a stand-in solver, no GPU)."""
+    import torch
+
+    import bench
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    closed = []
+
+    class Boom(RuntimeError):
+        pass
+
+    class FakeSolver:
+        def __init__(self, p, device=0, storage="fp32"):
+            pass
+
+        def set_fields(self, f):
+            pass
+
+        def residual(self):
+            return float("inf")
+
+        def step(self, n):
+            raise Boom("step failed")
+
+        def sync(self):
+            pass
+
+        def restart_fields(self):
+            return {}
+
+        def close(self):
+            closed.append(self)
+
+    class FakeModule:
+        Solver = FakeSolver
+
+    with pytest.raises(Boom):
+        bench.run_to_steady(FakeModule, {}, init={"X": None})
+    assert len(closed) == 1
+    with pytest.raises(Boom):
+        bench.precision_handoff(FakeModule, {}, "fp16")
+    assert len(closed) == 2
