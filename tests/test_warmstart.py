@@ -72,3 +72,48 @@ def test_trained_network_predicts_unseen_steady_fields():
     print("warm start", r)
     assert r["cold"]["converged"]
     assert r["warm"]["converged"] or r["warm"]["fallback"]
+
+
+def test_solve_closes_its_solver_on_errors(monkeypatch):
+    """warmstart.solve with a stand-in solver (no GPU): a failed field upload closes the
+    solver and raises; a solver error in a step counts as a diverged run and returns the
+    solver; any other error in a step closes it and raises."""
+    import torch
+
+    from paper_1804_07588_gb300 import fdlbm
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    closed = []
+    mode = {}
+
+    class FakeSolver:
+        def __init__(self, p, device=0):
+            pass
+
+        def set_fields(self, f):
+            if mode.get("upload"):
+                raise ValueError("bad fields")
+
+        def residual(self):
+            return 1.0
+
+        def step(self, n):
+            raise mode["step"]
+
+        def sync(self):
+            pass
+
+        def close(self):
+            closed.append(self)
+
+    monkeypatch.setattr(fdlbm, "Solver", FakeSolver)
+    mode.update(upload=True, step=RuntimeError("unused"))
+    with pytest.raises(ValueError):
+        WS.solve({}, init={"X": None})
+    assert len(closed) == 1
+    mode.update(upload=False, step=fdlbm.FdlbmError(-5, "unstable"))
+    s, st = WS.solve({}, init={"X": None})
+    assert st["diverged"] and not st["converged"] and len(closed) == 1
+    mode.update(step=KeyError("other"))
+    with pytest.raises(KeyError):
+        WS.solve({})
+    assert len(closed) == 2
