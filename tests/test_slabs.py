@@ -1,4 +1,4 @@
-"""The slab decomposition of the D2Q9 and D3Q19 paths (x slabs, 4-column ghost strips
+"""The slab decomposition of the D2Q9 and D3Q19 paths (x slabs, 3-column ghost strips
 exchanged by point-to-point send/recv every step, FP64 all-reduce of the totals and the
 residual), checked with the FP64 oracles as every rank's slab solver: gloo ranks on CPU,
 world sizes 2 and 4. The gathered moment fields must equal the undecomposed oracle's bit
