@@ -526,7 +526,8 @@ def run_reference(args, rank, world):
         "config": {"workload": WORKLOAD, "sample": desc,
                    "oracle": f"plain FP64 C, single-threaded, {ncores} concurrent processes on the host's cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
-                         "sample": f"{ncores} processes, each on its own crop of the bed like: {desc}",
+                         "sample": f"{ncores} concurrent single-threaded oracle processes, each on its own "
+                                   f"crop of the bed (the first: {desc})",
                          "single_core": {"value": single, "steps": args.steps, "seconds": el}},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
