@@ -64,3 +64,14 @@ def test_sweep_covers_every_combination(monkeypatch):
     assert len(calls) == len(autotune.BANDS) * len(autotune.TILE_ENTRIES) * len(autotune.WALL_ORDERS)
     assert (e["band_rows"], e["tile_entries"], e["wall_order"]) == (16, 192, 0)
     assert e["us_default"] == fake(None, None, 16, 256, 0)
+
+
+def test_committed_table_gives_swept_orders_for_the_bench_bed():
+    """The table shipped with the package answers for the 1024x512 bench bed in every
+    storage type, with values from the sweep sets (not the default fallback's path)."""
+    import os
+    assert os.path.exists(autotune.TABLE)
+    p = W.config1()
+    for storage in ("fp32", "bf16", "fp16"):
+        b, t, o = autotune.lookup(p, storage)
+        assert b in autotune.BANDS and t in autotune.TILE_ENTRIES and o in autotune.WALL_ORDERS
