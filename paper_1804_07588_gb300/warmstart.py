@@ -216,17 +216,24 @@ def predict(model, p: dict) -> np.ndarray:
 
 def warm_vs_cold(model, p: dict, tol=1e-6, every=250, max_steps=200_000, device=0) -> dict:
     """Steps and wall time to the residual tol from a cold start and from the network's
-    prediction (inference time included); a warm run that diverges or needs more steps
-    than the cold one is counted as its own cost plus the cold run (the fallback)."""
+    prediction (inference time included); a warm run that diverges, needs more steps
+    than the cold one, or whose predicted fields the solver rejects is counted as its own
+    cost plus the cold run (the fallback)."""
     import torch
+
+    from . import fdlbm
     s, cold = solve(p, None, tol, every, max_steps, device)
     s.close()
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
     init = fields_from_prediction(p, predict(model, p))
     t_inf = time.perf_counter() - t0
-    s, warm = solve(p, init, tol, every, max(cold["steps"], every), device)
-    s.close()
+    try:
+        s, warm = solve(p, init, tol, every, max(cold["steps"], every), device)
+        s.close()
+    except fdlbm.FdlbmError as e:  # fields outside the equilibrium's range: not used
+        warm = {"steps": 0, "seconds": 0.0, "residual": float("inf"), "converged": False,
+                "diverged": False, "rejected": str(e)[:200]}
     warm["seconds"] += t_inf
     warm["inference_seconds"] = t_inf
     warm["fallback"] = not warm["converged"]

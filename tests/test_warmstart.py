@@ -117,3 +117,39 @@ def test_solve_closes_its_solver_on_errors(monkeypatch):
     with pytest.raises(KeyError):
         WS.solve({})
     assert len(closed) == 2
+
+
+def test_rejected_prediction_falls_back_to_the_cold_run(monkeypatch):
+    """A prediction whose fields the solver rejects (stand-in solver, no GPU) is counted
+    like a diverged warm run: its cost plus the cold run."""
+    import torch
+
+    from paper_1804_07588_gb300 import fdlbm
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(WS, "predict", lambda model, p: None)
+    monkeypatch.setattr(WS, "fields_from_prediction", lambda p, y: {"X": None})
+
+    class FakeSolver:
+        def __init__(self, p, device=0):
+            self.r = 1.0
+
+        def set_fields(self, f):
+            raise fdlbm.FdlbmError(-1, "fields outside the equilibrium's range")
+
+        def residual(self):
+            return self.r
+
+        def step(self, n):
+            self.r *= 1e-3
+
+        def sync(self):
+            pass
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(fdlbm, "Solver", FakeSolver)
+    r = WS.warm_vs_cold(None, {}, tol=1e-6, every=10)
+    assert r["cold"]["converged"] and r["cold"]["steps"] == 30      # residual 1e-9 at the third check
+    assert r["warm"]["fallback"] and "rejected" in r["warm"]
+    assert r["warm"]["steps"] == r["cold"]["steps"] and r["warm"]["seconds"] >= r["cold"]["seconds"]
